@@ -1,0 +1,268 @@
+"""Seeded synthetic scene generators.
+
+This module produces INPUTS only: vertex positions, tetrahedra, obstacle
+triangles, Dirichlet flags, materials and solver parameters.  It holds none
+of the method's arithmetic (no mass lumping, no surface extraction, no
+energies, no distances); both the CUDA library and the CPU oracle derive
+everything else from these arrays on their own.
+
+The scenes stand in for the paper's assets (its meshes are not available):
+tetrahedralised cubes (Kuhn 6-tet split of a regular grid) dropped onto
+static triangle obstacles, shaped like the workloads of the paper's
+evaluation (section 6, Tab. 2): stable Neo-Hookean solids, E = 1e5 Pa,
+nu = 0.4, rho = 1000 kg/m^3, h = 0.01 s, contact radius delta = 1e-3 m.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Kuhn (Freudenthal) split of a unit cell into 6 tets sharing the main
+# diagonal 0 -> 7.  Corners are numbered by bits (x = 1, y = 2, z = 4).
+# Every cell uses the same diagonal, so neighbouring cells conform.
+_KUHN = []
+for a, b in ((0, 1), (0, 2), (1, 0), (1, 2), (2, 0), (2, 1)):
+    ca = 1 << a
+    cb = ca | (1 << b)
+    _KUHN.append((0, ca, cb, 7))
+_KUHN = np.array(_KUHN, dtype=np.int64)
+
+
+@dataclass
+class Params:
+    """Solver parameters (defaults: section 6 and Alg. 1-3 of the paper).
+
+    dt: time step h; delta: contact offset (section 4.2); eps, k_min:
+    termination rule (Eq. termination, section 6 uses 1e-3 and 2);
+    cg_tol: relative PCG tolerance; gamma_decay: Gamma of section 4.2;
+    c_mu: C of section 5.2; s_ccd: ACCD conservative rescaling.
+    """
+    dt: float = 0.01
+    delta: float = 1e-3
+    gravity: tuple = (0.0, 0.0, -9.8)
+    eps: float = 1e-3
+    k_min: int = 2
+    cg_tol: float = 1e-6
+    gamma_decay: float = 0.9
+    c_mu: float = 0.1
+    s_ccd: float = 0.1
+    max_outer: int = 1000
+    max_newton: int = 50
+    max_ls: int = 30
+    max_cg: int = 10000
+    precision: int = 0  # 0 = FP64, 1 = mixed (FP32 Hessian/SpMV/preconditioner)
+
+
+@dataclass
+class Scene:
+    name: str
+    rest: np.ndarray          # (nv, 3) float64 rest positions
+    x0: np.ndarray            # (nv, 3) float64 initial positions
+    v0: np.ndarray            # (nv, 3) float64 initial velocities
+    tets: np.ndarray          # (nt, 4) int32, positively oriented at rest
+    tet_mat: np.ndarray       # (nt,) int32 material index
+    mats: np.ndarray          # (nm, 3) float64: E [Pa], nu, rho [kg/m^3]
+    tris: np.ndarray          # (nx, 3) int32 obstacle triangles (vertex ids)
+    dirichlet: np.ndarray     # (nv,) uint8, 1 = prescribed (obstacle) vertex
+    params: Params = field(default_factory=Params)
+    n_steps: int = 20
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return int(self.x0.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tets.shape[0])
+
+    def bbox_diag(self, elastic_only: bool = True) -> float:
+        sel = self.dirichlet == 0 if elastic_only else slice(None)
+        p = self.x0[sel]
+        return float(np.linalg.norm(p.max(0) - p.min(0)))
+
+
+def cube_mesh(cells: int, side: float):
+    """Regular (cells+1)^3 grid on [0, side]^3 split into 6*cells^3 tets."""
+    n = cells + 1
+    g = np.arange(n, dtype=np.float64) * (side / cells)
+    zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")
+    verts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    ii, jj, kk = np.meshgrid(np.arange(cells), np.arange(cells), np.arange(cells), indexing="ij")
+    base = (kk.ravel() + n * jj.ravel() + n * n * ii.ravel())  # (x=kk, y=jj, z=ii)
+    corner_off = np.array([(c & 1) + n * ((c >> 1) & 1) + n * n * ((c >> 2) & 1) for c in range(8)])
+    tets = base[:, None, None] + corner_off[_KUHN][None, :, :]
+    tets = tets.reshape(-1, 4)
+    # orient positively on the regular grid
+    d = verts[tets[:, 1:]] - verts[tets[:, :1]]
+    neg = np.linalg.det(d) < 0
+    tets[neg] = tets[neg][:, [0, 2, 1, 3]]
+    return verts, tets.astype(np.int32)
+
+
+def ground_quad(half: float, z: float = 0.0, center=(0.0, 0.0)):
+    cx, cy = center
+    v = np.array([[cx - half, cy - half, z], [cx + half, cy - half, z],
+                  [cx + half, cy + half, z], [cx - half, cy + half, z]])
+    t = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+    return v, t
+
+
+def open_box(half: float, height: float):
+    """Floor (z=0) plus four walls, as 10 static triangles on 8 vertices."""
+    v = np.array([[-half, -half, 0], [half, -half, 0], [half, half, 0], [-half, half, 0],
+                  [-half, -half, height], [half, -half, height], [half, half, height],
+                  [-half, half, height]], dtype=np.float64)
+    t = [[0, 1, 2], [0, 2, 3]]
+    for a in range(4):
+        b = (a + 1) % 4
+        t += [[a, b, b + 4], [a, b + 4, a + 4]]
+    return v, np.array(t, dtype=np.int32)
+
+
+class _Builder:
+    def __init__(self):
+        self.verts, self.tets, self.mat, self.tris, self.dir = [], [], [], [], []
+        self.nv = 0
+
+    def add_solid(self, verts, tets, mat):
+        self.verts.append(verts)
+        self.tets.append(tets + self.nv)
+        self.mat.append(np.full(len(tets), mat, dtype=np.int32))
+        self.dir.append(np.zeros(len(verts), dtype=np.uint8))
+        self.nv += len(verts)
+
+    def add_obstacle(self, verts, tris):
+        self.verts.append(verts)
+        self.tris.append(tris + self.nv)
+        self.dir.append(np.ones(len(verts), dtype=np.uint8))
+        self.nv += len(verts)
+
+    def build(self, name, mats, params, n_steps, meta=None):
+        x = np.concatenate(self.verts).astype(np.float64)
+        tets = np.concatenate(self.tets).astype(np.int32) if self.tets else np.zeros((0, 4), np.int32)
+        tm = np.concatenate(self.mat) if self.mat else np.zeros(0, np.int32)
+        tris = np.concatenate(self.tris).astype(np.int32) if self.tris else np.zeros((0, 3), np.int32)
+        return Scene(name=name, rest=x.copy(), x0=x.copy(), v0=np.zeros_like(x), tets=tets,
+                     tet_mat=tm.astype(np.int32), mats=np.asarray(mats, np.float64).reshape(-1, 3),
+                     tris=tris, dirichlet=np.concatenate(self.dir), params=params,
+                     n_steps=n_steps, meta=meta or {})
+
+
+def _jittered_cube(rng, cells, side, origin, yaw=0.0, jitter=1e-4):
+    v, t = cube_mesh(cells, side)
+    v = v + rng.uniform(-jitter, jitter, size=v.shape)
+    if yaw != 0.0:
+        c, s = math.cos(yaw), math.sin(yaw)
+        ctr = np.array([side / 2, side / 2, 0.0])
+        r = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+        v = (v - ctr) @ r.T + ctr
+    return v + np.asarray(origin, dtype=np.float64), t
+
+
+def two_cubes(seed: int = 0, cells: int = 4, side: float = 0.1, precision: int = 0) -> Scene:
+    """Two jittered cubes (4^3 cells, 384 tets, 125 verts each), the upper one
+    1 mm above the lower, falling onto a static 2 m x 2 m ground quad at z = 0;
+    20 steps, FP64."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    z0 = 0.01
+    for k in range(2):
+        v, t = _jittered_cube(rng, cells, side, (-side / 2, -side / 2, z0 + k * (side + 1e-3)))
+        b.add_solid(v, t, 0)
+    gv, gt = ground_quad(1.0)
+    b.add_obstacle(gv, gt)
+    return b.build(f"two_cubes_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]],
+                   Params(precision=precision), 20, {"seed": seed, "cells": cells})
+
+
+def eight_cubes(seed: int = 0, cells: int = 16, side: float = 0.1, precision: int = 1) -> Scene:
+    """Eight jittered cubes (16^3 cells: 24,576 tets / 4,913 verts each) in a
+    2x2x2 layout with seeded yaw and offsets, dropped into a static open box
+    (0.6 x 0.6 m floor, 0.6 m walls); 50 steps, mixed precision."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    spacing = 0.17
+    for layer, zbase in enumerate((0.06, 0.20)):
+        for iy in range(2):
+            for ix in range(2):
+                cx = (ix - 0.5) * spacing + rng.uniform(-0.01, 0.01)
+                cy = (iy - 0.5) * spacing + rng.uniform(-0.01, 0.01)
+                yaw = rng.uniform(0.0, 2 * math.pi)
+                z = zbase + rng.uniform(0.0, 0.02)
+                v, t = _jittered_cube(rng, cells, side, (cx - side / 2, cy - side / 2, z), yaw)
+                b.add_solid(v, t, 0)
+    bv, bt = open_box(0.3, 0.6)
+    b.add_obstacle(bv, bt)
+    return b.build(f"eight_cubes_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]],
+                   Params(precision=precision), 50, {"seed": seed, "cells": cells})
+
+
+def single_cube(seed: int = 0, cells: int = 2, side: float = 0.1, z: float = 0.5,
+                v0=(0.0, 0.0, 0.0), with_ground: bool = False, gravity=(0.0, 0.0, -9.8),
+                xy=(0.0, 0.0)) -> Scene:
+    """One jittered cube, optionally above a ground quad (small test scene)."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    v, t = _jittered_cube(rng, cells, side, (xy[0] - side / 2, xy[1] - side / 2, z))
+    b.add_solid(v, t, 0)
+    if with_ground:
+        gv, gt = ground_quad(1.0)
+        b.add_obstacle(gv, gt)
+    s = b.build(f"single_cube_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]],
+                Params(gravity=tuple(gravity)), 10, {"seed": seed})
+    s.v0[:] = 0.0
+    s.v0[s.dirichlet == 0] = np.asarray(v0, dtype=np.float64)
+    return s
+
+
+def colliding_cubes(seed: int = 0, cells: int = 2, side: float = 0.1, gap: float = 0.004,
+                    speed: float = 1.0) -> Scene:
+    """Two cubes approaching each other along x with no gravity and no
+    obstacles (momentum-conservation test scene)."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    v, t = _jittered_cube(rng, cells, side, (-side - gap / 2, -side / 2, 0.0))
+    b.add_solid(v, t, 0)
+    v2, t2 = _jittered_cube(rng, cells, side, (gap / 2, -side / 2 + 0.02, 0.01))
+    b.add_solid(v2, t2, 0)
+    s = b.build(f"colliding_cubes_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]],
+                Params(gravity=(0.0, 0.0, 0.0)), 10, {"seed": seed})
+    n1 = len(v)
+    s.v0[:n1, 0] = speed
+    return s
+
+
+def moving_plate(seed: int = 0, cells: int = 3, side: float = 0.1, speed: float = 0.5) -> Scene:
+    """A cube resting near a ground quad, with a 2-triangle plate above it
+    that moves down at `speed` (moving Dirichlet boundary, section 5.3)."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    v, t = _jittered_cube(rng, cells, side, (-side / 2, -side / 2, 0.002))
+    b.add_solid(v, t, 0)
+    gv, gt = ground_quad(0.3)
+    b.add_obstacle(gv, gt)
+    pv, pt = ground_quad(0.12, z=side + 0.012)
+    pt = pt[:, [0, 2, 1]]
+    b.add_obstacle(pv, pt)
+    s = b.build(f"moving_plate_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]], Params(), 10,
+                {"seed": seed, "plate_speed": speed})
+    s.meta["plate_vertices"] = np.arange(s.nv - 4, s.nv)
+    return s
+
+
+def plate_targets(scene: Scene, step: int) -> np.ndarray:
+    """Prescribed obstacle positions at the end of step `step` (0-based) for
+    moving_plate scenes: the plate moves along -z at constant speed."""
+    x = scene.x0.copy()
+    ids = scene.meta["plate_vertices"]
+    x[ids, 2] -= scene.meta["plate_speed"] * scene.params.dt * (step + 1)
+    return x[scene.dirichlet == 1]
+
+
+CONFIGS = {
+    "two_cubes": two_cubes,
+    "eight_cubes": eight_cubes,
+}
