@@ -1,0 +1,378 @@
+"""Benchmark: time steps per second of the eight-cube scene (8 cubes of
+16^3 cells, 196,608 tets, 39,304 vertices, dropped into a static open box;
+mixed precision) through the C ABI, on one or more GPUs (one independent
+replica per rank, weak scaling).
+
+A "step" is one time step of Alg. 1 (all of: inertia target, mu, Newton
+solves with PCG, line search, multiplier update, active-set update, CCD,
+blending).  Warm-up steps advance the same simulation; the timed steps are
+the ones that follow.  L2 is flushed (a 512 MiB write) before every timed
+step, outside the timed interval; each step is timed with CUDA events on the
+library's stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s & PCG HBM GB/s vs peak; p50/p99 step latency, batched vs plain FP64"
+WORKLOAD = ("eight_cubes: 8 cubes x 16^3 cells (196,608 tets, 39,304 verts) with seeded yaw/offsets "
+            "dropped into a static open box; SNH E=1e5 nu=0.4 rho=1000, h=0.01, delta=1e-3, CG tol 1e-6, "
+            "mixed precision (FP32 Hessian/SpMV/preconditioner, FP64 CCD/TOI/multipliers/dots)")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        for s in self.samples:
+            for name, val in zip(self.NAMES, s[2:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of the timed kernels
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(kernel, info, nv, nt, nc, mixed):
+    w = 4 if mixed else 8
+    nnzb = info["nnzb"]
+    if kernel == "spmv_bsr_contact":
+        # values + column index per block, row pointer + x + y per vertex,
+        # contact pairs (12 gradient entries, weight, 4 ids, mask)
+        return nnzb * (9 * w + 4) + nv * (4 + 3 * w + 3 * w) + nc * (12 * 8 + 8 + 16 + 1)
+    if kernel == "pcg_update":
+        # read x(8) p(w) q(w) r(8) P^-1(9w); write x(8) r(8) z(w), per DoF / vertex
+        return nv * (3 * (8 + w + w + 8 + 8 + 8 + w) + 9 * w)
+    if kernel == "pcg_direction":
+        return nv * 3 * (3 * w + w)  # read z, p; write p, q
+    if kernel == "elastic_grad_hess":
+        # per tet: ids, 4 gathered positions, Dm^-1, V, mu, lam, block map;
+        # outputs: block values once, gradient
+        return nt * (16 + 96 + 72 + 24 + 40) + nnzb * 9 * w + nv * 24
+    if kernel == "energy":
+        return nt * (16 + 96 + 72 + 24) + nv * (8 + 1 + 48) + nc * (16 + 96 + 32)
+    return None
+
+
+def traffic_for(kernel):
+    """per-launch DRAM traffic from a committed ncu summary, if it was taken
+    on the current kernel source (else None)"""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2512_12151_b300", "csrc", ent["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(ws, v):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(seconds, seed=0):
+    """Times the oracle (single-threaded FP64 C) on the same scene from its
+    initial state, whole time steps, until `seconds` have elapsed (at least
+    one step)."""
+    import oracle as O
+    from paper_2512_12151_b300 import scenes
+    s = scenes.eight_cubes(seed)
+    o = O.Oracle(s)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= s.n_steps:
+            break
+    return n / el, n, el
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    budget = float(os.environ.get("BF_REF_SECONDS", "90"))
+    value, n, el = oracle_sample(budget)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 0,
+            "steps": n, "warmup": 0, "ms_per_step": 1000.0 * el / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("mixed precision (FP32 Hessian/SpMV/preconditioner, "
+                                                    "FP64 CCD/TOI/multipliers/dots)", "FP64 oracle"),
+                       "sample": f"first {n} time steps from the initial state"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} time steps of the eight-cube scene from rest "
+                                       f"({el:.1f} s, single-threaded FP64 C oracle, no warm-up)"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=47)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_init(args)
+    import torch
+    from paper_2512_12151_b300 import binding as B
+    from paper_2512_12151_b300 import build as build_mod
+    from paper_2512_12151_b300 import scenes
+    if not os.path.exists(B.LIB_PATH):
+        build_mod.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(seed):
+        s = scenes.eight_cubes(seed, precision=args.precision)
+        return s, B.Sim(s, stream=stream.cuda_stream)
+
+    seed = rank
+    s, sim = make(seed)
+    info = sim.info()
+    W, K = args.warmup, args.steps
+    stats_all = []
+    # ---- pass 1: device-resident steps, per-step CUDA events -------------
+    for _ in range(W):
+        _, st = sim.step(1)
+        stats_all.append(st[0])
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = B.bf_get_launch_count(sim.h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_wall0 = time.perf_counter()
+    for i in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        _, st = sim.step(1)
+        ev[i][1].record(stream)
+        stats_all.append(st[0])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(ws)
+    clk = clocks.stop()
+    launches = B.bf_get_launch_count(sim.h) - n0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = allmax(ws, sum(step_ms))
+    steps_all = allsum(ws, K)
+    value = steps_all / (total_ms / 1000.0)
+    ms_sorted = sorted(step_ms)
+    p50 = ms_sorted[len(ms_sorted) // 2]
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
+    timed_stats = stats_all[W:]
+    sim.close()
+
+    # ---- pass 2: same steps with per-kernel CUDA events (roofline) -------
+    s2, sim2 = make(seed)
+    for _ in range(W):
+        sim2.step(1)
+    B.bf_enable_timers(sim2.h, True)
+    for i in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sim2.step(1)
+    torch.cuda.synchronize()
+    timers = B.bf_get_timers(sim2.h)
+    sim2.close()
+    peak, peak_kind = load_peaks()
+    mixed = args.precision == 1
+    nc_mean = statistics.mean(st["n_contacts"] for st in timed_stats) if timed_stats else 0
+    kernels = {}
+    for name, (n, ms) in timers.items():
+        if n == 0:
+            continue
+        avg_ms = ms / n
+        ab = algorithmic_bytes(name, info, s.nv, s.nt, nc_mean, mixed)
+        kernels[name] = {"launches": n, "total_ms": round(ms, 3), "avg_us": round(1000 * avg_ms, 3),
+                         "alg_bytes": ab, "gbs": (ab / (avg_ms / 1000.0) / 1e9) if ab else None}
+    hbm_kernels = {k: v for k, v in kernels.items() if v["gbs"] is not None}
+    dom = max(hbm_kernels, key=lambda k: hbm_kernels[k]["total_ms"]) if hbm_kernels else None
+    roofline = None
+    if dom:
+        achieved = hbm_kernels[dom]["gbs"]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic_for(dom),
+                    "alg_bytes_per_launch": hbm_kernels[dom]["alg_bytes"],
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}, burst copy)",
+                    "note": "working set of this workload is L2-resident between flushes"}
+
+    # ---- pass 3: end to end through the C ABI with host buffers ----------
+    e2e = None
+    if not args.no_e2e:
+        s3 = scenes.eight_cubes(seed, precision=args.precision)
+        sim3 = B.Sim(s3, stream=stream.cuda_stream)
+        xin = torch.empty((s3.nv, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vin = torch.empty((s3.nv, 3), dtype=torch.float64, pin_memory=True).numpy()
+        xin[:] = s3.x0
+        vin[:] = s3.v0
+        for _ in range(W):
+            B.bf_step_host(sim3.h, xin, vin, xin, vin)
+        torch.cuda.synchronize()
+        barrier(ws)
+        e2e_s = 0.0
+        for i in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.bf_step_host(sim3.h, xin, vin, xin, vin)
+            e2e_s += time.perf_counter() - t0
+        sim3.close()
+        e2e_s = allmax(ws, e2e_s)
+        nbytes = 2 * s3.nv * 3 * 8
+        e2e = {"value": steps_all / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
+        v, n, el = oracle_sample(args.cpu_seconds, seed)
+        cpu = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n} time step(s) of the same scene from rest, FP64 single-threaded C "
+                         f"oracle ({el:.1f} s; contact-free steps, so this overstates its contact-step rate)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": K, "warmup": W,
+                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64 (mixed)" if mixed else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD if mixed else WORKLOAD.replace("mixed precision", "FP64"),
+                           "timed_steps": f"{W}..{W + K - 1}", "l2": "flushed (512 MiB write) before each "
+                           "timed step", "parallelism": f"{ws} independent replica(s), one per GPU",
+                           "p50_step_ms": round(p50, 3), "p99_step_ms": round(p99, 3),
+                           "wall_s": round(t_wall, 3),
+                           "mean_outer_iters": statistics.mean(st["outer_iters"] for st in timed_stats),
+                           "mean_cg_iters_per_step": statistics.mean(st["cg_iters"] for st in timed_stats),
+                           "mean_contacts": nc_mean},
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,236 @@
+/*
+ * bf.h -- C ABI of the B300 (sm_103a) implementation of the inner Newton
+ * step, active-set update and CCD of the barrier-free augmented-Lagrangian
+ * (AL) contact method of "Robust and Efficient Penetration-Free
+ * Elastodynamics without Barriers" (arXiv 2512.12151).
+ *
+ * Problem statement (section 3): linear tetrahedra with stacked positions
+ * x and velocities v in R^{3N}, lumped mass M, implicit Euler through the
+ * incremental potential E(x, x~) = 1/2 (x - x~)^T M (x - x~) + h^2 U(x),
+ * x~ = x^t + h v^t + h^2 M^-1 f_ext, subject to a penetration-free path.
+ * A time step (Alg. 1) alternates SolveSubproblem (Alg. 2, Newton on the AL
+ * energy of Eq. total-energy), UpdateActiveSet (Alg. 3) and MaxStepSize
+ * (CCD), blending x^[k+1] = (1 - alpha) x^[k] + alpha xhat^[k+1]
+ * (Eq. CCD-clamp) until the first K_min blend weights sum below eps
+ * (Eq. termination).
+ *
+ * Conventions for every entry point:
+ *  - Status: every function returns an int; 0 is BF_OK, negative values are
+ *    the BF_E_* codes below.  bf_status_str() names them.  Errors are per
+ *    call; a device-side error word is latched per scene and reported by
+ *    the next call that synchronises.
+ *  - Layout: positions and velocities are (n, 3) row-major FP64 (x0 y0 z0
+ *    x1 ...).  Pair keys are 5 int32: PT = {0, p, t0, t1, t2} with the
+ *    triangle's vertex ids sorted ascending; EE = {1, a0, a1, b0, b1} with
+ *    each edge's ids ascending and edge (a0, a1) < edge (b0, b1)
+ *    lexicographically.
+ *  - Memory: "host" arguments are caller-owned host buffers, copied during
+ *    the call; "device" arguments are caller-owned device buffers on the
+ *    scene's device, read or written on the scene's stream, and must stay
+ *    valid until that stream reaches the call's work.  The library owns all
+ *    scene state; it allocates it at creation through the optional
+ *    allocator (else cudaMalloc) and frees it in bf_scene_destroy.
+ *  - Threads: calls on one scene must not overlap; distinct scenes may be
+ *    driven from different host threads.
+ */
+#ifndef BF_H
+#define BF_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BF_OK 0
+#define BF_E_ARG (-1)          /* invalid argument or size */
+#define BF_E_OOM (-2)          /* device allocation failed */
+#define BF_E_CUDA (-3)         /* CUDA runtime error */
+#define BF_E_CG_MAXIT (-4)     /* PCG hit max_cg (result is the last iterate) */
+#define BF_E_NEWTON_MAXIT (-5) /* Newton loop hit max_newton */
+#define BF_E_LS_FAIL (-6)      /* line search found no decrease */
+#define BF_E_OUTER_MAXIT (-7)  /* Alg. 1 loop hit max_outer */
+#define BF_E_NONFINITE (-8)    /* NaN / Inf detected in a solve */
+#define BF_E_CAPACITY (-9)     /* a work buffer overflowed and could not grow */
+#define BF_E_NOT_FOUND (-10)   /* a pair key names no surface primitive pair */
+
+#define BF_PREC_FP64 0  /* everything FP64 */
+#define BF_PREC_MIXED 1 /* FP32 Hessian blocks / SpMV / preconditioner; FP64 gradient,
+                           dots, residuals, energies, CCD, TOI and multipliers */
+
+typedef struct bf_scene bf_scene;
+
+/* Mesh (section 3).  Vertices with dirichlet[v] = 1 are prescribed
+ * (section 5.3): obstacles are triangle meshes on such vertices.  tets are
+ * positively oriented at rest; mats holds (E [Pa], nu, rho [kg/m^3]) per
+ * material; tet_mat picks a material per tet. */
+typedef struct {
+    int32_t n_verts, n_tets, n_mats, n_obst_tris;
+    const double *rest_pos;  /* host, n_verts*3 */
+    const double *init_pos;  /* host, n_verts*3 */
+    const double *init_vel;  /* host, n_verts*3 (may be NULL: zero) */
+    const int32_t *tets;     /* host, n_tets*4 */
+    const int32_t *tet_mat;  /* host, n_tets */
+    const double *mats;      /* host, n_mats*3 */
+    const int32_t *obst_tris;/* host, n_obst_tris*3 (vertex ids of prescribed vertices) */
+    const uint8_t *dirichlet;/* host, n_verts (may be NULL: none) */
+} bf_mesh_desc;
+
+/* Solver parameters.  Paper defaults (section 6, Alg. 1-3): eps = 1e-3,
+ * k_min = 2, gamma_decay (Gamma) = 0.9, c_mu (C of section 5.2) = 0.1.
+ * s_ccd is the ACCD conservative rescaling (target gap s_ccd * d(x0)). */
+typedef struct {
+    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd;
+    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision;
+} bf_params;
+
+/* Per-time-step statistics (the columns of Tab. 1 / Tab. 2). */
+typedef struct {
+    int32_t outer_iters, newton_iters, cg_iters, n_contacts, status, ls_fail, cg_maxit, stalls;
+    double mean_alpha, min_alpha, mu, beta, delta, seconds;
+} bf_step_stats;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns NULL on failure.  Both run on the calling host thread. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} bf_allocator;
+
+/* ---- scene lifetime --------------------------------------------------- */
+
+/* Creates a scene on the current CUDA device: copies the mesh, derives the
+ * lumped mass m_v = sum_e rho V_e / 4 (prescribed vertices get mass 1 and
+ * no elastic energy), Dm^-1, the surface (tet faces used once, plus the
+ * obstacle triangles), the block-sparse pattern, and sizes work buffers.
+ * stream: a cudaStream_t (NULL = default stream) used by all later calls.
+ * Errors: BF_E_ARG (bad sizes, ids out of range, degenerate tets), BF_E_OOM. */
+int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_allocator *alloc,
+                    void *stream, bf_scene **out);
+int bf_scene_destroy(bf_scene *scene);
+int bf_set_stream(bf_scene *scene, void *stream);
+
+/* ---- time stepping (Alg. 1) ------------------------------------------- */
+
+/* Advances n_steps time steps with the cumulative-TOI termination of
+ * Eq. termination.  stats (host, n_steps entries, may be NULL) receives
+ * per-step statistics.  Returns the first non-zero step status. */
+int bf_step(bf_scene *scene, int32_t n_steps, bf_step_stats *stats);
+
+/* Same as bf_step for one step, with the state exchanged through host
+ * buffers: x_in/v_in (host, n_verts*3, may be NULL to keep the resident
+ * state) are uploaded first and x_out/v_out (host, may be NULL) are
+ * downloaded after the step. */
+int bf_step_host(bf_scene *scene, const double *x_in, const double *v_in, double *x_out,
+                 double *v_out, bf_step_stats *stats);
+
+/* State access (host buffers, n_verts*3 each, either may be NULL). */
+int bf_get_state(bf_scene *scene, double *x, double *v);
+int bf_set_state(bf_scene *scene, const double *x, const double *v);
+
+/* Moving boundary (section 5.3): target positions of the prescribed
+ * vertices at the end of the next step, in vertex order (host,
+ * n_prescribed*3).  They are applied to xhat^[0] of every later step until
+ * replaced. */
+int bf_set_obstacle_targets(bf_scene *scene, const double *targets);
+
+/* Active set C = {(i, lambda_i, gamma_i)} (Alg. 1-3).  get: writes up to
+ * cap pairs (keys host cap*5, lam/gam host cap) and the count to *n.
+ * set: replaces C (BF_E_NOT_FOUND if a key names no surface pair). */
+int bf_get_active_set(bf_scene *scene, int32_t cap, int32_t *n, int32_t *keys, double *lam,
+                      double *gam);
+int bf_set_active_set(bf_scene *scene, int32_t n, const int32_t *keys, const double *lam,
+                      const double *gam);
+
+/* Penalty stiffness mu and contact offset delta of the AL energy (section
+ * 4.2, section 5.2).  bf_step recomputes mu at the start of each step. */
+int bf_get_mu(bf_scene *scene, double *mu, double *delta);
+int bf_set_mu(bf_scene *scene, double mu, double delta);
+
+/* Sizes: n_surface_verts, n_surface_tris, n_surface_edges, nnz 3x3 blocks
+ * of the upper block-sparse pattern, n_prescribed (host int32[5]). */
+int bf_scene_info(bf_scene *scene, int32_t *info);
+
+const char *bf_status_str(int status);
+
+/* ---- teacher-forced entry points (same state as a step uses) ----------- */
+/* All positions below are device buffers of n_verts*3 FP64. */
+
+/* x~ = x^t + h v^t + h^2 g from the resident state (Alg. 1 line 1). */
+int bf_xtilde(bf_scene *scene, double *xtilde);
+
+/* Section 5.2: mu = c_mu * max_i (grad^2 E)_ii over free DoFs at xhat,
+ * from the PSD-projected elastic Hessian plus mass; stores and returns it. */
+int bf_mu_init(bf_scene *scene, const double *xtilde, const double *xhat, double *mu);
+
+/* Alg. 2 lines 2-4: d_i(x) and grad d_i(x) for every pair of C at xlin.
+ * dist (device, |C|) and grad (device, |C|*12, vertex order of the pair:
+ * PT point, t0, t1, t2 / EE a0, a1, b0, b1 of the internal primitive) may
+ * be NULL. */
+int bf_linearize(bf_scene *scene, const double *xlin, double *dist, double *grad);
+
+/* Alg. 2 lines 6-12 at xhat (after bf_linearize): gradient G (device,
+ * n_verts*3) of the AL energy with Dirichlet rows zeroed, and the
+ * assembled H kept in the scene (elastic PSD blocks + mass in upper BSR,
+ * contacts as mu gamma_i grad d_i grad d_i^T).  *energy (host, may be
+ * NULL) receives E(xhat). */
+int bf_assemble(bf_scene *scene, const double *xtilde, const double *xlin, const double *xhat,
+                double *grad, double *energy);
+
+/* y = H x with the H of the last bf_assemble (device n_verts*3 each);
+ * prescribed rows/columns are eliminated (identity on the diagonal). */
+int bf_hess_apply(bf_scene *scene, const double *x, double *y);
+
+/* Copies the upper block-sparse H (host): row_ptr (n_verts+1), col (nnzb),
+ * val (nnzb*9, row-major 3x3 blocks).  Any pointer may be NULL. */
+int bf_get_bsr(bf_scene *scene, int32_t *row_ptr, int32_t *col, double *val);
+
+/* Block-Jacobi PCG on the last assembled H (section 5.1): x (device) = the
+ * solution of H x = b (device) to ||r|| <= tol ||b||, at most maxit
+ * iterations; *iters (host) receives the count.  BF_E_CG_MAXIT if capped. */
+int bf_pcg(bf_scene *scene, const double *b, double *x, double tol, int32_t maxit, int32_t *iters);
+
+/* AL energy L (Eq. total-energy) at xhat with the slacks of the last
+ * bf_assemble held fixed (*L host). */
+int bf_energy(bf_scene *scene, const double *xtilde, const double *xlin, const double *xhat,
+              double *L);
+
+/* Alg. 2 SolveSubproblem: xhat (device, in/out) from xhat, updating the
+ * multipliers and decay factors of C.  newton/cg (host, may be NULL). */
+int bf_solve_subproblem(bf_scene *scene, const double *xtilde, const double *xlin, double *xhat,
+                        int32_t *newton, int32_t *cg);
+
+/* CCD hits (broad phase + ACCD, section 5.1) along x0 -> x1 over all
+ * admissible PT/EE pairs: up to cap keys (host cap*5) and TOIs (host cap);
+ * *n receives the total count. */
+int bf_ccd_hits(bf_scene *scene, const double *x0, const double *x1, int32_t cap, int32_t *n,
+                int32_t *keys, double *toi);
+
+/* Alg. 3 UpdateActiveSet(x, xhat, C); *n_active (host, may be NULL). */
+int bf_update_active_set(bf_scene *scene, const double *x, const double *xhat, int32_t *n_active);
+
+/* MaxStepSize: alpha = min(1, min_i TOI_i) along x0 -> x1 (*alpha host). */
+int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double *alpha);
+
+/* Narrow phase only: additive CCD on n explicit pairs of one type (0 = PT,
+ * 1 = EE); x0, x1 (device, n*12: the 4 vertices of each pair), toi
+ * (device, n; +inf = no hit within [0, 1]).  s: conservative rescaling.
+ * stream: cudaStream_t or NULL. */
+int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double s, double *toi,
+            void *stream);
+
+/* Per-kernel CUDA-event timing of the hot kernels during bf_step (off by
+ * default).  bf_get_timers fills, per kernel id 0..n-1, launches and total
+ * milliseconds (host int64 launches[n], double ms[n]); names[n] points to
+ * static strings.  Returns the number of timed kernels. */
+int bf_enable_timers(bf_scene *scene, int32_t on);
+/* Number of this library's own kernel launches issued for the scene since
+ * creation (sorts and scans done by CUB are not counted); *n host. */
+int bf_get_launch_count(bf_scene *scene, int64_t *n);
+int bf_get_timers(bf_scene *scene, int32_t cap, int64_t *launches, double *ms, const char **names);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -276,6 +276,13 @@ class Oracle:
         E = lib().or_assemble(C.c_void_p(self.h), _p(_f64(xtilde)), _p(_f64(xlin)), _p(_f64(xhat)), _p(g))
         return E, g
 
+    def slacks(self):
+        n = lib().or_active_count(C.c_void_p(self.h))
+        s = np.zeros(n)
+        if n:
+            lib().or_slacks(C.c_void_p(self.h), _p(s))
+        return s
+
     def hess_apply(self, v):
         o = np.zeros((self.nv, 3))
         lib().or_hess_apply(C.c_void_p(self.h), _p(_f64(v)), _p(o))

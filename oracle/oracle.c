@@ -918,6 +918,9 @@ double or_assemble(or_scene *S, const double *xtilde, const double *xlin, const 
     return E;
 }
 
+/* slack values s_i of the last or_assemble */
+void or_slacks(const or_scene *S, double *s) { memcpy(s, S->cs, S->nc * sizeof(double)); }
+
 /* Per-vertex diagonal 3x3 blocks of the full H (elastic + mass + the
  * contact terms mu gamma_i g_ia g_ia^T), before Dirichlet elimination. */
 static double *diag_blocks(const or_scene *S)

@@ -76,6 +76,7 @@ double or_mu_init(or_scene *S, const double *xhat, const double *xtilde);
 void or_linearize(or_scene *S, const double *xlin, double *d, double *g);
 double or_assemble(or_scene *S, const double *xtilde, const double *xlin, const double *xhat,
                    double *grad);
+void or_slacks(const or_scene *S, double *s);
 void or_hess_apply(const or_scene *S, const double *in, double *out);
 void or_hess_dense(const or_scene *S, double *out);
 int32_t or_pcg(const or_scene *S, const double *b, double *x, double tol, int32_t maxit);

@@ -1,0 +1,1030 @@
+// C ABI (include/bf.h) and the host-side drivers of Alg. 1 (time step) and
+// Alg. 2 (SolveSubproblem).  Every arithmetic step runs in the kernels of
+// bf_elastic.cu, bf_contact.cu, bf_linalg.cu and bf_ccd.cu; this file owns
+// the scene set-up (lumped mass, Dm^-1, surface, block pattern), memory,
+// control flow and the scalar decisions (line-search acceptance, alpha,
+// beta), which it reads back from the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+#include <vector>
+
+#include "bf.h"
+#include "bf_internal.cuh"
+
+struct bf_scene {
+    bf::Scene s;
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+};
+
+namespace bf {
+
+void launch_linearize_out(Scene &S, const double *xlin, double *dout, double *gout);
+
+static bf_scene *owner_of(Scene &S) { return reinterpret_cast<bf_scene *>(&S); }
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+void *dev_alloc(Scene &S, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (S.has_alloc) p = S.alloc.alloc(bytes, S.alloc.ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) S.owned.push_back(p);
+    return p;
+}
+
+void dev_free(Scene &S, void *p)
+{
+    if (!p) return;
+    auto it = std::find(S.owned.begin(), S.owned.end(), p);
+    if (it != S.owned.end()) S.owned.erase(it);
+    if (S.has_alloc) S.alloc.free(p, S.alloc.ctx);
+    else cudaFree(p);
+}
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_E_CUDA; }
+
+int sync_flags(Scene &S)
+{
+    cudaMemcpyAsync(S.h_scal, S.dscal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(S.h_flag, S.dflag, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, S.stream);
+    cudaError_t e = cudaStreamSynchronize(S.stream);
+    if (e != cudaSuccess) return BF_E_CUDA;
+    return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// timers
+// ---------------------------------------------------------------------------
+static const char *kTimerNames[T_N] = {"elastic_grad_hess", "spmv_bsr_contact", "pcg_update", "pcg_direction",
+                                       "contact_assemble", "energy", "ccd_narrow_accd", "lbvh_build"};
+
+ScopedTimer::ScopedTimer(Scene &s, int tid) : S(&s), id(tid)
+{
+    if (!S->timers_on) return;
+    auto take = [&]() {
+        cudaEvent_t e;
+        if (!S->ev_pool.empty()) {
+            e = S->ev_pool.back();
+            S->ev_pool.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    };
+    a = take();
+    b = take();
+    cudaEventRecord(a, S->stream);
+}
+
+ScopedTimer::~ScopedTimer()
+{
+    if (!a) return;
+    cudaEventRecord(b, S->stream);
+    owner_of(*S)->pending.emplace_back(id, a, b);
+}
+
+void flush_timers(Scene &S)
+{
+    auto &P = owner_of(S)->pending;
+    for (auto &t : P) {
+        float ms = 0.f;
+        cudaEventSynchronize(std::get<2>(t));
+        cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t));
+        S.t_launch[std::get<0>(t)] += 1;
+        S.t_ms[std::get<0>(t)] += ms;
+        S.ev_pool.push_back(std::get<1>(t));
+        S.ev_pool.push_back(std::get<2>(t));
+    }
+    P.clear();
+}
+
+// ---------------------------------------------------------------------------
+// small kernels used by the drivers
+// ---------------------------------------------------------------------------
+__global__ void k_scale(int n, double *__restrict__ out, const double *__restrict__ in, double s)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = s * in[i];
+}
+
+__global__ void k_apply_targets(int nd, const int *__restrict__ ids, const double *__restrict__ tg,
+                                double *__restrict__ x)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nd) return;
+    const int v = ids[i];
+    x[3 * v] = tg[3 * i];
+    x[3 * v + 1] = tg[3 * i + 1];
+    x[3 * v + 2] = tg[3 * i + 2];
+}
+
+__global__ void k_set_double(double *p, double v) { *p = v; }
+
+// ---------------------------------------------------------------------------
+// active set storage
+// ---------------------------------------------------------------------------
+static int partials_reserve(Scene &S)
+{
+    const long long work = (long long)S.nnzb + S.nt + S.nv + S.ccap + 1024;
+    const int need = 2 * cdiv(work, kThreads) + 64;
+    if (need <= S.npartials) return BF_OK;
+    if (S.partials) dev_free(S, S.partials);
+    S.partials = (double *)dev_alloc(S, need * sizeof(double));
+    if (!S.partials) return BF_E_OOM;
+    S.npartials = need;
+    return BF_OK;
+}
+
+int active_reserve(Scene &S, int n)
+{
+    if (n <= S.ccap) return BF_OK;
+    const int cap = std::max(n + n / 2, std::max(2 * S.ccap, 1024));
+    auto grow = [&](auto *&p, size_t elem, size_t per, bool keep) -> bool {
+        void *q = dev_alloc(S, (size_t)cap * per * elem);
+        if (!q) return false;
+        if (keep && p && S.nc)
+            cudaMemcpyAsync(q, p, (size_t)S.nc * per * elem, cudaMemcpyDeviceToDevice, S.stream);
+        if (p) {
+            cudaStreamSynchronize(S.stream);
+            dev_free(S, p);
+        }
+        p = reinterpret_cast<std::remove_reference_t<decltype(p)>>(q);
+        return true;
+    };
+    bool ok = grow(S.ctype, sizeof(int), 1, true) && grow(S.ca, sizeof(int), 1, true) &&
+              grow(S.cb, sizeof(int), 1, true) && grow(S.cv, sizeof(int4), 1, true) &&
+              grow(S.clam, sizeof(double), 1, true) && grow(S.cgam, sizeof(double), 1, true) &&
+              grow(S.cd, sizeof(double), 1, true) && grow(S.cg, sizeof(double), 12, true) &&
+              grow(S.cs, sizeof(double), 1, true) && grow(S.cw, sizeof(double), 1, true) &&
+              grow(S.cmask, 1, 1, true) && grow(S.ckey, sizeof(unsigned long long), 1, false) &&
+              grow(S.ckey_sorted, sizeof(unsigned long long), 1, false);
+    if (!ok) return BF_E_OOM;
+    S.ccap = cap;
+    return partials_reserve(S);
+}
+
+// ---------------------------------------------------------------------------
+// Newton step pieces
+// ---------------------------------------------------------------------------
+static void assemble(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
+{
+    cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
+    launch_vertex_init(S, xtilde, xhat);
+    launch_elastic(S, xhat);
+    launch_contact_assemble(S, xlin, xhat);
+    launch_pinv(S);
+}
+
+static double mu_init(Scene &S, const double *xtilde, const double *xhat)
+{
+    launch_vertex_init(S, xtilde, xhat);
+    launch_elastic(S, xhat);
+    const double mx = run_mu_max_diag(S);
+    S.mu = S.prm.c_mu * mx;
+    return S.mu;
+}
+
+struct SolveStats {
+    int newton = 0, cg = 0, ls_fail = 0, cg_maxit = 0, newton_cap = 0;
+};
+
+// Alg. 2 SolveSubproblem (xhat in/out).  Line search: r = 1, 1/2, ...,
+// 2^-max_ls with L(xhat + r p) <= L(xhat) + 1e-12 |L(xhat)| and the slacks
+// of the current Newton iteration held fixed.
+static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, double *xhat, SolveStats &ss)
+{
+    const int n = 3 * S.nv;
+    launch_linearize(S, xlin);
+    while (true) {
+        if (ss.newton >= S.prm.max_newton) {
+            ss.newton_cap++;
+            break;
+        }
+        assemble(S, xtilde, xlin, xhat);
+        k_scale<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, -1.0); ++S.n_launch;
+        int it = 0;
+        int st = run_pcg(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it);
+        ss.cg += it;
+        if (st == BF_E_CG_MAXIT) ss.cg_maxit++;
+        else if (st) return st;
+        const double L0 = run_energy(S, xtilde, xlin, xhat);
+        if (!std::isfinite(L0)) return BF_E_NONFINITE;
+        double r = 1.0;
+        bool ok = false;
+        for (int j = 0; j <= S.prm.max_ls; ++j) {
+            launch_axpy_to(S, S.xtmp, xhat, r, S.pdir, n);
+            const double L1 = run_energy(S, xtilde, xlin, S.xtmp);
+            if (std::isfinite(L1) && L1 <= L0 + 1e-12 * std::fabs(L0)) {
+                ok = true;
+                break;
+            }
+            r *= 0.5;
+        }
+        ss.newton++;
+        if (!ok) {
+            ss.ls_fail++;
+            break;
+        }
+        cudaMemcpyAsync(xhat, S.xtmp, n * sizeof(double), cudaMemcpyDeviceToDevice, S.stream);
+        if (r == 1.0) break;
+    }
+    launch_multiplier_update(S, xlin, xhat);
+    return check_cuda(cudaGetLastError());
+}
+
+// Alg. 1: one time step.
+static int step_once(Scene &S, bf_step_stats *out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = 3 * S.nv;
+    const size_t nb = n * sizeof(double);
+    bf_step_stats st{};
+    st.min_alpha = 1.0;
+    cudaMemcpyAsync(S.xt, S.x, nb, cudaMemcpyDeviceToDevice, S.stream);
+    launch_xtilde(S, S.xtilde);
+    cudaMemcpyAsync(S.xk, S.x, nb, cudaMemcpyDeviceToDevice, S.stream);
+    cudaMemcpyAsync(S.xh, S.x, nb, cudaMemcpyDeviceToDevice, S.stream);
+    if (S.has_targets && S.ndir)
+        {
+            k_apply_targets<<<cdiv(S.ndir, kThreads), kThreads, 0, S.stream>>>(S.ndir, S.dir_ids, S.targets, S.xh); ++S.n_launch;
+        }
+    S.delta = S.prm.delta;
+    mu_init(S, S.xtilde, S.xh);
+    if (!(S.mu > 0.0) || !std::isfinite(S.mu)) return BF_E_NONFINITE;
+    double beta = 1.0, asum = 0.0;
+    int k = 0, stall = 0, status = BF_OK;
+    SolveStats ss;
+    while (beta > S.prm.eps) {
+        if (k >= S.prm.max_outer) {
+            status = BF_E_OUTER_MAXIT;
+            break;
+        }
+        cudaMemcpyAsync(S.xh_prev, S.xh, nb, cudaMemcpyDeviceToDevice, S.stream);
+        int rc = solve_subproblem(S, S.xtilde, S.xk, S.xh, ss);
+        if (rc) return rc;
+        rc = run_update_active_set(S, S.xk, S.xh_prev);
+        if (rc) return rc;
+        double alpha = 1.0;
+        rc = run_ccd(S, S.xk, S.xh, false, &alpha, nullptr);
+        if (rc) return rc;
+        launch_blend(S, S.xk, S.xh, alpha, n);
+        if (k + 1 >= S.prm.k_min) beta = (1.0 - alpha) * beta;
+        ++k;
+        asum += alpha;
+        st.min_alpha = std::min(st.min_alpha, alpha);
+        if (alpha < 1e-4) {
+            if (++stall >= 50) {  // section 5.2 stall rule
+                S.mu *= 2.0;
+                S.delta *= 0.5;
+                stall = 0;
+                st.stalls++;
+            }
+        } else {
+            stall = 0;
+        }
+    }
+    launch_velocity(S);
+    int rc = sync_flags(S);
+    if (rc) return rc;
+    if (S.timers_on) flush_timers(S);
+    st.outer_iters = k;
+    st.newton_iters = ss.newton;
+    st.cg_iters = ss.cg;
+    st.n_contacts = S.nc;
+    st.ls_fail = ss.ls_fail;
+    st.cg_maxit = ss.cg_maxit;
+    st.mean_alpha = k ? asum / k : 0.0;
+    st.mu = S.mu;
+    st.beta = beta;
+    st.delta = S.delta;
+    st.status = status;
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (out) *out = st;
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// scene creation
+// ---------------------------------------------------------------------------
+static long long tri_key_sorted(int a, int b, int c)
+{
+    int t[3] = {a, b, c};
+    std::sort(t, t + 3);
+    return ((long long)t[0] << 42) | ((long long)t[1] << 21) | (long long)t[2];
+}
+
+static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
+{
+    const int nv = m->n_verts, nt = m->n_tets, nm = m->n_mats, nx = m->n_obst_tris;
+    if (nv <= 0 || nt < 0 || nx < 0 || (nt > 0 && nm <= 0) || !m->rest_pos || !m->init_pos) return BF_E_ARG;
+    if ((nt > 0 && (!m->tets || !m->tet_mat || !m->mats)) || (nx > 0 && !m->obst_tris)) return BF_E_ARG;
+    if (nv >= (1 << 30) || nt >= (1 << 30)) return BF_E_ARG;
+    if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
+        prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
+        prm->s_ccd >= 1)
+        return BF_E_ARG;
+    S.nv = nv;
+    S.nt = nt;
+    S.nm = nm;
+    S.nx = nx;
+    S.prm = *prm;
+    S.delta = prm->delta;
+    S.h_dir.assign(nv, 0);
+    if (m->dirichlet)
+        for (int v = 0; v < nv; ++v) S.h_dir[v] = m->dirichlet[v] ? 1 : 0;
+    for (int v = 0; v < nv; ++v)
+        if (S.h_dir[v]) S.h_dir_ids.push_back(v);
+    S.ndir = (int)S.h_dir_ids.size();
+    // per-tet rest data and lumped mass
+    std::vector<double> B(9 * (size_t)nt), vol(nt), emu(nt), elam(nt), mass(nv, 0.0);
+    for (int e = 0; e < nt; ++e) {
+        const int *t = m->tets + 4 * e;
+        for (int k = 0; k < 4; ++k)
+            if (t[k] < 0 || t[k] >= nv) return BF_E_ARG;
+        const int mi = m->tet_mat[e];
+        if (mi < 0 || mi >= nm) return BF_E_ARG;
+        double D[9];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) D[3 * r + k] = m->rest_pos[3 * t[k + 1] + r] - m->rest_pos[3 * t[0] + r];
+        const double det = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                           D[2] * (D[3] * D[7] - D[4] * D[6]);
+        if (!(det > 0.0)) return BF_E_ARG;
+        double *o = B.data() + 9 * (size_t)e;
+        o[0] = (D[4] * D[8] - D[5] * D[7]) / det;
+        o[1] = (D[2] * D[7] - D[1] * D[8]) / det;
+        o[2] = (D[1] * D[5] - D[2] * D[4]) / det;
+        o[3] = (D[5] * D[6] - D[3] * D[8]) / det;
+        o[4] = (D[0] * D[8] - D[2] * D[6]) / det;
+        o[5] = (D[2] * D[3] - D[0] * D[5]) / det;
+        o[6] = (D[3] * D[7] - D[4] * D[6]) / det;
+        o[7] = (D[1] * D[6] - D[0] * D[7]) / det;
+        o[8] = (D[0] * D[4] - D[1] * D[3]) / det;
+        vol[e] = det / 6.0;
+        const double E = m->mats[3 * mi], nu = m->mats[3 * mi + 1], rho = m->mats[3 * mi + 2];
+        if (!(E > 0) || !(nu > -1 && nu < 0.5) || !(rho > 0)) return BF_E_ARG;
+        emu[e] = E / (2.0 * (1.0 + nu));
+        elam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + emu[e];
+        for (int k = 0; k < 4; ++k) mass[t[k]] += rho * vol[e] / 4.0;
+    }
+    for (int v = 0; v < nv; ++v) {
+        if (S.h_dir[v]) mass[v] = 1.0;
+        else if (!(mass[v] > 0.0)) return BF_E_ARG;  // a free vertex must belong to a tet
+    }
+    // surface: tet faces used exactly once (outward order (1,2,3), (0,3,2),
+    // (0,1,3), (0,2,1) of a positively oriented tet), then obstacle triangles
+    static const int fl[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+    std::vector<std::pair<long long, int>> faces(4 * (size_t)nt);
+    for (int e = 0; e < nt; ++e)
+        for (int f = 0; f < 4; ++f) {
+            const int *t = m->tets + 4 * e;
+            faces[4 * e + f] = {tri_key_sorted(t[fl[f][0]], t[fl[f][1]], t[fl[f][2]]), 4 * e + f};
+        }
+    std::sort(faces.begin(), faces.end());
+    for (size_t i = 0; i < faces.size();) {
+        size_t j = i;
+        while (j < faces.size() && faces[j].first == faces[i].first) ++j;
+        if (j - i == 1) {
+            const int e = faces[i].second / 4, f = faces[i].second % 4;
+            for (int k = 0; k < 3; ++k) S.h_st.push_back(m->tets[4 * e + fl[f][k]]);
+        }
+        i = j;
+    }
+    for (int i = 0; i < nx; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const int v = m->obst_tris[3 * i + k];
+            if (v < 0 || v >= nv) return BF_E_ARG;
+            S.h_st.push_back(v);
+        }
+    S.nst = (int)(S.h_st.size() / 3);
+    std::vector<long long> ek;
+    for (int i = 0; i < S.nst; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const int a = S.h_st[3 * i + k], b = S.h_st[3 * i + (k + 1) % 3];
+            ek.push_back(((long long)std::min(a, b) << 32) | (long long)std::max(a, b));
+        }
+    std::sort(ek.begin(), ek.end());
+    ek.erase(std::unique(ek.begin(), ek.end()), ek.end());
+    for (long long k : ek) {
+        S.h_se.push_back((int)(k >> 32));
+        S.h_se.push_back((int)(k & 0xffffffff));
+    }
+    S.nse = (int)ek.size();
+    {
+        std::vector<char> on(nv, 0);
+        for (int v : S.h_st) on[v] = 1;
+        for (int v = 0; v < nv; ++v)
+            if (on[v]) S.h_sv.push_back(v);
+        S.nsv = (int)S.h_sv.size();
+    }
+    {
+        std::vector<std::pair<long long, int>> tk(S.nst);
+        for (int i = 0; i < S.nst; ++i) tk[i] = {tri_key_sorted(S.h_st[3 * i], S.h_st[3 * i + 1], S.h_st[3 * i + 2]), i};
+        std::sort(tk.begin(), tk.end());
+        for (auto &p : tk) {
+            S.h_tri_key_sorted.push_back(p.first);
+            S.h_tri_key_idx.push_back(p.second);
+        }
+    }
+    // upper block pattern: diagonal of every vertex + (a, b), a < b, sharing a tet
+    std::vector<long long> pk;
+    pk.reserve((size_t)nv + 10 * (size_t)nt);
+    for (int v = 0; v < nv; ++v) pk.push_back(((long long)v << 32) | v);
+    for (int e = 0; e < nt; ++e) {
+        const int *t = m->tets + 4 * e;
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j) {
+                const int a = std::min(t[i], t[j]), b = std::max(t[i], t[j]);
+                pk.push_back(((long long)a << 32) | b);
+            }
+    }
+    std::sort(pk.begin(), pk.end());
+    pk.erase(std::unique(pk.begin(), pk.end()), pk.end());
+    S.nnzb = (int)pk.size();
+    S.h_rowptr.assign(nv + 1, 0);
+    S.h_col.resize(S.nnzb);
+    std::vector<int> rowid(S.nnzb), diagblk(nv);
+    for (int k = 0; k < S.nnzb; ++k) {
+        const int r = (int)(pk[k] >> 32), c = (int)(pk[k] & 0xffffffff);
+        S.h_col[k] = c;
+        rowid[k] = r;
+        S.h_rowptr[r + 1]++;
+        if (r == c) diagblk[r] = k;
+    }
+    for (int v = 0; v < nv; ++v) S.h_rowptr[v + 1] += S.h_rowptr[v];
+    auto find_blk = [&](int r, int c) {
+        auto b = S.h_col.begin() + S.h_rowptr[r], e = S.h_col.begin() + S.h_rowptr[r + 1];
+        return (int)(std::lower_bound(b, e, c) - S.h_col.begin());
+    };
+    std::vector<int> tblk(10 * (size_t)nt);
+    for (int e = 0; e < nt; ++e) {
+        const int *t = m->tets + 4 * e;
+        int p = 0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = i; j < 4; ++j, ++p) {
+                const int a = t[i], b = t[j];
+                tblk[10 * (size_t)e + p] = a <= b ? find_blk(a, b) : (find_blk(b, a) | (int)0x80000000u);
+            }
+    }
+    // ---- device buffers ----
+    const size_t n3 = 3 * (size_t)nv;
+    auto D = [&](size_t bytes) { return dev_alloc(S, bytes); };
+#define BF_ALLOC(ptr, type, count)                         \
+    do {                                                   \
+        ptr = (type *)D((size_t)(count) * sizeof(type));   \
+        if (!ptr) return BF_E_OOM;                         \
+    } while (0)
+    BF_ALLOC(S.x, double, n3);
+    BF_ALLOC(S.v, double, n3);
+    BF_ALLOC(S.xt, double, n3);
+    BF_ALLOC(S.xtilde, double, n3);
+    BF_ALLOC(S.xk, double, n3);
+    BF_ALLOC(S.xh, double, n3);
+    BF_ALLOC(S.xh_prev, double, n3);
+    BF_ALLOC(S.xtmp, double, n3);
+    BF_ALLOC(S.targets, double, 3 * (size_t)std::max(S.ndir, 1));
+    BF_ALLOC(S.dir, uint8_t, nv);
+    BF_ALLOC(S.mass, double, nv);
+    BF_ALLOC(S.tets, int4, std::max(nt, 1));
+    BF_ALLOC(S.B, double, 9 * (size_t)std::max(nt, 1));
+    BF_ALLOC(S.vol, double, std::max(nt, 1));
+    BF_ALLOC(S.emu, double, std::max(nt, 1));
+    BF_ALLOC(S.elam, double, std::max(nt, 1));
+    BF_ALLOC(S.tblk, int, 10 * (size_t)std::max(nt, 1));
+    BF_ALLOC(S.rowptr, int, nv + 1);
+    BF_ALLOC(S.col, int, S.nnzb);
+    BF_ALLOC(S.rowid, int, S.nnzb);
+    BF_ALLOC(S.diagblk, int, nv);
+    if (S.prm.precision == BF_PREC_MIXED) {
+        BF_ALLOC(S.valf, float, 9 * (size_t)S.nnzb);
+        BF_ALLOC(S.pinvf, float, 9 * (size_t)nv);
+        BF_ALLOC(S.cg_pf, float, n3);
+        BF_ALLOC(S.cg_qf, float, n3);
+        BF_ALLOC(S.cg_zf, float, n3);
+    } else {
+        BF_ALLOC(S.val, double, 9 * (size_t)S.nnzb);
+        BF_ALLOC(S.pinv, double, 9 * (size_t)nv);
+    }
+    BF_ALLOC(S.cdiag, double, 9 * (size_t)nv);
+    BF_ALLOC(S.grad, double, n3);
+    BF_ALLOC(S.cg_x, double, n3);
+    BF_ALLOC(S.cg_r, double, n3);
+    BF_ALLOC(S.cg_b, double, n3);
+    BF_ALLOC(S.cg_p, double, n3);
+    BF_ALLOC(S.cg_q, double, n3);
+    BF_ALLOC(S.cg_z, double, n3);
+    BF_ALLOC(S.pdir, double, n3);
+    BF_ALLOC(S.counter, unsigned, 4);
+    BF_ALLOC(S.dscal, double, S_NSCAL);
+    BF_ALLOC(S.dflag, int, F_NFLAG);
+    BF_ALLOC(S.sv, int, std::max(S.nsv, 1));
+    BF_ALLOC(S.st, int, 3 * (size_t)std::max(S.nst, 1));
+    BF_ALLOC(S.se, int, 2 * (size_t)std::max(S.nse, 1));
+    BF_ALLOC(S.tv, unsigned long long, nv);
+    BF_ALLOC(S.bounds, double, 8);
+    BF_ALLOC(S.dir_ids, int, std::max(S.ndir, 1));
+#undef BF_ALLOC
+    if (cudaMallocHost(&S.h_scal, S_NSCAL * sizeof(double)) != cudaSuccess) return BF_E_OOM;
+    if (cudaMallocHost(&S.h_flag, F_NFLAG * sizeof(int)) != cudaSuccess) return BF_E_OOM;
+    cudaStream_t s = S.stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    up(S.x, m->init_pos, n3 * 8);
+    if (m->init_vel) up(S.v, m->init_vel, n3 * 8);
+    else cudaMemsetAsync(S.v, 0, n3 * 8, s);
+    up(S.dir, S.h_dir.data(), nv);
+    up(S.mass, mass.data(), nv * 8);
+    up(S.tets, m->tets, (size_t)nt * 16);
+    up(S.B, B.data(), B.size() * 8);
+    up(S.vol, vol.data(), nt * 8);
+    up(S.emu, emu.data(), nt * 8);
+    up(S.elam, elam.data(), nt * 8);
+    up(S.tblk, tblk.data(), tblk.size() * 4);
+    up(S.rowptr, S.h_rowptr.data(), (nv + 1) * 4);
+    up(S.col, S.h_col.data(), S.nnzb * 4);
+    up(S.rowid, rowid.data(), S.nnzb * 4);
+    up(S.diagblk, diagblk.data(), nv * 4);
+    up(S.sv, S.h_sv.data(), S.nsv * 4);
+    up(S.st, S.h_st.data(), S.h_st.size() * 4);
+    up(S.se, S.h_se.data(), S.h_se.size() * 4);
+    up(S.dir_ids, S.h_dir_ids.data(), S.ndir * 4);
+    cudaMemsetAsync(S.counter, 0, 16, s);
+    cudaMemsetAsync(S.dscal, 0, S_NSCAL * 8, s);
+    cudaMemsetAsync(S.dflag, 0, F_NFLAG * 4, s);
+    int st = active_reserve(S, 1024);
+    if (st) return st;
+    st = ccd_reserve(S, 1 << 16, 1 << 16, 1 << 14);
+    if (st) return st;
+    st = partials_reserve(S);
+    if (st) return st;
+    // keep host copies of everything the hot path needs for the duration of
+    // the async uploads
+    st = check_cuda(cudaStreamSynchronize(s));
+    return st;
+}
+
+static void destroy(Scene &S)
+{
+    if (S.stream) cudaStreamSynchronize(S.stream);
+    std::vector<void *> o = S.owned;
+    for (void *p : o) dev_free(S, p);
+    if (S.h_scal) cudaFreeHost(S.h_scal);
+    if (S.h_flag) cudaFreeHost(S.h_flag);
+    for (cudaEvent_t e : S.ev_pool) cudaEventDestroy(e);
+}
+
+// canonical key (bf.h) of an internal pair
+static void canon(const Scene &S, int type, int a, int b, int32_t *k)
+{
+    k[0] = type;
+    if (type == PT) {
+        int t[3] = {S.h_st[3 * b], S.h_st[3 * b + 1], S.h_st[3 * b + 2]};
+        std::sort(t, t + 3);
+        k[1] = a;
+        k[2] = t[0];
+        k[3] = t[1];
+        k[4] = t[2];
+    } else {
+        k[1] = S.h_se[2 * a];
+        k[2] = S.h_se[2 * a + 1];
+        k[3] = S.h_se[2 * b];
+        k[4] = S.h_se[2 * b + 1];
+    }
+}
+
+static int find_edge(const Scene &S, int a, int b)
+{
+    int lo = 0, hi = S.nse - 1;
+    while (lo <= hi) {
+        const int m = (lo + hi) / 2;
+        const int ma = S.h_se[2 * m], mb = S.h_se[2 * m + 1];
+        if (ma == a && mb == b) return m;
+        if (ma < a || (ma == a && mb < b)) lo = m + 1;
+        else hi = m - 1;
+    }
+    return -1;
+}
+
+static int4 host_pair_verts(const Scene &S, int type, int a, int b)
+{
+    if (type == PT) return make_int4(a, S.h_st[3 * b], S.h_st[3 * b + 1], S.h_st[3 * b + 2]);
+    return make_int4(S.h_se[2 * a], S.h_se[2 * a + 1], S.h_se[2 * b], S.h_se[2 * b + 1]);
+}
+
+}  // namespace bf
+
+using namespace bf;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define SCENE_OR_ARG(p)             \
+    if (!(p)) return BF_E_ARG;      \
+    Scene &S = (p)->s
+
+extern "C" {
+
+int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_allocator *alloc, void *stream,
+                    bf_scene **out)
+{
+    if (!mesh || !params || !out) return BF_E_ARG;
+    *out = nullptr;
+    bf_scene *h = new bf_scene();
+    Scene &S = h->s;
+    S.stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        S.alloc = *alloc;
+        S.has_alloc = true;
+    }
+    const int st = create(S, mesh, params);
+    if (st) {
+        destroy(S);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return BF_OK;
+}
+
+int bf_scene_destroy(bf_scene *scene)
+{
+    if (!scene) return BF_E_ARG;
+    destroy(scene->s);
+    delete scene;
+    return BF_OK;
+}
+
+int bf_set_stream(bf_scene *scene, void *stream)
+{
+    SCENE_OR_ARG(scene);
+    cudaStreamSynchronize(S.stream);
+    S.stream = (cudaStream_t)stream;
+    return BF_OK;
+}
+
+int bf_step(bf_scene *scene, int32_t n_steps, bf_step_stats *stats)
+{
+    SCENE_OR_ARG(scene);
+    if (n_steps < 0) return BF_E_ARG;
+    for (int i = 0; i < n_steps; ++i) {
+        bf_step_stats st{};
+        const int rc = step_once(S, &st);
+        if (stats) stats[i] = st;
+        if (rc) return rc;
+    }
+    return BF_OK;
+}
+
+int bf_step_host(bf_scene *scene, const double *x_in, const double *v_in, double *x_out, double *v_out,
+                 bf_step_stats *stats)
+{
+    SCENE_OR_ARG(scene);
+    const size_t nb = 3 * (size_t)S.nv * sizeof(double);
+    if (x_in) cudaMemcpyAsync(S.x, x_in, nb, cudaMemcpyHostToDevice, S.stream);
+    if (v_in) cudaMemcpyAsync(S.v, v_in, nb, cudaMemcpyHostToDevice, S.stream);
+    int rc = step_once(S, stats);
+    if (rc) return rc;
+    if (x_out) cudaMemcpyAsync(x_out, S.x, nb, cudaMemcpyDeviceToHost, S.stream);
+    if (v_out) cudaMemcpyAsync(v_out, S.v, nb, cudaMemcpyDeviceToHost, S.stream);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_get_state(bf_scene *scene, double *x, double *v)
+{
+    SCENE_OR_ARG(scene);
+    const size_t nb = 3 * (size_t)S.nv * sizeof(double);
+    if (x) cudaMemcpyAsync(x, S.x, nb, cudaMemcpyDeviceToHost, S.stream);
+    if (v) cudaMemcpyAsync(v, S.v, nb, cudaMemcpyDeviceToHost, S.stream);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_set_state(bf_scene *scene, const double *x, const double *v)
+{
+    SCENE_OR_ARG(scene);
+    const size_t nb = 3 * (size_t)S.nv * sizeof(double);
+    if (x) cudaMemcpyAsync(S.x, x, nb, cudaMemcpyHostToDevice, S.stream);
+    if (v) cudaMemcpyAsync(S.v, v, nb, cudaMemcpyHostToDevice, S.stream);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_set_obstacle_targets(bf_scene *scene, const double *targets)
+{
+    SCENE_OR_ARG(scene);
+    if (!targets) {
+        S.has_targets = 0;
+        return BF_OK;
+    }
+    if (S.ndir == 0) return BF_E_ARG;
+    cudaMemcpyAsync(S.targets, targets, 3 * (size_t)S.ndir * sizeof(double), cudaMemcpyHostToDevice, S.stream);
+    S.has_targets = 1;
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_get_active_set(bf_scene *scene, int32_t cap, int32_t *n, int32_t *keys, double *lam, double *gam)
+{
+    SCENE_OR_ARG(scene);
+    if (n) *n = S.nc;
+    const int m = std::min(cap, S.nc);
+    if (m <= 0) return BF_OK;
+    std::vector<int> t(m), a(m), b(m);
+    std::vector<double> l(m), g(m);
+    cudaMemcpyAsync(t.data(), S.ctype, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(a.data(), S.ca, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(b.data(), S.cb, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(l.data(), S.clam, m * 8, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(g.data(), S.cgam, m * 8, cudaMemcpyDeviceToHost, S.stream);
+    const int st = check_cuda(cudaStreamSynchronize(S.stream));
+    if (st) return st;
+    for (int i = 0; i < m; ++i) {
+        if (keys) canon(S, t[i], a[i], b[i], keys + 5 * i);
+        if (lam) lam[i] = l[i];
+        if (gam) gam[i] = g[i];
+    }
+    return BF_OK;
+}
+
+int bf_set_active_set(bf_scene *scene, int32_t n, const int32_t *keys, const double *lam, const double *gam)
+{
+    SCENE_OR_ARG(scene);
+    if (n < 0 || (n > 0 && (!keys || !lam || !gam))) return BF_E_ARG;
+    std::vector<int> t(n), a(n), b(n);
+    std::vector<int4> v(n);
+    for (int i = 0; i < n; ++i) {
+        const int32_t *k = keys + 5 * i;
+        if (k[0] == PT) {
+            const long long key = tri_key_sorted(k[2], k[3], k[4]);
+            auto it = std::lower_bound(S.h_tri_key_sorted.begin(), S.h_tri_key_sorted.end(), key);
+            if (it == S.h_tri_key_sorted.end() || *it != key) return BF_E_NOT_FOUND;
+            t[i] = PT;
+            a[i] = k[1];
+            b[i] = S.h_tri_key_idx[it - S.h_tri_key_sorted.begin()];
+            if (a[i] < 0 || a[i] >= S.nv) return BF_E_NOT_FOUND;
+        } else if (k[0] == EE) {
+            t[i] = EE;
+            a[i] = find_edge(S, k[1], k[2]);
+            b[i] = find_edge(S, k[3], k[4]);
+            if (a[i] < 0 || b[i] < 0) return BF_E_NOT_FOUND;
+            if (a[i] > b[i]) std::swap(a[i], b[i]);
+        } else {
+            return BF_E_ARG;
+        }
+        v[i] = host_pair_verts(S, t[i], a[i], b[i]);
+    }
+    S.nc = 0;
+    int st = active_reserve(S, std::max(n, 1));
+    if (st) return st;
+    if (n) {
+        cudaMemcpyAsync(S.ctype, t.data(), n * 4, cudaMemcpyHostToDevice, S.stream);
+        cudaMemcpyAsync(S.ca, a.data(), n * 4, cudaMemcpyHostToDevice, S.stream);
+        cudaMemcpyAsync(S.cb, b.data(), n * 4, cudaMemcpyHostToDevice, S.stream);
+        cudaMemcpyAsync(S.cv, v.data(), n * 16, cudaMemcpyHostToDevice, S.stream);
+        cudaMemcpyAsync(S.clam, lam, n * 8, cudaMemcpyHostToDevice, S.stream);
+        cudaMemcpyAsync(S.cgam, gam, n * 8, cudaMemcpyHostToDevice, S.stream);
+    }
+    S.nc = n;
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_get_mu(bf_scene *scene, double *mu, double *delta)
+{
+    SCENE_OR_ARG(scene);
+    if (mu) *mu = S.mu;
+    if (delta) *delta = S.delta;
+    return BF_OK;
+}
+
+int bf_set_mu(bf_scene *scene, double mu, double delta)
+{
+    SCENE_OR_ARG(scene);
+    if (!(mu > 0.0) || delta < 0.0) return BF_E_ARG;
+    S.mu = mu;
+    S.delta = delta;
+    return BF_OK;
+}
+
+int bf_scene_info(bf_scene *scene, int32_t *info)
+{
+    SCENE_OR_ARG(scene);
+    if (!info) return BF_E_ARG;
+    info[0] = S.nsv;
+    info[1] = S.nst;
+    info[2] = S.nse;
+    info[3] = S.nnzb;
+    info[4] = S.ndir;
+    return BF_OK;
+}
+
+const char *bf_status_str(int status)
+{
+    switch (status) {
+    case BF_OK: return "ok";
+    case BF_E_ARG: return "invalid argument";
+    case BF_E_OOM: return "device allocation failed";
+    case BF_E_CUDA: return "CUDA error";
+    case BF_E_CG_MAXIT: return "PCG reached max_cg";
+    case BF_E_NEWTON_MAXIT: return "Newton loop reached max_newton";
+    case BF_E_LS_FAIL: return "line search failed";
+    case BF_E_OUTER_MAXIT: return "time step reached max_outer";
+    case BF_E_NONFINITE: return "non-finite value";
+    case BF_E_CAPACITY: return "work buffer capacity exceeded";
+    case BF_E_NOT_FOUND: return "pair key not found";
+    default: return "unknown status";
+    }
+}
+
+int bf_xtilde(bf_scene *scene, double *xtilde)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde) return BF_E_ARG;
+    launch_xtilde(S, xtilde);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_mu_init(bf_scene *scene, const double *xtilde, const double *xhat, double *mu)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde || !xhat) return BF_E_ARG;
+    const double m = mu_init(S, xtilde, xhat);
+    if (mu) *mu = m;
+    return std::isfinite(m) && m > 0 ? BF_OK : BF_E_NONFINITE;
+}
+
+int bf_linearize(bf_scene *scene, const double *xlin, double *dist, double *grad)
+{
+    SCENE_OR_ARG(scene);
+    if (!xlin) return BF_E_ARG;
+    launch_linearize_out(S, xlin, dist, grad);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_assemble(bf_scene *scene, const double *xtilde, const double *xlin, const double *xhat, double *grad,
+                double *energy)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde || !xlin || !xhat) return BF_E_ARG;
+    if (!(S.mu > 0.0)) return BF_E_ARG;
+    assemble(S, xtilde, xlin, xhat);
+    if (grad) cudaMemcpyAsync(grad, S.grad, 3 * (size_t)S.nv * 8, cudaMemcpyDeviceToDevice, S.stream);
+    if (energy) {
+        *energy = run_energy(S, xtilde, xlin, xhat);
+    }
+    int st = sync_flags(S);
+    if (st) return st;
+    return (S.h_flag[F_ERR] & ERR_NONFINITE) ? BF_E_NONFINITE : BF_OK;
+}
+
+int bf_hess_apply(bf_scene *scene, const double *x, double *y)
+{
+    SCENE_OR_ARG(scene);
+    if (!x || !y) return BF_E_ARG;
+    launch_spmv(S, x, y, false, nullptr);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_get_bsr(bf_scene *scene, int32_t *row_ptr, int32_t *col, double *val)
+{
+    SCENE_OR_ARG(scene);
+    if (row_ptr) std::memcpy(row_ptr, S.h_rowptr.data(), (S.nv + 1) * 4);
+    if (col) std::memcpy(col, S.h_col.data(), (size_t)S.nnzb * 4);
+    if (val) {
+        std::vector<double> planes(9 * (size_t)S.nnzb);
+        if (S.prm.precision == BF_PREC_MIXED) {
+            std::vector<float> pf(9 * (size_t)S.nnzb);
+            cudaMemcpyAsync(pf.data(), S.valf, pf.size() * 4, cudaMemcpyDeviceToHost, S.stream);
+            cudaStreamSynchronize(S.stream);
+            for (size_t i = 0; i < pf.size(); ++i) planes[i] = pf[i];
+        } else {
+            cudaMemcpyAsync(planes.data(), S.val, planes.size() * 8, cudaMemcpyDeviceToHost, S.stream);
+        }
+        const int st = check_cuda(cudaStreamSynchronize(S.stream));
+        if (st) return st;
+        for (int k = 0; k < S.nnzb; ++k)
+            for (int e = 0; e < 9; ++e) val[9 * (size_t)k + e] = planes[(size_t)e * S.nnzb + k];
+    }
+    return BF_OK;
+}
+
+int bf_pcg(bf_scene *scene, const double *b, double *x, double tol, int32_t maxit, int32_t *iters)
+{
+    SCENE_OR_ARG(scene);
+    if (!b || !x || !(tol > 0) || maxit < 1) return BF_E_ARG;
+    int it = 0;
+    const int st = run_pcg(S, b, x, tol, maxit, &it);
+    if (iters) *iters = it;
+    return st;
+}
+
+int bf_energy(bf_scene *scene, const double *xtilde, const double *xlin, const double *xhat, double *L)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde || !xlin || !xhat || !L) return BF_E_ARG;
+    *L = run_energy(S, xtilde, xlin, xhat);
+    return std::isfinite(*L) ? BF_OK : BF_E_NONFINITE;
+}
+
+int bf_solve_subproblem(bf_scene *scene, const double *xtilde, const double *xlin, double *xhat, int32_t *newton,
+                        int32_t *cg)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde || !xlin || !xhat || !(S.mu > 0)) return BF_E_ARG;
+    SolveStats ss;
+    const int st = solve_subproblem(S, xtilde, xlin, xhat, ss);
+    if (newton) *newton = ss.newton;
+    if (cg) *cg = ss.cg;
+    if (st) return st;
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_ccd_hits(bf_scene *scene, const double *x0, const double *x1, int32_t cap, int32_t *n, int32_t *keys,
+                double *toi)
+{
+    SCENE_OR_ARG(scene);
+    if (!x0 || !x1) return BF_E_ARG;
+    int nh = 0;
+    int st = run_ccd(S, x0, x1, true, nullptr, &nh);
+    if (st) return st;
+    if (n) *n = nh;
+    const int m = std::min(cap, nh);
+    if (m <= 0) return BF_OK;
+    std::vector<int> t(m), a(m), b(m);
+    std::vector<double> tt(m);
+    cudaMemcpyAsync(t.data(), S.hit_type, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(a.data(), S.hit_a, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(b.data(), S.hit_b, m * 4, cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(tt.data(), S.hit_toi, m * 8, cudaMemcpyDeviceToHost, S.stream);
+    st = check_cuda(cudaStreamSynchronize(S.stream));
+    if (st) return st;
+    for (int i = 0; i < m; ++i) {
+        if (keys) canon(S, t[i], a[i], b[i], keys + 5 * i);
+        if (toi) toi[i] = tt[i];
+    }
+    return BF_OK;
+}
+
+int bf_update_active_set(bf_scene *scene, const double *x, const double *xhat, int32_t *n_active)
+{
+    SCENE_OR_ARG(scene);
+    if (!x || !xhat) return BF_E_ARG;
+    const int st = run_update_active_set(S, x, xhat);
+    if (n_active) *n_active = S.nc;
+    return st;
+}
+
+int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double *alpha)
+{
+    SCENE_OR_ARG(scene);
+    if (!x0 || !x1 || !alpha) return BF_E_ARG;
+    return run_ccd(S, x0, x1, false, alpha, nullptr);
+}
+
+int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double s, double *toi, void *stream)
+{
+    if ((type != PT && type != EE) || n < 0 || (n > 0 && (!x0 || !x1 || !toi)) || !(s > 0 && s < 1))
+        return BF_E_ARG;
+    const int st = accd_pairs(type, n, x0, x1, s, toi, (cudaStream_t)stream);
+    if (st) return st;
+    return check_cuda(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
+int bf_enable_timers(bf_scene *scene, int32_t on)
+{
+    SCENE_OR_ARG(scene);
+    S.timers_on = on != 0;
+    for (int i = 0; i < T_N; ++i) {
+        S.t_launch[i] = 0;
+        S.t_ms[i] = 0.0;
+    }
+    return BF_OK;
+}
+
+int bf_get_launch_count(bf_scene *scene, int64_t *n)
+{
+    SCENE_OR_ARG(scene);
+    if (!n) return BF_E_ARG;
+    *n = S.n_launch;
+    return BF_OK;
+}
+
+int bf_get_timers(bf_scene *scene, int32_t cap, int64_t *launches, double *ms, const char **names)
+{
+    SCENE_OR_ARG(scene);
+    cudaStreamSynchronize(S.stream);
+    flush_timers(S);
+    for (int i = 0; i < T_N && i < cap; ++i) {
+        if (launches) launches[i] = S.t_launch[i];
+        if (ms) ms[i] = S.t_ms[i];
+        if (names) names[i] = kTimerNames[i];
+    }
+    return T_N;
+}
+
+}  // extern "C"

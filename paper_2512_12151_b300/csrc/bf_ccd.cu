@@ -1,0 +1,875 @@
+// Collision detection and the active set (section 5.1, Alg. 3).
+//
+// This translation unit is compiled with -fmad=false: the unsigned
+// distances and the additive CCD below evaluate their FP64 arithmetic in a
+// fixed order (products rounded, sums left to right, IEEE division and
+// square root), so that a time of impact depends only on its 24 input
+// coordinates.
+//
+// Broad phase: a linear BVH (Karras 2012: Morton codes, radix sort, radix
+// tree, bottom-up refit) over the swept boxes of the surface triangles and
+// of the surface edges, rebuilt for every CCD pass; vertex boxes query the
+// triangle tree, edge boxes the edge tree.  A pair is a candidate when the
+// closed swept boxes overlap (box coordinates are exact min/max values), it
+// shares no vertex, and not all four of its vertices are prescribed.
+// Narrow phase: additive CCD (the ACCD of section 5.1) with thickness 0 and
+// target gap s * d(x0).
+#include <cub/cub.cuh>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "bf_device.cuh"
+#include "bf_internal.cuh"
+
+namespace bf {
+
+// ---------------------------------------------------------------------------
+// distances (fixed evaluation order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dot3(const double *a, const double *b)
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+// squared distance from p to the closed segment [a, b]; *t = parameter
+__device__ double seg_d2(const double *p, const double *a, const double *b, double *tout)
+{
+    double e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    const double ee = dot3(e, e);
+    double t = 0.0;
+    if (ee > 0.0) t = dot3(ap, e) / ee;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    double r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = p[k] - (a[k] + t * e[k]);
+    *tout = t;
+    return dot3(r, r);
+}
+
+// squared distance from p to the closed triangle (a, b, c); w = weights of
+// the closest point
+__device__ double tri_d2(const double *p, const double *a, const double *b, const double *c, double *w)
+{
+    double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    const double d00 = dot3(ab, ab), d01 = dot3(ab, ac), d11 = dot3(ac, ac);
+    const double d20 = dot3(ap, ab), d21 = dot3(ap, ac);
+    const double den = d00 * d11 - d01 * d01;
+    if (den > 0.0) {
+        const double v = (d11 * d20 - d01 * d21) / den;
+        const double ww = (d00 * d21 - d01 * d20) / den;
+        const double u = (1.0 - v) - ww;
+        if (u >= 0.0 && v >= 0.0 && ww >= 0.0) {
+            double r[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r[k] = p[k] - ((a[k] + v * ab[k]) + ww * ac[k]);
+            w[0] = u;
+            w[1] = v;
+            w[2] = ww;
+            return dot3(r, r);
+        }
+    }
+    double t;
+    double best = seg_d2(p, a, b, &t);
+    w[0] = 1.0 - t; w[1] = t; w[2] = 0.0;
+    double d = seg_d2(p, b, c, &t);
+    if (d < best) { best = d; w[0] = 0.0; w[1] = 1.0 - t; w[2] = t; }
+    d = seg_d2(p, c, a, &t);
+    if (d < best) { best = d; w[0] = t; w[1] = 0.0; w[2] = 1.0 - t; }
+    return best;
+}
+
+// squared distance between closed segments [a0, a1] and [b0, b1]
+__device__ double edge_d2(const double *a0, const double *a1, const double *b0, const double *b1, double *wa,
+                          double *wb)
+{
+    double ea[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+    double eb[3] = {b1[0] - b0[0], b1[1] - b0[1], b1[2] - b0[2]};
+    double w[3] = {a0[0] - b0[0], a0[1] - b0[1], a0[2] - b0[2]};
+    const double A = dot3(ea, ea), B = dot3(ea, eb), C = dot3(eb, eb), D = dot3(ea, w), E = dot3(eb, w);
+    const double den = A * C - B * B;
+    double best = INFINITY;
+    if (den > 0.0) {
+        const double s = (B * E - C * D) / den;
+        const double t = (A * E - B * D) / den;
+        if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {
+            double r[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r[k] = (a0[k] + s * ea[k]) - (b0[k] + t * eb[k]);
+            best = dot3(r, r);
+            wa[0] = 1.0 - s; wa[1] = s; wb[0] = 1.0 - t; wb[1] = t;
+        }
+    }
+    double t, d;
+    d = seg_d2(a0, b0, b1, &t);
+    if (d < best) { best = d; wa[0] = 1.0; wa[1] = 0.0; wb[0] = 1.0 - t; wb[1] = t; }
+    d = seg_d2(a1, b0, b1, &t);
+    if (d < best) { best = d; wa[0] = 0.0; wa[1] = 1.0; wb[0] = 1.0 - t; wb[1] = t; }
+    d = seg_d2(b0, a0, a1, &t);
+    if (d < best) { best = d; wb[0] = 1.0; wb[1] = 0.0; wa[0] = 1.0 - t; wa[1] = t; }
+    d = seg_d2(b1, a0, a1, &t);
+    if (d < best) { best = d; wb[0] = 0.0; wb[1] = 1.0; wa[0] = 1.0 - t; wa[1] = t; }
+    return best;
+}
+
+__device__ __forceinline__ double pair_d2(int type, const double *x)
+{
+    double w[3], wb[2];
+    if (type == PT) return tri_d2(x, x + 3, x + 6, x + 9, w);
+    return edge_d2(x, x + 3, x + 6, x + 9, w, wb);
+}
+
+// Additive CCD along x0 -> x1 (positions of the pair's 4 vertices).
+// Returns true with *toi on a hit at t <= tmax.
+__device__ bool accd(int type, const double *x0, const double *x1, double s, double tmax, int max_iter,
+                     double *toi)
+{
+    double p[12], x[12], n[4];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = x1[k] - x0[k];
+    double pbar[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pbar[c] = (((p[c] + p[3 + c]) + p[6 + c]) + p[9 + c]) * 0.25;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[3 * k + c] = p[3 * k + c] - pbar[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) n[k] = sqrt(dot3(p + 3 * k, p + 3 * k));
+    const double lp = type == PT ? n[0] + fmax(fmax(n[1], n[2]), n[3]) : fmax(n[0], n[1]) + fmax(n[2], n[3]);
+    if (lp == 0.0) return false;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[k] = x0[k];
+    double d = sqrt(pair_d2(type, x));
+    const double g = s * d;
+    double t = 0.0;
+    double tl = ((1.0 - s) * d) / lp;
+    for (int it = 0; it < max_iter; ++it) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) x[k] = x[k] + tl * p[k];
+        d = sqrt(pair_d2(type, x));
+        if (t > 0.0 && d < g) {
+            *toi = t;
+            return true;
+        }
+        t = t + tl;
+        if (t > tmax) return false;
+        tl = (0.9 * d) / lp;
+    }
+    *toi = t;
+    return true;
+}
+
+__device__ __forceinline__ int4 pair_vertices(int type, int a, int b, const int *__restrict__ st,
+                                              const int *__restrict__ se)
+{
+    if (type == PT) return make_int4(a, st[3 * b], st[3 * b + 1], st[3 * b + 2]);
+    return make_int4(se[2 * a], se[2 * a + 1], se[2 * b], se[2 * b + 1]);
+}
+
+__device__ __forceinline__ void gather12(const double *__restrict__ x, int4 v, double *o)
+{
+    const int id[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[3 * k + c] = x[3 * id[k] + c];
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 2 lines 2-4: d_i(x), grad d_i(x) (envelope theorem at the closest
+// points), and the free-vertex mask of each pair
+// ---------------------------------------------------------------------------
+__global__ void k_linearize(int nc, const int *__restrict__ ctype, const int4 *__restrict__ cv,
+                            const double *__restrict__ x, const uint8_t *__restrict__ dir, double *__restrict__ cd,
+                            double *__restrict__ cg, unsigned char *__restrict__ cmask, double *dout, double *gout)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const int4 v = cv[i];
+    double X[12], cw[4];
+    gather12(x, v, X);
+    double d2;
+    if (ctype[i] == PT) {
+        double w[3];
+        d2 = tri_d2(X, X + 3, X + 6, X + 9, w);
+        cw[0] = 1.0; cw[1] = -w[0]; cw[2] = -w[1]; cw[3] = -w[2];
+    } else {
+        double wa[2], wb[2];
+        d2 = edge_d2(X, X + 3, X + 6, X + 9, wa, wb);
+        cw[0] = wa[0]; cw[1] = wa[1]; cw[2] = -wb[0]; cw[3] = -wb[1];
+    }
+    const double d = sqrt(d2);
+    double diff[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) diff[c] += cw[k] * X[3 * k + c];
+    cd[i] = d;
+    if (dout) dout[i] = d;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double gv = d > 0.0 ? cw[k] * diff[c] / d : 0.0;
+            cg[12 * (size_t)i + 3 * k + c] = gv;
+            if (gout) gout[12 * (size_t)i + 3 * k + c] = gv;
+        }
+    const int id[4] = {v.x, v.y, v.z, v.w};
+    unsigned char m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (!dir[id[k]]) m |= (unsigned char)(1u << k);
+    cmask[i] = m;
+}
+
+void launch_linearize(Scene &S, const double *xlin)
+{
+    if (S.nc == 0) return;
+    {
+        k_linearize<<<cdiv(S.nc, kThreads), kThreads, 0, S.stream>>>(S.nc, S.ctype, S.cv, xlin, S.dir, S.cd, S.cg,
+                                                                 S.cmask, nullptr, nullptr); ++S.n_launch;
+    }
+}
+
+void launch_linearize_out(Scene &S, const double *xlin, double *dout, double *gout)
+{
+    if (S.nc == 0) return;
+    {
+        k_linearize<<<cdiv(S.nc, kThreads), kThreads, 0, S.stream>>>(S.nc, S.ctype, S.cv, xlin, S.dir, S.cd, S.cg,
+                                                                 S.cmask, dout, gout); ++S.n_launch;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LBVH
+// ---------------------------------------------------------------------------
+template <int NV>
+__global__ void k_prim_boxes(int n, const int *__restrict__ ids, const double *__restrict__ x0,
+                             const double *__restrict__ x1, double *__restrict__ lo, double *__restrict__ hi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int v = ids[NV * (size_t)i + k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a = x0[3 * v + c], b = x1[3 * v + c];
+            l[c] = fmin(l[c], fmin(a, b));
+            h[c] = fmax(h[c], fmax(a, b));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[3 * (size_t)i + c] = l[c];
+        hi[3 * (size_t)i + c] = h[c];
+    }
+}
+
+__device__ __forceinline__ int f2ord(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void k_centroid_bounds(int n, const double *__restrict__ lo, const double *__restrict__ hi, int *bnd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < n)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float m = (float)(0.5 * (lo[3 * (size_t)i + c] + hi[3 * (size_t)i + c]));
+            mn[c] = m;
+            mx[c] = m;
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicMin(bnd + c, f2ord(mn[c]));
+            atomicMax(bnd + 3 + c, f2ord(mx[c]));
+        }
+}
+
+__device__ __forceinline__ unsigned expand10(unsigned v)
+{
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__global__ void k_morton(int n, const double *__restrict__ lo, const double *__restrict__ hi, const int *bnd,
+                         unsigned *__restrict__ code, int *__restrict__ prim)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float b0 = ord2f(bnd[c]), b1 = ord2f(bnd[3 + c]);
+        const float m = (float)(0.5 * (lo[3 * (size_t)i + c] + hi[3 * (size_t)i + c]));
+        float u = b1 > b0 ? (m - b0) / (b1 - b0) : 0.5f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        q[c] = min((unsigned)(u * 1024.0f), 1023u);
+    }
+    code[i] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    prim[i] = i;
+}
+
+__device__ __forceinline__ int lcp(const unsigned *__restrict__ m, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    const unsigned a = m[i], b = m[j];
+    if (a == b) return 32 + __clz((unsigned)(i ^ j));
+    return __clz(a ^ b);
+}
+
+__global__ void k_radix_tree(int n, const unsigned *__restrict__ m, int2 *__restrict__ child, int *__restrict__ parent)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (lcp(m, n, i, i + 1) - lcp(m, n, i, i - 1)) > 0 ? 1 : -1;
+    const int dmin = lcp(m, n, i, i - d);
+    int lmax = 2;
+    while (lcp(m, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (lcp(m, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = lcp(m, n, i, j);
+    int s = 0;
+    for (int div = 2;; div <<= 1) {
+        const int t = (l + div - 1) / div;
+        if (lcp(m, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    const int gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int left = (min(i, j) == gamma) ? (n - 1 + gamma) : gamma;
+    const int right = (max(i, j) == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
+    child[i] = make_int2(left, right);
+    parent[left] = i;
+    parent[right] = i;
+}
+
+__global__ void k_refit(int n, const int *__restrict__ prim, const int2 *__restrict__ child,
+                        const int *__restrict__ parent, int *__restrict__ flags, const double *__restrict__ plo,
+                        const double *__restrict__ phi, double *lo, double *hi)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int node = n - 1 + k;
+    const int p = prim[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[3 * (size_t)node + c] = plo[3 * (size_t)p + c];
+        hi[3 * (size_t)node + c] = phi[3 * (size_t)p + c];
+    }
+    for (int level = 0; node != 0; ++level) {
+        if (level > 96) {  // deeper than any radix tree over 30-bit codes + index bits
+            atomicOr(flags + n, 1);
+            return;
+        }
+        const int par = parent[node];
+        __threadfence();
+        if (atomicAdd(flags + par, 1) == 0) return;  // the sibling finishes the parent
+        __threadfence();
+        const int2 ch = child[par];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[3 * (size_t)par + c] = fmin(__ldcg(lo + 3 * (size_t)ch.x + c), __ldcg(lo + 3 * (size_t)ch.y + c));
+            hi[3 * (size_t)par + c] = fmax(__ldcg(hi + 3 * (size_t)ch.x + c), __ldcg(hi + 3 * (size_t)ch.y + c));
+        }
+        node = par;
+    }
+}
+
+static void cub_tmp_ensure(Scene &S, size_t bytes)
+{
+    if (bytes <= S.cub_tmp_bytes) return;
+    if (S.cub_tmp) dev_free(S, S.cub_tmp);
+    S.cub_tmp_bytes = bytes + bytes / 2;
+    S.cub_tmp = dev_alloc(S, S.cub_tmp_bytes);
+}
+
+static int bvh_reserve(Scene &S, LBVH &T, int n)
+{
+    if (n <= T.cap) return BF_OK;
+    int cap = std::max(n, 16);
+    void *old[] = {T.morton, T.morton_alt, T.prim, T.prim_alt, T.child, T.parent, T.flags, T.lo, T.hi, T.plo, T.phi};
+    for (void *p : old)
+        if (p) dev_free(S, p);
+    T.morton = (unsigned *)dev_alloc(S, cap * sizeof(unsigned));
+    T.morton_alt = (unsigned *)dev_alloc(S, cap * sizeof(unsigned));
+    T.prim = (int *)dev_alloc(S, cap * sizeof(int));
+    T.prim_alt = (int *)dev_alloc(S, cap * sizeof(int));
+    T.child = (int2 *)dev_alloc(S, cap * sizeof(int2));
+    T.parent = (int *)dev_alloc(S, 2 * cap * sizeof(int));
+    T.flags = (int *)dev_alloc(S, (cap + 1) * sizeof(int));
+    T.lo = (double *)dev_alloc(S, 2 * 3 * (size_t)cap * sizeof(double));
+    T.hi = (double *)dev_alloc(S, 2 * 3 * (size_t)cap * sizeof(double));
+    T.plo = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
+    T.phi = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
+    if (!T.morton || !T.morton_alt || !T.prim || !T.prim_alt || !T.child || !T.parent || !T.flags || !T.lo || !T.hi ||
+        !T.plo || !T.phi)
+        return BF_E_OOM;
+    T.cap = cap;
+    return BF_OK;
+}
+
+template <int NV>
+static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0, const double *x1)
+{
+    T.n = n;
+    if (n == 0) return BF_OK;
+    int st = bvh_reserve(S, T, n);
+    if (st) return st;
+    ScopedTimer tm(S, T_BVH);
+    const int nb = cdiv(n, kThreads);
+    k_prim_boxes<NV><<<nb, kThreads, 0, S.stream>>>(n, ids, x0, x1, T.plo, T.phi); ++S.n_launch;
+    int init[6];
+    for (int c = 0; c < 3; ++c) {
+        init[c] = 0x7f800000;           // +inf as ordered int
+        init[3 + c] = (int)0x807fffff;  // -inf as ordered int
+    }
+    int *bnd = (int *)S.bounds;
+    cudaMemcpyAsync(bnd, init, sizeof(init), cudaMemcpyHostToDevice, S.stream);
+    k_centroid_bounds<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd); ++S.n_launch;
+    k_morton<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd, T.morton, T.prim); ++S.n_launch;
+    cub::DoubleBuffer<unsigned> keys(T.morton, T.morton_alt);
+    cub::DoubleBuffer<int> vals(T.prim, T.prim_alt);
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, vals, n, 0, 30, S.stream);
+    cub_tmp_ensure(S, bytes);
+    cub::DeviceRadixSort::SortPairs(S.cub_tmp, bytes, keys, vals, n, 0, 30, S.stream);
+    if (keys.Current() != T.morton) {
+        std::swap(T.morton, T.morton_alt);
+        std::swap(T.prim, T.prim_alt);
+    }
+    if (n > 1) k_radix_tree<<<cdiv(n - 1, kThreads), kThreads, 0, S.stream>>>(n, T.morton, T.child, T.parent); ++S.n_launch;
+    cudaMemsetAsync(T.flags, 0, (n + 1) * sizeof(int), S.stream);
+    k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.flags, T.plo, T.phi, T.lo, T.hi); ++S.n_launch;
+    return BF_OK;
+}
+
+__device__ __forceinline__ bool box_overlap(const double *l1, const double *h1, const double *l2, const double *h2)
+{
+    return !(l1[0] > h2[0] || l2[0] > h1[0] || l1[1] > h2[1] || l2[1] > h1[1] || l1[2] > h2[2] || l2[2] > h1[2]);
+}
+
+// queries: vertices against the triangle tree (type PT) or edges against
+// the edge tree (type EE, b > a only)
+template <int TYPE>
+__global__ void k_query(int nq, const int *__restrict__ qids, const double *__restrict__ x0,
+                        const double *__restrict__ x1, int n, const int2 *__restrict__ child,
+                        const int *__restrict__ prim, const double *__restrict__ lo, const double *__restrict__ hi,
+                        const int *__restrict__ st, const int *__restrict__ se, const uint8_t *__restrict__ dir,
+                        int2 *__restrict__ cand, int cap, int *count, int *dflag)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq || n == 0) return;
+    double ql[3], qh[3];
+    int qa, qv0, qv1 = -1;
+    if (TYPE == PT) {
+        qa = qids[q];
+        qv0 = qa;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a = x0[3 * qa + c], b = x1[3 * qa + c];
+            ql[c] = fmin(a, b);
+            qh[c] = fmax(a, b);
+        }
+    } else {
+        qa = q;
+        qv0 = se[2 * q];
+        qv1 = se[2 * q + 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a = x0[3 * qv0 + c], b = x1[3 * qv0 + c], a2 = x0[3 * qv1 + c], b2 = x1[3 * qv1 + c];
+            ql[c] = fmin(fmin(a, b), fmin(a2, b2));
+            qh[c] = fmax(fmax(a, b), fmax(a2, b2));
+        }
+    }
+    const bool qdir = TYPE == PT ? dir[qv0] != 0 : (dir[qv0] && dir[qv1]);
+    int stack[64];
+    int sp = 0;
+    stack[sp++] = 0;
+    for (int visits = 0; sp > 0; ++visits) {
+        if (visits > 2 * n + 64) {  // a tree has 2n - 1 nodes
+            atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
+            return;
+        }
+        const int node = stack[--sp];
+        if (!box_overlap(ql, qh, lo + 3 * (size_t)node, hi + 3 * (size_t)node)) continue;
+        if (node >= n - 1) {
+            const int b = prim[node - (n - 1)];
+            bool ok;
+            if (TYPE == PT) {
+                const int t0 = st[3 * b], t1 = st[3 * b + 1], t2 = st[3 * b + 2];
+                ok = qv0 != t0 && qv0 != t1 && qv0 != t2 && !(qdir && dir[t0] && dir[t1] && dir[t2]);
+            } else {
+                const int e0 = se[2 * b], e1 = se[2 * b + 1];
+                ok = b > qa && e0 != qv0 && e0 != qv1 && e1 != qv0 && e1 != qv1 && !(qdir && dir[e0] && dir[e1]);
+            }
+            if (ok) {
+                const int idx = atomicAdd(count, 1);
+                if (idx < cap) cand[idx] = make_int2(qa, b);
+            }
+        } else {
+            const int2 ch = child[node];
+            if (sp + 2 > 64) {
+                atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
+                return;
+            }
+            stack[sp++] = ch.x;
+            stack[sp++] = ch.y;
+        }
+    }
+}
+
+// narrow phase over candidates; mode 0: min TOI, mode 1: collect hits
+template <int TYPE>
+__global__ void k_narrow(int n, const int2 *__restrict__ cand, const int *__restrict__ st, const int *__restrict__ se,
+                         const double *__restrict__ x0, const double *__restrict__ x1, double s, int max_iter, int mode,
+                         double *toi_min, int *hit_type, int *hit_a, int *hit_b, double *hit_toi, int hit_cap,
+                         int *nhit)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 c = cand[i];
+    const int4 v = pair_vertices(TYPE, c.x, c.y, st, se);
+    double p0[12], p1[12], t;
+    gather12(x0, v, p0);
+    gather12(x1, v, p1);
+    if (!accd(TYPE, p0, p1, s, 1.0, max_iter, &t)) return;
+    if (mode == 0) {
+        atomic_min_pos(toi_min, t);
+    } else {
+        const int idx = atomicAdd(nhit, 1);
+        if (idx < hit_cap) {
+            hit_type[idx] = TYPE;
+            hit_a[idx] = c.x;
+            hit_b[idx] = c.y;
+            hit_toi[idx] = t;
+        }
+    }
+}
+
+__global__ void k_accd_pairs(int type, int n, const double *__restrict__ x0, const double *__restrict__ x1, double s,
+                             int max_iter, double *__restrict__ toi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double t;
+    toi[i] = accd(type, x0 + 12 * (size_t)i, x1 + 12 * (size_t)i, s, 1.0, max_iter, &t) ? t : INFINITY;
+}
+
+int accd_pairs(int type, int n, const double *x0, const double *x1, double s, double *toi, cudaStream_t st)
+{
+    if (n <= 0) return BF_OK;
+    k_accd_pairs<<<cdiv(n, 128), 128, 0, st>>>(type, n, x0, x1, s, kAccdMaxIter, toi);
+    return check_cuda(cudaGetLastError());
+}
+
+int ccd_reserve(Scene &S, int npt, int nee, int nhit)
+{
+    const int need = std::max(npt, nee);
+    if (need > S.cand_cap) {
+        const int cap = std::max(need + need / 2, 1024);
+        if (S.cand_pt) dev_free(S, S.cand_pt);
+        if (S.cand_ee) dev_free(S, S.cand_ee);
+        S.cand_pt = (int2 *)dev_alloc(S, cap * sizeof(int2));
+        S.cand_ee = (int2 *)dev_alloc(S, cap * sizeof(int2));
+        if (!S.cand_pt || !S.cand_ee) return BF_E_OOM;
+        S.cand_cap = cap;
+    }
+    if (nhit > S.hit_cap) {
+        const int cap = std::max(nhit + nhit / 2, 1024);
+        void *old[] = {S.hit_type, S.hit_a, S.hit_b, S.hit_toi, S.hit_key, S.hit_key_alt, S.hit_idx, S.hit_idx_alt,
+                       S.keep};
+        for (void *p : old)
+            if (p) dev_free(S, p);
+        S.hit_type = (int *)dev_alloc(S, cap * sizeof(int));
+        S.hit_a = (int *)dev_alloc(S, cap * sizeof(int));
+        S.hit_b = (int *)dev_alloc(S, cap * sizeof(int));
+        S.hit_toi = (double *)dev_alloc(S, cap * sizeof(double));
+        S.hit_key = (unsigned long long *)dev_alloc(S, cap * sizeof(unsigned long long));
+        S.hit_key_alt = (unsigned long long *)dev_alloc(S, cap * sizeof(unsigned long long));
+        S.hit_idx = (int *)dev_alloc(S, cap * sizeof(int));
+        S.hit_idx_alt = (int *)dev_alloc(S, cap * sizeof(int));
+        S.keep = (int *)dev_alloc(S, cap * sizeof(int));
+        if (!S.hit_type || !S.hit_a || !S.hit_b || !S.hit_toi || !S.hit_key || !S.hit_key_alt || !S.hit_idx ||
+            !S.hit_idx_alt || !S.keep)
+            return BF_E_OOM;
+        S.hit_cap = cap;
+    }
+    return BF_OK;
+}
+
+// Broad + narrow phase along x0 -> x1.  collect_hits: store every hit
+// (type, a, b, toi) and return their count; else *alpha_out =
+// min(1, min TOI).
+int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, double *alpha_out, int *nhits_out)
+{
+    int st = bvh_build<3>(S, S.bvh_tri, S.nst, S.st, x0, x1);
+    if (st) return st;
+    st = bvh_build<2>(S, S.bvh_edge, S.nse, S.se, x0, x1);
+    if (st) return st;
+    int npt = 0, nee = 0;
+    cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        cudaMemsetAsync(S.dflag + F_NCAND_PT, 0, 2 * sizeof(int), S.stream);
+        if (S.nsv && S.nst)
+            {
+                k_query<PT><<<cdiv(S.nsv, 128), 128, 0, S.stream>>>(S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.child,
+                                                                S.bvh_tri.prim, S.bvh_tri.lo, S.bvh_tri.hi, S.st,
+                                                                S.se, S.dir, S.cand_pt, S.cand_cap,
+                                                                S.dflag + F_NCAND_PT, S.dflag); ++S.n_launch;
+            }
+        if (S.nse > 1)
+            {
+                k_query<EE><<<cdiv(S.nse, 128), 128, 0, S.stream>>>(S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.child,
+                                                                S.bvh_edge.prim, S.bvh_edge.lo, S.bvh_edge.hi, S.st,
+                                                                S.se, S.dir, S.cand_ee, S.cand_cap,
+                                                                S.dflag + F_NCAND_EE, S.dflag); ++S.n_launch;
+            }
+        st = sync_flags(S);
+        if (st) return st;
+        npt = S.h_flag[F_NCAND_PT];
+        nee = S.h_flag[F_NCAND_EE];
+        if (S.h_flag[F_ERR] & ERR_CAND_OVERFLOW) return BF_E_CAPACITY;
+        if (npt <= S.cand_cap && nee <= S.cand_cap) break;
+        st = ccd_reserve(S, npt, nee, 0);
+        if (st) return st;
+    }
+    if (npt > S.cand_cap || nee > S.cand_cap) return BF_E_CAPACITY;
+    const double s = S.prm.s_ccd;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if (collect_hits) {
+            cudaMemsetAsync(S.dflag + F_NHIT, 0, sizeof(int), S.stream);
+        } else {
+            const double one = 1.0;
+            cudaMemcpyAsync(S.dscal + S_TOI, &one, sizeof(double), cudaMemcpyHostToDevice, S.stream);
+        }
+        {
+            ScopedTimer tm(S, T_CCD_NARROW);
+            if (npt)
+                {
+                    k_narrow<PT><<<cdiv(npt, 128), 128, 0, S.stream>>>(npt, S.cand_pt, S.st, S.se, x0, x1, s, kAccdMaxIter,
+                                                                  collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type,
+                                                                  S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
+                                                                  S.dflag + F_NHIT); ++S.n_launch;
+                }
+            if (nee)
+                {
+                    k_narrow<EE><<<cdiv(nee, 128), 128, 0, S.stream>>>(nee, S.cand_ee, S.st, S.se, x0, x1, s, kAccdMaxIter,
+                                                                  collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type,
+                                                                  S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
+                                                                  S.dflag + F_NHIT); ++S.n_launch;
+                }
+        }
+        st = sync_flags(S);
+        if (st) return st;
+        if (!collect_hits) {
+            if (alpha_out) *alpha_out = std::min(1.0, S.h_scal[S_TOI]);
+            return BF_OK;
+        }
+        const int nh = S.h_flag[F_NHIT];
+        if (nh <= S.hit_cap) {
+            if (nhits_out) *nhits_out = nh;
+            return BF_OK;
+        }
+        st = ccd_reserve(S, 0, 0, nh);
+        if (st) return st;
+    }
+    return BF_E_CAPACITY;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3 UpdateActiveSet
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long pair_key(int type, int a, int b)
+{
+    return ((unsigned long long)type << 62) | ((unsigned long long)a << 31) | (unsigned long long)b;
+}
+
+__global__ void k_ckeys(int nc, const int *__restrict__ ctype, const int *__restrict__ ca, const int *__restrict__ cb,
+                        unsigned long long *__restrict__ key)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) key[i] = pair_key(ctype[i], ca[i], cb[i]);
+}
+
+// new pairs (not in C) lower the per-vertex minimum TOI T_v (lines 3-7)
+__global__ void k_new_hits(int nh, const int *__restrict__ ht, const int *__restrict__ ha, const int *__restrict__ hb,
+                           const double *__restrict__ htoi, const unsigned long long *__restrict__ ck, int nc,
+                           const int *__restrict__ st, const int *__restrict__ se, int *__restrict__ isnew,
+                           unsigned long long *__restrict__ tv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nh) return;
+    const unsigned long long k = pair_key(ht[i], ha[i], hb[i]);
+    int lo = 0, hi = nc - 1;
+    bool found = false;
+    while (lo <= hi) {
+        const int m = (lo + hi) >> 1;
+        const unsigned long long km = ck[m];
+        if (km == k) {
+            found = true;
+            break;
+        }
+        if (km < k) lo = m + 1;
+        else hi = m - 1;
+    }
+    isnew[i] = found ? 0 : 1;
+    if (found) return;
+    const int4 v = pair_vertices(ht[i], ha[i], hb[i], st, se);
+    const unsigned long long t = (unsigned long long)__double_as_longlong(htoi[i]);
+    atomicMin(tv + v.x, t);
+    atomicMin(tv + v.y, t);
+    atomicMin(tv + v.z, t);
+    atomicMin(tv + v.w, t);
+}
+
+// keep a new pair whose TOI equals T_v of one of its vertices (lines 8-13)
+__global__ void k_keep(int nh, const int *__restrict__ ht, const int *__restrict__ ha, const int *__restrict__ hb,
+                       const double *__restrict__ htoi, const int *__restrict__ isnew, const int *__restrict__ st,
+                       const int *__restrict__ se, const unsigned long long *__restrict__ tv,
+                       unsigned long long *__restrict__ kkey, int *__restrict__ kidx, int *nkeep)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nh || !isnew[i]) return;
+    const int4 v = pair_vertices(ht[i], ha[i], hb[i], st, se);
+    const unsigned long long t = (unsigned long long)__double_as_longlong(htoi[i]);
+    if (tv[v.x] == t || tv[v.y] == t || tv[v.z] == t || tv[v.w] == t) {
+        const int j = atomicAdd(nkeep, 1);
+        kkey[j] = pair_key(ht[i], ha[i], hb[i]);
+        kidx[j] = i;
+    }
+}
+
+__global__ void k_append(int nk, int nc, const int *__restrict__ kidx, const int *__restrict__ ht,
+                         const int *__restrict__ ha, const int *__restrict__ hb, const int *__restrict__ st,
+                         const int *__restrict__ se, int *ctype, int *ca, int *cb, int4 *cv, double *clam, double *cgam)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nk) return;
+    const int i = kidx[j];
+    const int o = nc + j;
+    ctype[o] = ht[i];
+    ca[o] = ha[i];
+    cb[o] = hb[i];
+    cv[o] = pair_vertices(ht[i], ha[i], hb[i], st, se);
+    clam[o] = 0.0;
+    cgam[o] = 1.0;
+}
+
+// prune gamma < 0.01 (lines 14-18): stable compaction in place via a scan
+__global__ void k_prune_flags(int nc, const double *__restrict__ cgam, int *__restrict__ flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) flag[i] = cgam[i] < 0.01 ? 0 : 1;
+}
+
+template <class T>
+__global__ void k_scatter(int nc, const int *__restrict__ flag, const int *__restrict__ pos, const T *__restrict__ in,
+                          T *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc && flag[i]) out[pos[i]] = in[i];
+}
+
+int active_reserve(Scene &S, int n);
+
+template <class T>
+static void compact_array(Scene &S, int nc, const int *flag, const int *pos, T *&arr, void *scratch)
+{
+    k_scatter<T><<<cdiv(nc, kThreads), kThreads, 0, S.stream>>>(nc, flag, pos, arr, (T *)scratch); ++S.n_launch;
+    cudaMemcpyAsync(arr, scratch, nc * sizeof(T), cudaMemcpyDeviceToDevice, S.stream);
+}
+
+int run_update_active_set(Scene &S, const double *x, const double *xhat)
+{
+    int nh = 0;
+    int st = run_ccd(S, x, xhat, true, nullptr, &nh);
+    if (st) return st;
+    if (nh > 0) {
+        // sorted keys of C for the membership test
+        size_t bytes = 0;
+        if (S.nc > 0) {
+            k_ckeys<<<cdiv(S.nc, kThreads), kThreads, 0, S.stream>>>(S.nc, S.ctype, S.ca, S.cb, S.ckey); ++S.n_launch;
+            cub::DeviceRadixSort::SortKeys(nullptr, bytes, S.ckey, S.ckey_sorted, S.nc, 0, 64, S.stream);
+            cub_tmp_ensure(S, bytes);
+            cub::DeviceRadixSort::SortKeys(S.cub_tmp, bytes, S.ckey, S.ckey_sorted, S.nc, 0, 64, S.stream);
+        }
+        cudaMemsetAsync(S.tv, 0x7f, (size_t)S.nv * sizeof(unsigned long long), S.stream);
+        k_new_hits<<<cdiv(nh, kThreads), kThreads, 0, S.stream>>>(nh, S.hit_type, S.hit_a, S.hit_b, S.hit_toi,
+                                                                  S.ckey_sorted, S.nc, S.st, S.se, S.keep, S.tv); ++S.n_launch;
+        cudaMemsetAsync(S.dflag + F_NKEEP, 0, sizeof(int), S.stream);
+        k_keep<<<cdiv(nh, kThreads), kThreads, 0, S.stream>>>(nh, S.hit_type, S.hit_a, S.hit_b, S.hit_toi, S.keep,
+                                                             S.st, S.se, S.tv, S.hit_key, S.hit_idx,
+                                                             S.dflag + F_NKEEP); ++S.n_launch;
+        st = sync_flags(S);
+        if (st) return st;
+        const int nk = S.h_flag[F_NKEEP];
+        if (nk > 0) {
+            // deterministic order: sort the kept pairs by key
+            cub::DoubleBuffer<unsigned long long> kb(S.hit_key, S.hit_key_alt);
+            cub::DoubleBuffer<int> vb(S.hit_idx, S.hit_idx_alt);
+            bytes = 0;
+            cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb, vb, nk, 0, 64, S.stream);
+            cub_tmp_ensure(S, bytes);
+            cub::DeviceRadixSort::SortPairs(S.cub_tmp, bytes, kb, vb, nk, 0, 64, S.stream);
+            st = active_reserve(S, S.nc + nk);
+            if (st) return st;
+            {
+                k_append<<<cdiv(nk, kThreads), kThreads, 0, S.stream>>>(nk, S.nc, vb.Current(), S.hit_type, S.hit_a,
+                                                                   S.hit_b, S.st, S.se, S.ctype, S.ca, S.cb, S.cv,
+                                                                   S.clam, S.cgam); ++S.n_launch;
+            }
+            S.nc += nk;
+        }
+    }
+    if (S.nc == 0) return BF_OK;
+    // prune
+    int *flag = (int *)S.ckey;  // reuse scratch (>= nc ints)
+    int *pos = (int *)S.ckey_sorted;
+    k_prune_flags<<<cdiv(S.nc, kThreads), kThreads, 0, S.stream>>>(S.nc, S.cgam, flag); ++S.n_launch;
+    size_t bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, bytes, flag, pos, S.nc, S.stream);
+    cub_tmp_ensure(S, bytes);
+    cub::DeviceScan::ExclusiveSum(S.cub_tmp, bytes, flag, pos, S.nc, S.stream);
+    int lastflag = 0, lastpos = 0;
+    cudaMemcpyAsync(&lastflag, flag + S.nc - 1, sizeof(int), cudaMemcpyDeviceToHost, S.stream);
+    cudaMemcpyAsync(&lastpos, pos + S.nc - 1, sizeof(int), cudaMemcpyDeviceToHost, S.stream);
+    st = check_cuda(cudaStreamSynchronize(S.stream));
+    if (st) return st;
+    const int keep = lastpos + lastflag;
+    if (keep == S.nc) return BF_OK;
+    void *scratch = S.cw;  // nc doubles of scratch (recomputed every Newton iteration)
+    void *scratch16 = S.cg; // 12 nc doubles
+    compact_array<int>(S, S.nc, flag, pos, S.ctype, scratch);
+    compact_array<int>(S, S.nc, flag, pos, S.ca, scratch);
+    compact_array<int>(S, S.nc, flag, pos, S.cb, scratch);
+    compact_array<double>(S, S.nc, flag, pos, S.clam, scratch);
+    compact_array<double>(S, S.nc, flag, pos, S.cgam, scratch);
+    compact_array<int4>(S, S.nc, flag, pos, S.cv, scratch16);
+    S.nc = keep;
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace bf

@@ -1,0 +1,192 @@
+// Internal declarations of the CUDA library behind include/bf.h.
+//
+// Data layout in HBM (one scene):
+//  - positions / velocities / gradients: (nv, 3) FP64 AoS;
+//  - tets: int4; Dm^-1 as 9 FP64 per tet; per-tet Lame parameters and rest
+//    volume; tblk: for each tet its 10 upper 3x3 blocks (i' <= j') as BSR
+//    block indices, bit 31 set when the block is stored transposed;
+//  - Hessian: upper block-sparse rows (diagonal + upper blocks of the
+//    elastic / mass pattern), values as 9 SoA planes val[e * nnzb + k]
+//    (FP64, or FP32 in mixed precision) so that consecutive threads read
+//    consecutive addresses; contact terms stay rank-1 per pair
+//    (mu gamma_i g_i g_i^T) and are applied matrix-free;
+//  - active set: SoA arrays (type, prim a, prim b, 4 vertex ids, lambda,
+//    gamma, d, 12 gradient entries, slack, free-vertex mask).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "bf.h"
+
+namespace bf {
+
+enum { PT = 0, EE = 1 };
+
+// device scalar slots (dscal)
+enum {
+    S_RZ = 0, S_BB, S_ALPHA, S_BETA, S_RR, S_PQ, S_E0, S_E1, S_MU, S_TOI, S_DOT, S_MAXDIAG,
+    S_NSCAL = 32
+};
+// device flag slots (dflag)
+enum {
+    F_DONE = 0, F_ITERS, F_ERR, F_MAXIT, F_NCAND_PT, F_NCAND_EE, F_NHIT, F_NKEEP, F_NSCRATCH,
+    F_NFLAG = 32
+};
+// error bits in dflag[F_ERR]
+enum { ERR_NONFINITE = 1, ERR_CAND_OVERFLOW = 2, ERR_HIT_OVERFLOW = 4, ERR_PQ = 8 };
+
+enum TimerId { T_ELASTIC = 0, T_SPMV, T_PCG_UPDATE, T_PCG_DIR, T_CONTACT, T_ENERGY, T_CCD_NARROW,
+               T_BVH, T_N };
+
+struct LBVH {
+    int n = 0, cap = 0;
+    // leaves: sorted primitive ids; nodes 0..n-2 internal, n-1..2n-2 leaves
+    unsigned *morton = nullptr, *morton_alt = nullptr;
+    int *prim = nullptr, *prim_alt = nullptr;
+    int2 *child = nullptr;
+    int *parent = nullptr;
+    int *flags = nullptr;
+    double *lo = nullptr, *hi = nullptr;  // 3 per node
+    double *plo = nullptr, *phi = nullptr;  // exact primitive boxes, 3 per primitive
+};
+
+struct Scene {
+    int nv = 0, nt = 0, nm = 0, nx = 0, ndir = 0;
+    int nsv = 0, nst = 0, nse = 0, nnzb = 0;
+    bf_params prm{};
+    double mu = 0.0, delta = 0.0;
+    int has_targets = 0;
+    cudaStream_t stream = nullptr;
+    bf_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> owned;
+
+    // host topology
+    std::vector<int> h_sv, h_st, h_se, h_rowptr, h_col;
+    std::vector<uint8_t> h_dir;
+    std::vector<int> h_dir_ids;
+    std::vector<long long> h_tri_key_sorted;  // sorted-vertex triangle keys, ascending
+    std::vector<int> h_tri_key_idx;
+
+    // device state
+    double *x = nullptr, *v = nullptr, *xt = nullptr, *xtilde = nullptr, *xk = nullptr,
+           *xh = nullptr, *xh_prev = nullptr, *xtmp = nullptr, *targets = nullptr;
+    uint8_t *dir = nullptr;
+    double *mass = nullptr;
+    int4 *tets = nullptr;
+    double *B = nullptr, *vol = nullptr, *emu = nullptr, *elam = nullptr;
+    int *tblk = nullptr;
+    int *rowptr = nullptr, *col = nullptr, *rowid = nullptr, *diagblk = nullptr;
+    double *val = nullptr;  // 9 planes FP64
+    float *valf = nullptr;  // 9 planes FP32 (mixed)
+    double *grad = nullptr;
+    double *cdiag = nullptr;  // contact diagonal blocks (nv x 9) for the preconditioner
+    double *pinv = nullptr;
+    float *pinvf = nullptr;
+    // PCG work vectors (n = 3 nv)
+    double *cg_x = nullptr, *cg_r = nullptr, *cg_b = nullptr, *cg_p = nullptr, *cg_q = nullptr,
+           *cg_z = nullptr, *pdir = nullptr;
+    float *cg_pf = nullptr, *cg_qf = nullptr, *cg_zf = nullptr;
+    // reductions
+    double *partials = nullptr;
+    int npartials = 0;
+    unsigned *counter = nullptr;
+    double *dscal = nullptr;
+    int *dflag = nullptr;
+    double *h_scal = nullptr;  // pinned mirrors
+    int *h_flag = nullptr;
+
+    // surface primitives
+    int *sv = nullptr, *st = nullptr, *se = nullptr;
+
+    // active set (capacity ccap)
+    int nc = 0, ccap = 0;
+    int *ctype = nullptr, *ca = nullptr, *cb = nullptr;
+    int4 *cv = nullptr;
+    double *clam = nullptr, *cgam = nullptr, *cd = nullptr, *cg = nullptr, *cs = nullptr,
+           *cw = nullptr;
+    unsigned char *cmask = nullptr;
+    unsigned long long *ckey = nullptr, *ckey_sorted = nullptr;
+    // CCD work
+    LBVH bvh_tri, bvh_edge;
+    int cand_cap = 0;
+    int2 *cand_pt = nullptr, *cand_ee = nullptr;
+    int hit_cap = 0;
+    int *hit_type = nullptr, *hit_a = nullptr, *hit_b = nullptr;
+    double *hit_toi = nullptr;
+    unsigned long long *hit_key = nullptr, *hit_key_alt = nullptr;
+    int *hit_idx = nullptr, *hit_idx_alt = nullptr;
+    unsigned long long *tv = nullptr;  // per-vertex min TOI bits
+    int *keep = nullptr;
+    void *cub_tmp = nullptr;
+    size_t cub_tmp_bytes = 0;
+    double *bounds = nullptr;  // Morton-code box (6 ordered ints)
+    int *dir_ids = nullptr;    // prescribed vertex ids (ndir)
+
+    // kernel launches issued by this scene (own kernels, not library sorts)
+    long long n_launch = 0;
+    // timers
+    bool timers_on = false;
+    int64_t t_launch[T_N] = {0};
+    double t_ms[T_N] = {0};
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+// ---- memory ----
+void *dev_alloc(Scene &S, size_t bytes);
+void dev_free(Scene &S, void *p);
+
+// ---- timers (per-kernel CUDA events on the scene's stream) ----
+struct ScopedTimer {
+    Scene *S;
+    int id;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ScopedTimer(Scene &s, int tid);
+    ~ScopedTimer();
+};
+void flush_timers(Scene &S);
+
+// ---- launchers: linear algebra (bf_linalg.cu) ----
+void launch_zero(Scene &S, double *p, size_t n);
+void launch_spmv(Scene &S, const double *x, double *y, bool with_dot, const int *done);
+void launch_pinv(Scene &S);
+int run_pcg(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
+void launch_axpy_to(Scene &S, double *out, const double *a, double r, const double *p, int n);
+void launch_blend(Scene &S, double *xk, const double *xh, double alpha, int n);
+void launch_velocity(Scene &S);
+
+// ---- launchers: elasticity (bf_elastic.cu) ----
+void launch_vertex_init(Scene &S, const double *xtilde, const double *xhat);
+void launch_elastic(Scene &S, const double *xhat);
+double run_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat);
+double run_mu_max_diag(Scene &S);
+void launch_xtilde(Scene &S, double *xtilde);
+
+// ---- launchers: contacts (bf_contact.cu) ----
+void launch_contact_assemble(Scene &S, const double *xlin, const double *xhat);
+void launch_multiplier_update(Scene &S, const double *xlin, const double *xhat);
+void launch_contact_energy(Scene &S, const double *xlin, const double *xhat, double *partials,
+                           int nblocks_offset);
+
+// ---- launchers: CCD and active set (bf_ccd.cu) ----
+void launch_linearize(Scene &S, const double *xlin);
+int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, double *alpha_out,
+            int *nhits_out);
+int run_update_active_set(Scene &S, const double *x, const double *xhat);
+int accd_pairs(int type, int n, const double *x0, const double *x1, double s, double *toi,
+               cudaStream_t st);
+int ccd_reserve(Scene &S, int npt, int nee, int nhit);
+int active_reserve(Scene &S, int n);
+
+// ---- sync helpers ----
+int sync_flags(Scene &S);  // copies dscal/dflag to host mirrors, returns CUDA status
+int check_cuda(cudaError_t e);
+
+inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+constexpr int kThreads = 256;
+constexpr int kAccdMaxIter = 100000;
+
+}  // namespace bf

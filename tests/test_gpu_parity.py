@@ -1,0 +1,363 @@
+"""CUDA library vs the FP64 oracle, teacher-forced: both sides start from the
+same oracle-produced state (positions, velocities, active set, mu, delta)
+and each stage of Alg. 1-3 is compared.
+
+Tolerances: FP64 floating-point results agree to 1e-9 relative (different
+summation orders and an analytic instead of a Jacobi eigensystem); TOIs are
+bit-exact (both sides evaluate the distances and the additive CCD in the
+same FP64 operation order, without FMA contraction); pair sets are equal;
+positions after a step agree within 1e-6 x the bounding-box diagonal
+(1e-4 in mixed precision)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2512_12151_b300 import binding as B
+from paper_2512_12151_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a, np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def keyset(keys):
+    return {tuple(int(v) for v in k) for k in keys}
+
+
+@pytest.fixture(scope="module")
+def contact_state():
+    """two-cube scene (FP64) advanced by the oracle into first contact"""
+    s = scenes.two_cubes(0)
+    o = O.Oracle(s)
+    o.step(5)
+    x, v = o.get_state()
+    keys, lam, gam = o.active_get()
+    assert len(keys) > 50
+    return s, x, v, keys, lam, gam
+
+
+def make_pair(s, x, v, keys, lam, gam, precision=0):
+    p = scenes.Params(**{**s.params.__dict__, "precision": precision})
+    sim = B.Sim(s, p)
+    B.bf_set_state(sim.h, x, v)
+    B.bf_set_active_set(sim.h, keys, lam, gam)
+    o = O.Oracle(s, p)
+    o.set_state(x, v)
+    o.active_set(keys, lam, gam)
+    return sim, o
+
+
+def test_xtilde_mu_linearize_assemble(torch_cuda, contact_state):
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    sim, o = make_pair(s, x, v, keys, lam, gam)
+    xt_o = o.xtilde()
+    xt_g = torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda")
+    B.bf_xtilde(sim.h, xt_g)
+    assert np.abs(host(xt_g) - xt_o).max() <= 1e-15
+    mu_o = o.mu_init(x, xt_o)
+    mu_g = B.bf_mu_init(sim.h, dev(torch, xt_o), dev(torch, x))
+    assert mu_g == pytest.approx(mu_o, rel=1e-10)
+    # linearisation at x
+    d_o, g_o = o.linearize(x)
+    d_g = torch.zeros(len(keys), dtype=torch.float64, device="cuda")
+    g_g = torch.zeros((len(keys), 12), dtype=torch.float64, device="cuda")
+    B.bf_linearize(sim.h, dev(torch, x), d_g, g_g)
+    assert np.abs(host(d_g) - d_o).max() <= 1e-12 * max(1.0, np.abs(d_o).max())
+    assert np.abs(host(g_g) - g_o).max() <= 1e-9
+    # gradient and Hessian action at a perturbed xhat
+    rng = np.random.default_rng(1)
+    xh = x + (0.5 * (xt_o - x) + 2e-4 * rng.standard_normal(x.shape)) * (s.dirichlet == 0)[:, None]
+    E_o, G_o = o.assemble(xt_o, x, xh)
+    G_g = torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda")
+    E_g = B.bf_assemble(sim.h, dev(torch, xt_o), dev(torch, x), dev(torch, xh), G_g)
+    assert np.abs(host(G_g) - G_o).max() <= 1e-9 * np.abs(G_o).max()
+    for k in range(3):
+        w = rng.standard_normal((s.nv, 3))
+        y_o = o.hess_apply(w)
+        y_g = torch.zeros_like(G_g)
+        B.bf_hess_apply(sim.h, dev(torch, w), y_g)
+        free = s.dirichlet == 0
+        assert np.abs(host(y_g)[free] - y_o[free]).max() <= 1e-9 * np.abs(y_o[free]).max()
+    # AL energy with the slacks of this assembly
+    L_o = o.energy_L(xt_o, x, xh, o.slacks())
+    L_g = B.bf_energy(sim.h, dev(torch, xt_o), dev(torch, x), dev(torch, xh))
+    assert L_g == pytest.approx(L_o, rel=1e-11, abs=1e-15)
+    sim.close()
+
+
+def test_pcg_solution(torch_cuda, contact_state):
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    sim, o = make_pair(s, x, v, keys, lam, gam)
+    xt = o.xtilde()
+    o.mu_init(x, xt)
+    B.bf_mu_init(sim.h, dev(torch, xt), dev(torch, x))
+    o.linearize(x)
+    B.bf_linearize(sim.h, dev(torch, x))
+    E_o, G_o = o.assemble(xt, x, x)
+    G_g = torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda")
+    B.bf_assemble(sim.h, dev(torch, xt), dev(torch, x), dev(torch, x), G_g)
+    b = -G_o
+    H = o.hess_dense()
+    ref = np.linalg.solve(H, b.reshape(-1))
+    for tol in (1e-6, 1e-10):
+        xg = torch.zeros_like(G_g)
+        it, _ = B.bf_pcg(sim.h, dev(torch, b), xg, tol, 100000)
+        p_o, it_o = o.pcg(b, tol=tol, maxit=100000)
+        pg = host(xg).reshape(-1)
+        assert np.linalg.norm(H @ pg - b.reshape(-1)) <= tol * np.linalg.norm(b) * 1.01
+        assert abs(it - it_o) <= max(2, it_o // 20)
+        assert np.linalg.norm(pg - ref) <= tol * np.linalg.cond(H) * np.linalg.norm(ref)
+    sim.close()
+
+
+def test_accd_bit_exact(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(7)
+    for ptype in (0, 1):
+        n = 4000
+        x0 = rng.standard_normal((n, 12)) * 0.1
+        x1 = x0 + rng.standard_normal((n, 12)) * 0.12
+        toi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        B.bf_accd(ptype, dev(torch, x0), dev(torch, x1), 0.1, toi)
+        tg = host(toi)
+        to = np.array([O.accd(ptype, x0[i], x1[i]) for i in range(n)])
+        assert (np.isinf(tg) == np.isinf(to)).all()
+        fin = np.isfinite(to)
+        assert fin.sum() > 50
+        assert (tg[fin] == to[fin]).all(), np.abs(tg[fin] - to[fin]).max()
+
+
+def contact_motion(s, x, seed=0, scale=3e-3):
+    rng = np.random.default_rng(seed)
+    free = (s.dirichlet == 0)[:, None]
+    return x + free * (scale * rng.standard_normal(x.shape) + np.array([0, 0, -2.0 * scale]))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_ccd_hits_and_alpha(torch_cuda, contact_state, seed):
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    sim, o = make_pair(s, x, v, keys, lam, gam)
+    x1 = contact_motion(s, x, seed)
+    k_o, t_o = o.ccd_hits(x, x1)
+    k_g, t_g = B.bf_ccd_hits(sim.h, dev(torch, x), dev(torch, x1))
+    assert len(k_o) > 20
+    A = {tuple(k): t for k, t in zip(k_o.tolist(), t_o)}
+    Bm = {tuple(k): t for k, t in zip(k_g.tolist(), t_g)}
+    assert A.keys() == Bm.keys()
+    assert all(Bm[k] == A[k] for k in A)  # bit-exact TOIs
+    a_o = o.max_step_size(x, x1)
+    a_g = B.bf_max_step_size(sim.h, dev(torch, x), dev(torch, x1))
+    assert a_g == a_o
+    sim.close()
+
+
+def test_update_active_set(torch_cuda, contact_state):
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    # drop some pairs and decay others so that adding and pruning both happen
+    sel = np.arange(len(keys)) % 3 != 0
+    gam2 = gam.copy()
+    gam2[::5] = 0.005
+    sim, o = make_pair(s, x, v, keys[sel], lam[sel], gam2[sel])
+    x1 = contact_motion(s, x, 3)
+    n_o = o.update_active_set(x, x1)
+    n_g = B.bf_update_active_set(sim.h, dev(torch, x), dev(torch, x1))
+    ko, lo, go = o.active_get()
+    kg, lg, gg = B.bf_get_active_set(sim.h)
+    assert n_o == n_g == len(ko) == len(kg)
+    assert keyset(ko) == keyset(kg)
+    Lo = {tuple(k): (l, g) for k, l, g in zip(ko.tolist(), lo, go)}
+    Lg = {tuple(k): (l, g) for k, l, g in zip(kg.tolist(), lg, gg)}
+    assert all(Lo[k] == Lg[k] for k in Lo)
+    sim.close()
+
+
+def test_solve_subproblem(torch_cuda, contact_state):
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    sim, o = make_pair(s, x, v, keys, lam, gam)
+    xt = o.xtilde()
+    mu = o.mu_init(x, xt)
+    B.bf_set_mu(sim.h, mu, s.params.delta)
+    xh_o, nn_o, cg_o, lsf_o = o.solve_subproblem(xt, x, x)
+    xh_g = dev(torch, x)
+    nn_g, cg_g = B.bf_solve_subproblem(sim.h, dev(torch, xt), dev(torch, x), xh_g)
+    diag = s.bbox_diag()
+    assert nn_g == nn_o
+    assert np.abs(host(xh_g) - xh_o).max() <= 1e-9 * diag
+    ko, lo, go = o.active_get()
+    kg, lg, gg = B.bf_get_active_set(sim.h)
+    assert (ko == kg).all()
+    assert np.abs(lg - lo).max() <= 1e-7 * max(1e-12, np.abs(lo).max())
+    assert (gg == go).all()
+    sim.close()
+
+
+@pytest.mark.parametrize("start", [0, 4, 6])
+def test_one_step_from_oracle_state(torch_cuda, start):
+    s = scenes.two_cubes(0)
+    o = O.Oracle(s)
+    if start:
+        o.step(start)
+    x, v = o.get_state()
+    keys, lam, gam = o.active_get()
+    sim = B.Sim(s)
+    B.bf_set_state(sim.h, x, v)
+    B.bf_set_active_set(sim.h, keys, lam, gam)
+    st_o = o.step(1)[1][0]
+    _, st_g = sim.step(1)
+    xo, vo = o.get_state()
+    xg, vg = sim.state()
+    diag = s.bbox_diag()
+    assert np.abs(xg - xo).max() <= 1e-6 * diag
+    assert st_g[0]["outer_iters"] == st_o["outer_iters"]
+    ko, _, _ = o.active_get()
+    kg, _, _ = B.bf_get_active_set(sim.h)
+    assert keyset(ko) == keyset(kg)
+    sim.close()
+
+
+def test_trajectory_fp64(torch_cuda):
+    s = scenes.two_cubes(0)
+    o = O.Oracle(s)
+    sim = B.Sim(s)
+    diag = s.bbox_diag()
+    errs = []
+    for step in range(s.n_steps):
+        o.step(1)
+        sim.step(1)
+        xo, _ = o.get_state()
+        xg, _ = sim.state()
+        errs.append(np.abs(xg - xo).max() / diag)
+    print("per-step max error / bbox diagonal:", ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-6
+    sim.close()
+
+
+def test_trajectory_mixed(torch_cuda):
+    s = scenes.two_cubes(0, precision=1)
+    p64 = scenes.Params(**{**s.params.__dict__, "precision": 0})
+    o = O.Oracle(s, p64)
+    sim = B.Sim(s)
+    diag = s.bbox_diag()
+    errs = []
+    for step in range(s.n_steps):
+        o.step(1)
+        sim.step(1)
+        xo, _ = o.get_state()
+        xg, _ = sim.state()
+        errs.append(np.abs(xg - xo).max() / diag)
+    print("mixed per-step max error / bbox diagonal:", ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-4
+    sim.close()
+
+
+def test_step_host_matches_device_path(torch_cuda):
+    s = scenes.two_cubes(1)
+    a = B.Sim(s)
+    b = B.Sim(s)
+    a.step(6)
+    x, v = s.x0.copy(), s.v0.copy()
+    xo, vo = np.zeros_like(x), np.zeros_like(v)
+    for i in range(6):
+        B.bf_step_host(b.h, x, v, xo, vo)
+        x, v = xo.copy(), vo.copy()
+    xa, va = a.state()
+    assert np.abs(xa - xo).max() <= 1e-12
+    a.close()
+    b.close()
+
+
+def test_free_fall_and_no_obstacles(torch_cuda):
+    s = scenes.single_cube(seed=3, cells=3, v0=(0.2, 0.1, -0.3))
+    sim = B.Sim(s)
+    _, st = sim.step(1)
+    assert st[0]["outer_iters"] == 2 and st[0]["n_contacts"] == 0
+    x, v = sim.state()
+    h, g = s.params.dt, np.array(s.params.gravity)
+    assert np.abs(x - (s.x0 + h * s.v0 + h * h * g)).max() <= 1e-9
+    sim.close()
+
+
+def test_mixed_assembly_full_size_sampled(torch_cuda):
+    """eight-cube scene at full size (196,608 tets, FP32 Hessian blocks):
+    the FP64 gradient and the FP32 Hessian action agree with the oracle."""
+    torch = torch_cuda
+    s = scenes.eight_cubes(0)
+    p64 = scenes.Params(**{**s.params.__dict__, "precision": 0})
+    o = O.Oracle(s, p64)
+    sim = B.Sim(s)
+    x = s.x0
+    xt = o.xtilde()
+    rng = np.random.default_rng(2)
+    xh = x + 3e-4 * rng.standard_normal(x.shape) * (s.dirichlet == 0)[:, None]
+    mu = o.mu_init(xh, xt)
+    mu_g = B.bf_mu_init(sim.h, dev(torch, xt), dev(torch, xh))
+    assert mu_g == pytest.approx(mu, rel=1e-5)
+    B.bf_set_mu(sim.h, mu, s.params.delta)
+    E_o, G_o = o.assemble(xt, x, xh)
+    G_g = torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda")
+    B.bf_assemble(sim.h, dev(torch, xt), dev(torch, x), dev(torch, xh), G_g)
+    assert np.abs(host(G_g) - G_o).max() <= 1e-9 * np.abs(G_o).max()
+    w = rng.standard_normal((s.nv, 3))
+    y_o = o.hess_apply(w)
+    y_g = torch.zeros_like(G_g)
+    B.bf_hess_apply(sim.h, dev(torch, w), y_g)
+    free = s.dirichlet == 0
+    assert np.abs(host(y_g)[free] - y_o[free]).max() <= 1e-5 * np.abs(y_o[free]).max()
+    sim.close()
+
+
+def test_ccd_full_size(torch_cuda):
+    """eight-cube scene: a falling motion of one time step; hit sets and
+    TOIs equal the oracle's."""
+    torch = torch_cuda
+    s = scenes.eight_cubes(0)
+    o = O.Oracle(s)
+    sim = B.Sim(s)
+    x = s.x0
+    rng = np.random.default_rng(5)
+    free = (s.dirichlet == 0)[:, None]
+    x1 = x + free * (np.array([0.0, 0.0, -0.07]) + 2e-3 * rng.standard_normal(x.shape))
+    k_o, t_o = o.ccd_hits(x, x1)
+    k_g, t_g = B.bf_ccd_hits(sim.h, dev(torch, x), dev(torch, x1))
+    assert len(k_o) > 100
+    A = {tuple(k): t for k, t in zip(k_o.tolist(), t_o)}
+    Bm = {tuple(k): t for k, t in zip(k_g.tolist(), t_g)}
+    assert A.keys() == Bm.keys()
+    assert all(Bm[k] == A[k] for k in A)
+    sim.close()
+
+
+def test_empty_and_edge_cases(torch_cuda):
+    torch = torch_cuda
+    s = scenes.single_cube(seed=0, cells=1, with_ground=True, z=0.3)
+    sim = B.Sim(s)
+    # empty active set: update with no motion adds nothing
+    x = dev(torch, s.x0)
+    assert B.bf_update_active_set(sim.h, x, x) == 0
+    assert B.bf_max_step_size(sim.h, x, x) == 1.0
+    k, l, g = B.bf_get_active_set(sim.h)
+    assert len(k) == 0
+    # unknown key is rejected, bad sizes are rejected
+    with pytest.raises(B.BfError):
+        B.bf_set_active_set(sim.h, np.array([[0, 0, 1, 2, 3]]), np.zeros(1), np.ones(1))
+    toi = torch.zeros(0, dtype=torch.float64, device="cuda")
+    B.bf_accd(0, toi, toi, 0.1, toi)
+    sim.close()
