@@ -225,6 +225,20 @@ int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double 
  * milliseconds (host int64 launches[n], double ms[n]); names[n] points to
  * static strings.  Returns the number of timed kernels. */
 int bf_enable_timers(bf_scene *scene, int32_t on);
+/* PCG execution.  0 = three launches per iteration with the scalar
+ * recurrences kept on the device.  1..15 = one persistent cooperative
+ * launch per solve with two grid barriers per iteration and up to `mode`
+ * CTAs per SM (default 1), keeping the matrix in shared memory when it
+ * fits; adding 16 forbids the shared-memory copy (blocks streamed from
+ * global memory).  Same arithmetic in every mode. */
+int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
+
+/* Configuration of the persistent PCG chosen at the scene's first solve
+ * (host int32[8]): mode, CTAs, threads per CTA, shared memory bytes per
+ * CTA, matrix resident in shared memory (0/1), max rows, max blocks and
+ * max window vertices per CTA (zeros before the first solve). */
+int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
+
 /* Number of this library's own kernel launches issued for the scene since
  * creation (sorts and scans done by CUB are not counted); *n host. */
 int bf_get_launch_count(bf_scene *scene, int64_t *n);

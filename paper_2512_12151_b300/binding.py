@@ -102,6 +102,8 @@ def lib():
         "bf_accd": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_enable_timers": [_P, C.c_int32],
         "bf_get_launch_count": [_P, C.POINTER(C.c_int64)],
+        "bf_set_pcg_mode": [_P, C.c_int32],
+        "bf_get_pcg_config": [_P, _P],
         "bf_get_timers": [_P, C.c_int32, _P, _P, _P],
     }
     for name, args in sig.items():
@@ -339,6 +341,17 @@ def bf_accd(ptype, x0, x1, s, toi, stream=None):
 
 def bf_enable_timers(h, on=True):
     _check("bf_enable_timers", lib().bf_enable_timers(h, int(on)))
+
+
+def bf_set_pcg_mode(h, mode):
+    _check("bf_set_pcg_mode", lib().bf_set_pcg_mode(h, mode))
+
+
+def bf_get_pcg_config(h):
+    cfg = np.zeros(8, np.int32)
+    _check("bf_get_pcg_config", lib().bf_get_pcg_config(h, _np_ptr(cfg)))
+    return dict(zip(("mode", "ctas", "threads", "smem_bytes", "resident", "max_rows", "max_blocks", "max_window"),
+                    cfg.tolist()))
 
 
 def bf_get_launch_count(h):

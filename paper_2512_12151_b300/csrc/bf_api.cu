@@ -65,7 +65,10 @@ int sync_flags(Scene &S)
 // timers
 // ---------------------------------------------------------------------------
 static const char *kTimerNames[T_N] = {"elastic_grad_hess", "spmv_bsr_contact", "pcg_update", "pcg_direction",
-                                       "contact_assemble", "energy", "ccd_narrow_accd", "lbvh_build"};
+                                       "contact_assemble", "energy", "ccd_narrow_accd", "lbvh_build",
+                                       "pcg_persistent", "pcg_phase_spmv", "pcg_phase_reduce1",
+                                       "pcg_phase_update", "pcg_phase_reduce2", "pcg_phase_stage_cum",
+                                       "pcg_phase_rows_cum", "pcg_phase_contact_cum"};
 
 ScopedTimer::ScopedTimer(Scene &s, int tid) : S(&s), id(tid)
 {
@@ -135,7 +138,12 @@ __global__ void k_set_double(double *p, double v) { *p = v; }
 static int partials_reserve(Scene &S)
 {
     const long long work = (long long)S.nnzb + S.nt + S.nv + S.ccap + 1024;
-    const int need = 2 * cdiv(work, kThreads) + 64;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // per-phase grids need 2 values per CTA; the persistent PCG 3 per
+    // co-resident CTA (at most 8 per SM)
+    const int need = std::max(2 * cdiv(work, kThreads), 3 * 8 * std::max(nsm, 1)) + 64;
     if (need <= S.npartials) return BF_OK;
     if (S.partials) dev_free(S, S.partials);
     S.partials = (double *)dev_alloc(S, need * sizeof(double));
@@ -464,6 +472,45 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         auto b = S.h_col.begin() + S.h_rowptr[r], e = S.h_col.begin() + S.h_rowptr[r + 1];
         return (int)(std::lower_bound(b, e, c) - S.h_col.begin());
     };
+    // full-row view: for row r, its diagonal and upper blocks (r, c) and the
+    // lower blocks (c, r) stored in row c, transposed
+    {
+        std::vector<int> cnt(nv, 0);
+        for (int k = 0; k < S.nnzb; ++k) {
+            cnt[rowid[k]]++;
+            if (S.h_col[k] != rowid[k]) cnt[S.h_col[k]]++;
+        }
+        S.h_frowptr.assign(nv + 1, 0);
+        for (int v = 0; v < nv; ++v) S.h_frowptr[v + 1] = S.h_frowptr[v] + cnt[v];
+        S.nfull = S.h_frowptr[nv];
+    }
+    std::vector<int> fnbr(S.nfull), fblk(S.nfull);
+    {
+        std::vector<int> fill(S.h_frowptr.begin(), S.h_frowptr.end() - 1);
+        for (int k = 0; k < S.nnzb; ++k) {  // rows in order, so each row's entries end up sorted by neighbour
+            const int r = rowid[k], c = S.h_col[k];
+            fnbr[fill[r]] = c;
+            fblk[fill[r]++] = k;
+        }
+        // lower blocks, appended after each row's upper ones would break
+        // neighbour order; insert them and sort each row by neighbour
+        for (int k = 0; k < S.nnzb; ++k) {
+            const int r = rowid[k], c = S.h_col[k];
+            if (r == c) continue;
+            fnbr[fill[c]] = r;
+            fblk[fill[c]++] = k | (int)0x80000000u;
+        }
+        for (int v = 0; v < nv; ++v) {
+            const int b = S.h_frowptr[v], e = S.h_frowptr[v + 1];
+            std::vector<std::pair<int, int>> tmp;
+            for (int i = b; i < e; ++i) tmp.push_back({fnbr[i], fblk[i]});
+            std::sort(tmp.begin(), tmp.end());
+            for (int i = b; i < e; ++i) {
+                fnbr[i] = tmp[i - b].first;
+                fblk[i] = tmp[i - b].second;
+            }
+        }
+    }
     std::vector<int> tblk(10 * (size_t)nt);
     for (int e = 0; e < nt; ++e) {
         const int *t = m->tets + 4 * e;
@@ -503,12 +550,17 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     BF_ALLOC(S.col, int, S.nnzb);
     BF_ALLOC(S.rowid, int, S.nnzb);
     BF_ALLOC(S.diagblk, int, nv);
+    BF_ALLOC(S.frowptr, int, nv + 1);
+    BF_ALLOC(S.fnbr, int, S.nfull);
+    BF_ALLOC(S.fblk, int, S.nfull);
     if (S.prm.precision == BF_PREC_MIXED) {
         BF_ALLOC(S.valf, float, 9 * (size_t)S.nnzb);
         BF_ALLOC(S.pinvf, float, 9 * (size_t)nv);
         BF_ALLOC(S.cg_pf, float, n3);
         BF_ALLOC(S.cg_qf, float, n3);
         BF_ALLOC(S.cg_zf, float, n3);
+        BF_ALLOC(S.cg_pf2, float, n3);
+        BF_ALLOC(S.cg_qcf, float, n3);
     } else {
         BF_ALLOC(S.val, double, 9 * (size_t)S.nnzb);
         BF_ALLOC(S.pinv, double, 9 * (size_t)nv);
@@ -522,6 +574,9 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     BF_ALLOC(S.cg_q, double, n3);
     BF_ALLOC(S.cg_z, double, n3);
     BF_ALLOC(S.pdir, double, n3);
+    BF_ALLOC(S.cg_p2, double, n3);
+    BF_ALLOC(S.cg_qc, double, n3);
+    BF_ALLOC(S.bar, unsigned, 4);
     BF_ALLOC(S.counter, unsigned, 4);
     BF_ALLOC(S.dscal, double, S_NSCAL);
     BF_ALLOC(S.dflag, int, F_NFLAG);
@@ -553,6 +608,10 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     up(S.col, S.h_col.data(), S.nnzb * 4);
     up(S.rowid, rowid.data(), S.nnzb * 4);
     up(S.diagblk, diagblk.data(), nv * 4);
+    up(S.frowptr, S.h_frowptr.data(), (nv + 1) * 4);
+    up(S.fnbr, fnbr.data(), (size_t)S.nfull * 4);
+    S.h_fnbr = fnbr;
+    up(S.fblk, fblk.data(), (size_t)S.nfull * 4);
     up(S.sv, S.h_sv.data(), S.nsv * 4);
     up(S.st, S.h_st.data(), S.h_st.size() * 4);
     up(S.se, S.h_se.data(), S.h_se.size() * 4);
@@ -908,7 +967,7 @@ int bf_get_bsr(bf_scene *scene, int32_t *row_ptr, int32_t *col, double *val)
         const int st = check_cuda(cudaStreamSynchronize(S.stream));
         if (st) return st;
         for (int k = 0; k < S.nnzb; ++k)
-            for (int e = 0; e < 9; ++e) val[9 * (size_t)k + e] = planes[(size_t)e * S.nnzb + k];
+            for (int e = 0; e < 9; ++e) val[9 * (size_t)k + e] = planes[9 * (size_t)k + e];
     }
     return BF_OK;
 }
@@ -1003,6 +1062,34 @@ int bf_enable_timers(bf_scene *scene, int32_t on)
         S.t_launch[i] = 0;
         S.t_ms[i] = 0.0;
     }
+    return BF_OK;
+}
+
+int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
+{
+    SCENE_OR_ARG(scene);
+    if (mode < 0 || mode > 32) return BF_E_ARG;
+    S.pcg_mode = mode == 0 ? 0 : 1;
+    if (mode > 0) {
+        S.pcg_ctas_per_sm = mode & 15;
+        S.pcg_allow_resident = (mode & 16) ? 0 : 1;
+        S.pcg_grid = 0;  // recomputed at the next solve
+    }
+    return BF_OK;
+}
+
+int bf_get_pcg_config(bf_scene *scene, int32_t *cfg)
+{
+    SCENE_OR_ARG(scene);
+    if (!cfg) return BF_E_ARG;
+    cfg[0] = S.pcg_mode;
+    cfg[1] = S.pcg_grid;
+    cfg[2] = S.pcg_block;
+    cfg[3] = S.pcg_smem;
+    cfg[4] = S.pcg_resident;
+    cfg[5] = S.pcg_max_rows;
+    cfg[6] = S.pcg_max_ent;
+    cfg[7] = S.pcg_max_win;
     return BF_OK;
 }
 

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
                 for (int c = 0; c < 3; ++c) {
                     const HT h = sc * (T1[r][0] * U[c][0] + T1[r][1] * U[c][1] + T1[r][2] * U[c][2]);
                     const int ent = tr ? (3 * c + r) : (3 * r + c);
-                    atomic_add_val(val + (size_t)ent * nnzb + blk, (double)h);
+                    atomic_add_val(val + 9 * (size_t)blk + ent, (double)h);
                 }
         }
 }
@@ -348,7 +348,7 @@ __global__ void k_vertex_init(int nv, int nnzb, const int *__restrict__ diagblk,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         grad[3 * a + c] = d ? 0.0 : m * (xh[3 * a + c] - xt[3 * a + c]);
-        val[(size_t)(4 * c) * nnzb + k] = (MT)m;
+        val[9 * (size_t)k + 4 * c] = (MT)m;
     }
 #pragma unroll
     for (int e = 0; e < 9; ++e) cdiag[9 * (size_t)a + e] = 0.0;
@@ -377,7 +377,7 @@ __global__ void k_max_diag(int nv, int nnzb, const int *__restrict__ diagblk, co
     double m = 0.0;
     if (a < nv && !dir[a]) {
         const int k = diagblk[a];
-        for (int c = 0; c < 3; ++c) m = fmax(m, (double)val[(size_t)(4 * c) * nnzb + k]);
+        for (int c = 0; c < 3; ++c) m = fmax(m, (double)val[9 * (size_t)k + 4 * c]);
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_pos(out, m);

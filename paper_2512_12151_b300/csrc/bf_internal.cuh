@@ -6,10 +6,11 @@
 //    volume; tblk: for each tet its 10 upper 3x3 blocks (i' <= j') as BSR
 //    block indices, bit 31 set when the block is stored transposed;
 //  - Hessian: upper block-sparse rows (diagonal + upper blocks of the
-//    elastic / mass pattern), values as 9 SoA planes val[e * nnzb + k]
-//    (FP64, or FP32 in mixed precision) so that consecutive threads read
-//    consecutive addresses; contact terms stay rank-1 per pair
-//    (mu gamma_i g_i g_i^T) and are applied matrix-free;
+//    elastic / mass pattern), 3x3 blocks stored contiguously (9 values,
+//    FP64, or FP32 in mixed precision); a full-row view (frowptr, fnbr,
+//    fblk: every block of a vertex row, upper ones and transposed lower
+//    ones) serves the row-gather SpMV of the PCG; contact terms stay rank-1
+//    per pair (mu gamma_i g_i g_i^T) and are applied matrix-free;
 //  - active set: SoA arrays (type, prim a, prim b, 4 vertex ids, lambda,
 //    gamma, d, 12 gradient entries, slack, free-vertex mask).
 #pragma once
@@ -28,7 +29,9 @@ enum { PT = 0, EE = 1 };
 // device scalar slots (dscal)
 enum {
     S_RZ = 0, S_BB, S_ALPHA, S_BETA, S_RR, S_PQ, S_E0, S_E1, S_MU, S_TOI, S_DOT, S_MAXDIAG,
-    S_NSCAL = 32
+    S_T_SPMV, S_T_RED1, S_T_UPD, S_T_RED2, S_RES = 16,  // S_RES..S_RES+23: reduction accumulators
+    S_T_STAGE = 40, S_T_ROWS, S_T_CONTACT,
+    S_NSCAL = 48
 };
 // device flag slots (dflag)
 enum {
@@ -36,10 +39,11 @@ enum {
     F_NFLAG = 32
 };
 // error bits in dflag[F_ERR]
-enum { ERR_NONFINITE = 1, ERR_CAND_OVERFLOW = 2, ERR_HIT_OVERFLOW = 4, ERR_PQ = 8 };
+enum { ERR_NONFINITE = 1, ERR_CAND_OVERFLOW = 2, ERR_HIT_OVERFLOW = 4, ERR_PQ = 8, ERR_BARRIER = 16 };
 
 enum TimerId { T_ELASTIC = 0, T_SPMV, T_PCG_UPDATE, T_PCG_DIR, T_CONTACT, T_ENERGY, T_CCD_NARROW,
-               T_BVH, T_N };
+               T_BVH, T_PCG_PERSISTENT, T_PCG_PH_SPMV, T_PCG_PH_RED1, T_PCG_PH_UPD, T_PCG_PH_RED2,
+               T_PCG_PH_STAGE, T_PCG_PH_ROWS, T_PCG_PH_CONTACT, T_N };
 
 struct LBVH {
     int n = 0, cap = 0;
@@ -80,6 +84,12 @@ struct Scene {
     double *B = nullptr, *vol = nullptr, *emu = nullptr, *elam = nullptr;
     int *tblk = nullptr;
     int *rowptr = nullptr, *col = nullptr, *rowid = nullptr, *diagblk = nullptr;
+    int nfull = 0;
+    int *frowptr = nullptr, *fnbr = nullptr, *fblk = nullptr;  // full-row view
+    std::vector<int> h_frowptr;
+    int *part = nullptr;      // persistent PCG: CTA row ranges (grid + 1)
+    int pcg_smem = 0;         // dynamic shared memory of the persistent PCG (bytes)
+    int pcg_resident = 0;     // 1: matrix resident in shared memory
     double *val = nullptr;  // 9 planes FP64
     float *valf = nullptr;  // 9 planes FP32 (mixed)
     double *grad = nullptr;
@@ -89,7 +99,18 @@ struct Scene {
     // PCG work vectors (n = 3 nv)
     double *cg_x = nullptr, *cg_r = nullptr, *cg_b = nullptr, *cg_p = nullptr, *cg_q = nullptr,
            *cg_z = nullptr, *pdir = nullptr;
-    float *cg_pf = nullptr, *cg_qf = nullptr, *cg_zf = nullptr;
+    float *cg_pf = nullptr, *cg_qf = nullptr, *cg_zf = nullptr, *cg_pf2 = nullptr, *cg_qcf = nullptr;
+    double *cg_qc = nullptr;  // contact part of H p (accumulated with atomics)
+    double *cg_p2 = nullptr;  // second direction buffer of the persistent PCG
+    unsigned *bar = nullptr;  // grid barrier: count, generation
+    int pcg_grid = 0;         // co-resident CTAs of the persistent PCG (0 = not set up)
+    int pcg_mode = 1;         // 1 = persistent cooperative kernel, 0 = one launch per phase
+    int pcg_ctas_per_sm = 1;  // persistent PCG: CTAs per SM (capped by occupancy)
+    int pcg_allow_resident = 1;  // persistent PCG may keep the matrix in shared memory
+    int pcg_max_rows = 0, pcg_max_ent = 0, pcg_max_win = 0, pcg_block = 256;
+    unsigned short *pcg_erow = nullptr;  // CTA-local row of every full-row entry
+    int *win = nullptr;       // persistent PCG: staged vertex window per CTA
+    std::vector<int> h_fnbr;
     // reductions
     double *partials = nullptr;
     int npartials = 0;
@@ -154,6 +175,7 @@ void launch_zero(Scene &S, double *p, size_t n);
 void launch_spmv(Scene &S, const double *x, double *y, bool with_dot, const int *done);
 void launch_pinv(Scene &S);
 int run_pcg(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
+int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
 void launch_axpy_to(Scene &S, double *out, const double *a, double r, const double *p, int n);
 void launch_blend(Scene &S, double *xk, const double *xh, double alpha, int n);
 void launch_velocity(Scene &S);

@@ -16,8 +16,8 @@ template <class A, class B>
 using wider_t = typename std::conditional<(sizeof(A) >= sizeof(B)), A, B>::type;
 
 // ---------------------------------------------------------------------------
-// y += H x.  Threads [0, nnzb) own one stored 3x3 block each (SoA planes, so
-// a warp reads 9 coalesced 128-byte lines); the row part is reduced with a
+// y += H x.  Threads [0, nnzb) own one stored 3x3 block each; the row part
+// is reduced with a
 // segmented warp scan (blocks are sorted by row) and the transposed part of
 // off-diagonal blocks is scattered with atomics.  Threads
 // [nnzb, nnzb + nc) own one contact pair: y_a += mu gamma g_a (g . x) over
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(
         const int c = col[tid];
         CT a[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) a[e] = (CT)val[(size_t)e * nnzb + tid];
+        for (int e = 0; e < 9; ++e) a[e] = (CT)val[9 * (size_t)tid + e];
         const CT xc0 = (CT)x[3 * c], xc1 = (CT)x[3 * c + 1], xc2 = (CT)x[3 * c + 2];
         yr0 = a[0] * xc0 + a[1] * xc1 + a[2] * xc2;
         yr1 = a[3] * xc0 + a[4] * xc1 + a[5] * xc2;
@@ -158,7 +158,7 @@ __global__ void k_pinv(int nv, int nnzb, const int *__restrict__ diagblk, const 
     } else {
         const int k = diagblk[a];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) m[e] = (double)val[(size_t)e * nnzb + k] + cdiag[9 * (size_t)a + e];
+        for (int e = 0; e < 9; ++e) m[e] = (double)val[9 * (size_t)k + e] + cdiag[9 * (size_t)a + e];
     }
     const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
     const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
@@ -398,6 +398,7 @@ static int pcg_impl(Scene &S, const MT *val, const MT *pinv, VT *p, VT *q, VT *z
 
 int run_pcg(Scene &S, const double *b, double *x, double tol, int maxit, int *iters)
 {
+    if (S.pcg_mode == 1) return run_pcg_persistent(S, b, x, tol, maxit, iters);
     if (S.prm.precision == BF_PREC_MIXED)
         return pcg_impl<float, float>(S, S.valf, S.pinvf, S.cg_pf, S.cg_qf, S.cg_zf, b, x, tol, maxit, iters);
     return pcg_impl<double, double>(S, S.val, S.pinv, S.cg_p, S.cg_q, S.cg_z, b, x, tol, maxit, iters);

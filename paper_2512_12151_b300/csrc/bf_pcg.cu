@@ -1,0 +1,790 @@
+// Persistent block-Jacobi PCG (section 5.1): one cooperative launch per
+// linear solve, all CTAs co-resident.
+//
+// Work split: CTA c owns the contiguous vertex rows [part[c], part[c+1]),
+// balanced by block count.  It keeps x, r, the row sums q = (H p) and the
+// 3x3 preconditioner of its rows in shared memory for the whole solve and,
+// when they fit in the combined shared memory of the GPU (the "resident"
+// variant), also the blocks of its rows (full-row view: upper blocks and
+// the transposed lower ones), row after row, with its neighbours as 16-bit
+// offsets into the CTA's vertex window, which covers every neighbour of its
+// rows.  Each iteration stages p = z + beta p_old over that window into
+// shared memory (16 bytes per vertex) with coalesced loads; consecutive
+// threads then take consecutive blocks (bank-conflict-free: 9 words per
+// block), reduce the products per row with a segmented warp scan and store
+// each row segment with one shared-memory add, so the SpMV needs no global
+// atomics.  The contact terms
+// mu gamma g g^T p go to a separate vector with global atomics (few pairs,
+// dealt round-robin to the CTAs).
+//
+// Two grid-wide reductions per iteration double as the grid barriers:
+//   A: q = H p, p = z + beta p_old (double-buffered p, so no barrier
+//      separates the direction update from the SpMV); reduce p.q -> alpha
+//   B: x += alpha p, r -= alpha q, z = P r; reduce r.z and r.r -> beta,
+//      convergence test.
+// Every CTA reads the same reduced bits, so all take the same decisions.
+// Every spin has an iteration limit (ERR_BARRIER).  Mixed precision runs the
+// iterations in FP32 (p, q, z, r and the increment of x) with the dot
+// products accumulated in FP64, and makes reliable updates: whenever |r| has
+// dropped by 10x since the last one, or the recurrence signals convergence,
+// x is folded into its FP64 value and r is recomputed as b - H x with FP64
+// vectors (FP32 matrix); convergence is decided on that residual.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "bf_device.cuh"
+#include "bf_internal.cuh"
+
+namespace bf {
+
+constexpr int kPcgMaxThreads = 256;
+
+struct PcgArgs {
+    int nv, nc;
+    const int *part, *win, *frowptr;
+    const unsigned short *erow;
+    const int *fnbr, *fblk;
+    const void *val;
+    const int4 *cv;
+    const double *cg, *cw;
+    const unsigned char *cmask;
+    const void *pinv;
+    const double *b;
+    double *x;
+    void *z, *p0, *p1, *qc;
+    double *qd, *res;
+    unsigned *bar;
+    double tol2;
+    int maxit, max_replace, max_rows, max_ent, max_win;
+    double *dscal;
+    int *dflag;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Block sum of K doubles with few FP64 instructions: every thread parks its
+// values in shared memory, the first (up to four) warps each add a share
+// (lane-strided, then 5 shuffle levels) and thread 0 adds the shares.  The
+// result is valid in thread 0.
+template <int K>
+__device__ __forceinline__ void cta_sum(double (&v)[K])
+{
+    __shared__ double sh[K][kPcgMaxThreads];
+    __shared__ double q4[K][4];
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = min(4, (int)(blockDim.x + 31) >> 5);  // warps taking part
+    const int quarter = ((int)blockDim.x + nw - 1) / nw;
+    if (w < nw) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (int i = lane; i < quarter; i += 32) {
+                const int j = w * quarter + i;
+                if (j < (int)blockDim.x) t += sh[k][j];
+            }
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) q4[k][w] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = q4[k][0];
+            for (int i = 1; i < nw; ++i) t += q4[k][i];
+            v[k] = t;
+        }
+}
+
+// Grid-wide sum of K values that doubles as the grid barrier.
+// Reduction: each CTA adds its block sum to accumulator slot (n % 3) with an
+// FP64 atomic add, n = the count of reductions so far in this launch; CTA 0
+// zeroes slot (n + 1) % 3 before it arrives (that slot was last read before
+// the previous barrier and is next written after this one).  Barrier: one
+// arrival counter whose top bit flips when every CTA has arrived (CTA 0
+// adds 0x80000000 - (gridDim.x - 1), the others 1), with a release on the
+// arrival and acquire loads while spinning (bounded; ERR_BARRIER).
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], double *acc, unsigned &n, unsigned *bar, int *dflag,
+                                            double (&tot)[K])
+{
+    __shared__ int s_ok;
+    cta_sum<K>(v);
+    const unsigned slot = n % 3u, next = (n + 1u) % 3u;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) atomicAdd(acc + 8 * slot + k, v[k]);
+        if (blockIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[8 * next + k] = 0.0;
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
+        int ok = 1;
+        unsigned long long spins = 0;
+        while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
+            if (++spins > (1ull << 28)) {
+                atomicOr(dflag + F_ERR, ERR_BARRIER);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = __ldcg(acc + 8 * slot + k);
+    ++n;
+    const bool ok = s_ok != 0;
+    __syncthreads();
+    return ok;
+}
+
+__device__ __forceinline__ void smem_add(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void smem_add(double *p, double v) { atomicAdd(p, v); }
+
+// Row sums of H u over the CTA's rows, added into s_q (component-major,
+// s_q[c * ldq + row], zeroed by the caller).  Consecutive threads take
+// consecutive entries; the products are reduced per row with a segmented
+// warp scan and each row segment is added to shared memory once.
+// getu(v_rel, out) loads u at window offset v_rel; ent(pos, a) loads the 9
+// block values of entry pos and returns the neighbour's window offset.
+template <class CT, class GetU, class Ent>
+__device__ __forceinline__ void row_sums(int ne, const unsigned short *erow, GetU getu, Ent ent, CT *s_q, int ldq)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < ne; base += blockDim.x) {  // same trip count in every thread
+        const int e = base + threadIdx.x;
+        int row = -1;
+        CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
+        if (e < ne) {
+            row = erow[e];
+            CT a[9], u[3];
+            getu(ent(e, a), u);
+            y0 = a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
+            y1 = a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
+            y2 = a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const CT t0 = __shfl_up_sync(0xffffffffu, y0, o);
+            const CT t1 = __shfl_up_sync(0xffffffffu, y1, o);
+            const CT t2 = __shfl_up_sync(0xffffffffu, y2, o);
+            const int ru = __shfl_up_sync(0xffffffffu, row, o);
+            if (lane >= o && ru == row) {
+                y0 += t0;
+                y1 += t1;
+                y2 += t2;
+            }
+        }
+        const int rn = __shfl_down_sync(0xffffffffu, row, 1);
+        if (row >= 0 && (lane == 31 || rn != row)) {
+            smem_add(s_q + row, y0);
+            smem_add(s_q + ldq + row, y1);
+            smem_add(s_q + 2 * ldq + row, y2);
+        }
+    }
+}
+
+// contact part: y += sum_i mu gamma_i g_i (g_i . u) over the pairs, dealt
+// round-robin to the CTAs (pair i -> CTA i % gridDim.x) so that no CTA
+// carries more than its share; arithmetic in CT, the u^T H_c u share
+// returned in FP64
+template <class CT, class VO, class GetU>
+__device__ __forceinline__ double contact_pass(const PcgArgs &A, GetU getu, VO *y)
+{
+    double dot = 0.0;
+    for (int i = threadIdx.x * gridDim.x + blockIdx.x; i < A.nc; i += gridDim.x * blockDim.x) {
+        const int4 v = A.cv[i];
+        const unsigned char m = A.cmask[i];
+        const int vid[4] = {v.x, v.y, v.z, v.w};
+        const double *g = A.cg + 12 * (size_t)i;
+        CT gl[12], s = CT(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            CT u[3] = {CT(0), CT(0), CT(0)};
+            if (m >> q & 1) getu(vid[q], u);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gl[3 * q + j] = (CT)g[3 * q + j];
+                s += gl[3 * q + j] * u[j];
+            }
+        }
+        const CT t = (CT)A.cw[i] * s;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (m >> q & 1)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) atomicAdd(y + 3 * vid[q] + j, (VO)(t * gl[3 * q + j]));
+        dot += (double)(t * s);
+    }
+    return dot;
+}
+
+template <class T>
+__device__ __forceinline__ void load3v(const T *src, T *u)
+{
+    if (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(src);
+        u[0] = q.x; u[1] = q.y; u[2] = q.z;
+    } else {
+        u[0] = src[0]; u[1] = src[1]; u[2] = src[2];
+    }
+}
+
+// Shared-memory layout of the persistent PCG (byte offsets, 16-byte aligned
+// sections), shared by the kernel and the host-side sizing.
+struct PcgLayout {
+    size_t x, hx, xl, r, q, pinv, p4, val, nbr, erow, total;
+};
+
+__host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
+                                                bool res)
+{
+    PcgLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    const int rt = mixed ? 4 : 8;
+    L.x = take(3 * (size_t)max_rows * 8);
+    L.hx = take(mixed ? 3 * (size_t)max_rows * 8 : 0);
+    L.xl = take(mixed ? 3 * (size_t)max_rows * rt : 0);
+    L.r = take(3 * (size_t)max_rows * rt);
+    L.q = take(3 * (size_t)max_rows * ct);
+    L.pinv = take(9 * (size_t)max_rows * mt);
+    L.p4 = take(4 * (size_t)max_win * ct);
+    L.val = take(res ? 9 * (size_t)max_ent * mt : 0);
+    L.nbr = take(res ? (size_t)max_ent * 2 : 0);
+    L.erow = take(res ? (size_t)max_ent * 2 : 0);
+    L.total = o;
+    return L;
+}
+
+template <class MT, class VT, bool RES>
+__global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
+{
+    using CT = typename std::conditional<(sizeof(MT) >= sizeof(VT)), MT, VT>::type;
+    constexpr bool mixed = sizeof(VT) == 4;
+    using RT = typename std::conditional<mixed, float, double>::type;  // r and the iteration part of x
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MT *__restrict__ gval = (const MT *)A.val;
+    const MT *__restrict__ gpinv = (const MT *)A.pinv;
+    VT *__restrict__ z = (VT *)A.z;
+    VT *__restrict__ qc = (VT *)A.qc;
+    VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
+    const int c = blockIdx.x;
+    const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
+    const int wlo = A.win[2 * c], whi = A.win[2 * c + 1];
+    const int E0 = A.frowptr[r0], ne = A.frowptr[r1] - E0;  // the CTA's full-row entries
+    const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, RES);
+    const int ld = A.max_rows;  // per-row arrays are component-major: a[c * ld + row]
+    double *s_x = (double *)(smem + L.x);
+    double *s_hx = (double *)(smem + L.hx);
+    RT *s_xl = (RT *)(smem + L.xl);
+    RT *s_r = (RT *)(smem + L.r);
+    CT *s_q = (CT *)(smem + L.q);
+    MT *s_pinv = (MT *)(smem + L.pinv);
+    CT *s_p4 = (CT *)(smem + L.p4);
+    MT *s_val = (MT *)(smem + L.val);
+    unsigned short *s_nbr = (unsigned short *)(smem + L.nbr);
+    unsigned short *s_erow = (unsigned short *)(smem + L.erow);
+    const unsigned short *erow = RES ? s_erow : A.erow + E0;
+    for (int i = threadIdx.x; i < 9 * nr; i += blockDim.x) s_pinv[i] = gpinv[9 * (size_t)r0 + i];
+    if (RES) {
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int fe = E0 + e;
+            const int fb = A.fblk[fe];
+            const MT *src = gval + 9 * (size_t)(fb & 0x7fffffff);
+            MT *dst = s_val + 9 * e;
+            if (fb < 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) dst[3 * i + j] = src[3 * j + i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) dst[i] = src[i];
+            }
+            s_nbr[e] = (unsigned short)(A.fnbr[fe] - wlo);
+            s_erow[e] = A.erow[fe];
+        }
+    }
+    __syncthreads();
+    // block values of local entry pos (row-major, lower blocks transposed);
+    // returns the neighbour's window offset
+    auto ent = [&](int pos, CT *a) -> int {
+        if (RES) {
+            const MT *t = s_val + 9 * pos;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) a[i] = (CT)t[i];
+            return s_nbr[pos];
+        } else {
+            const int fe = E0 + pos;
+            const int fb = __ldg(A.fblk + fe);
+            const MT *src = gval + 9 * (size_t)(fb & 0x7fffffff);
+            if (fb < 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) a[3 * i + j] = (CT)__ldg(src + 3 * j + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a[i] = (CT)__ldg(src + i);
+            }
+            return __ldg(A.fnbr + fe) - wlo;
+        }
+    };
+    // z = P r for row i, and the row's share of r.z
+    auto precond = [&](int i, const RT *rv) -> double {
+        const int a = r0 + i;
+        const MT *P = s_pinv + 9 * i;
+        CT zc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            zc[k] = (CT)P[3 * k] * (CT)rv[0] + (CT)P[3 * k + 1] * (CT)rv[1] + (CT)P[3 * k + 2] * (CT)rv[2];
+            z[3 * a + k] = (VT)zc[k];
+        }
+        if (mixed) return (double)((float)rv[0] * (float)zc[0] + (float)rv[1] * (float)zc[1] + (float)rv[2] * (float)zc[2]);
+        return ((double)rv[0] * (double)zc[0] + (double)rv[1] * (double)zc[1]) + (double)rv[2] * (double)zc[2];
+    };
+    auto rnorm = [&](const RT *rv) -> double {
+        if (mixed) return (double)((float)rv[0] * (float)rv[0] + (float)rv[1] * (float)rv[1] + (float)rv[2] * (float)rv[2]);
+        return ((double)rv[0] * (double)rv[0] + (double)rv[1] * (double)rv[1]) + (double)rv[2] * (double)rv[2];
+    };
+    double t2[2];
+    unsigned nred = 0;  // reductions so far (selects the accumulator slot)
+    unsigned long long tA = 0, tA2 = 0, tB = 0, tB2 = 0, t0 = 0, tS = 0, tR = 0, tC = 0;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    // ---- init: r = b, x = 0, z = P r, p_old = 0, qc = 0 --------------------
+    {
+        double v[2] = {0.0, 0.0};
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+            const int a = r0 + i;
+            RT rv[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                rv[k] = (RT)A.b[3 * a + k];
+                s_r[k * ld + i] = rv[k];
+                s_x[k * ld + i] = 0.0;
+                if (mixed) s_xl[k * ld + i] = RT(0);
+                s_q[k * ld + i] = CT(0);
+                qc[3 * a + k] = VT(0);
+                pb[0][3 * a + k] = VT(0);
+                if (mixed) A.qd[3 * a + k] = 0.0;
+                v[1] += A.b[3 * a + k] * A.b[3 * a + k];  // |b|^2 in FP64
+            }
+            v[0] += precond(i, rv);
+        }
+        if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
+    }
+    double rz = t2[0];
+    const double bb = t2[1];
+    double rr = bb, beta = 0.0, rr_ref = bb;
+    int it = 0, parity = 0, folds = 0, maxit_hit = 0, bad = 0;
+    if (!(bb > 0.0) || !isfinite(bb) || !isfinite(rz)) {
+        bad = !(bb == 0.0);
+        goto finish;
+    }
+    for (;;) {
+        VT *pold = pb[parity], *pnew = pb[parity ^ 1];
+        double pq[1];
+        // ---- phase A: q = H p, p = z + beta p_old ---------------------------
+        {
+            if (timer) t0 = globaltimer();
+            const CT bt = (CT)beta;
+            {  // stage p over the window (coalesced loads issued together)
+                const int nf = 3 * (whi - wlo);
+                const VT *zw = z + 3 * wlo, *pw = pold + 3 * wlo;
+                for (int f0 = threadIdx.x; f0 < nf; f0 += 8 * blockDim.x) {
+                    VT zz[8], pp[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int f = f0 + k * blockDim.x;
+                        zz[k] = f < nf ? __ldcg(zw + f) : VT(0);
+                        pp[k] = f < nf ? __ldcg(pw + f) : VT(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int f = f0 + k * blockDim.x;
+                        if (f < nf) s_p4[4 * (f / 3) + f % 3] = (CT)zz[k] + bt * (CT)pp[k];
+                    }
+                }
+            }
+            __syncthreads();
+            if (timer) tS += globaltimer() - t0;
+            auto getp = [&](int vr, CT *o) { load3v(s_p4 + 4 * vr, o); };
+            row_sums<CT>(ne, erow, getp, ent, s_q, ld);
+            if (timer) tR += globaltimer() - t0;
+            auto getp_g = [&](int v, CT *o) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) o[k] = (CT)__ldcg(z + 3 * v + k) + bt * (CT)__ldcg(pold + 3 * v + k);
+            };
+            double v1[1] = {contact_pass<CT, VT>(A, getp_g, qc)};
+            __syncthreads();
+            if (timer) tC += globaltimer() - t0;
+            CT pqs = CT(0);
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                const int a = r0 + i;
+                CT p[3];
+                load3v(s_p4 + 4 * (a - wlo), p);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) pnew[3 * a + k] = (VT)p[k];
+                pqs += p[0] * s_q[i] + p[1] * s_q[ld + i] + p[2] * s_q[2 * ld + i];
+            }
+            v1[0] += (double)pqs;
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tA += t1 - t0;
+                t0 = t1;
+            }
+            if (!grid_reduce<1>(v1, A.res, nred, A.bar, A.dflag, pq)) return;
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tA2 += t1 - t0;
+                t0 = t1;
+            }
+        }
+        if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
+            bad = rr > A.tol2 * bb;  // a zero direction after convergence is benign
+            goto finish;
+        }
+        // ---- phase B: x, r, z updates ---------------------------------------
+        {
+            const double alpha = rz / pq[0];
+            const RT al = (RT)alpha;
+            double v[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                const int a = r0 + i;
+                VT qg[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) qg[k] = __ldcg(qc + 3 * a + k);
+                CT pc[3];
+                load3v(s_p4 + 4 * (a - wlo), pc);
+                RT rv[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if (mixed) s_xl[k * ld + i] += al * (RT)pc[k];
+                    else s_x[k * ld + i] += alpha * (double)pc[k];
+                    const RT qv = (RT)s_q[k * ld + i] + (RT)qg[k];
+                    rv[k] = s_r[k * ld + i] - al * qv;
+                    s_r[k * ld + i] = rv[k];
+                    s_q[k * ld + i] = CT(0);
+                    qc[3 * a + k] = VT(0);
+                }
+                v[0] += precond(i, rv);
+                v[1] += rnorm(rv);
+            }
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tB += t1 - t0;
+                t0 = t1;
+            }
+            if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
+            if (timer) tB2 += globaltimer() - t0;
+        }
+        ++it;
+        const double rz_old = rz;
+        beta = t2[0] / rz_old;
+        rz = t2[0];
+        rr = t2[1];
+        parity ^= 1;
+        if (!isfinite(rr) || !isfinite(rz)) {
+            bad = 1;
+            goto finish;
+        }
+        bool done = rr <= A.tol2 * bb;
+        if (mixed && folds < A.max_replace && (done || rr <= 0.01 * rr_ref)) {
+            // reliable update: x += x_l in FP64, then r = b - H x with FP64
+            // vectors (FP32 matrix); the direction p is kept and beta rescaled
+            for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double xv = s_x[k * ld + i] + (double)s_xl[k * ld + i];
+                    s_x[k * ld + i] = xv;
+                    s_xl[k * ld + i] = RT(0);
+                    A.x[3 * (r0 + i) + k] = xv;
+                }
+            double dummy[1] = {0.0};
+            if (!grid_reduce<1>(dummy, A.res, nred, A.bar, A.dflag, dummy)) return;
+            auto getx = [&](int vr, double *o) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) o[k] = __ldcg(A.x + 3 * (wlo + vr) + k);
+            };
+            auto ent64 = [&](int pos, double *a) -> int {
+                CT t[9];
+                const int v = ent(pos, t);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) a[k] = (double)t[k];
+                return v;
+            };
+            for (int i = threadIdx.x; i < 3 * ld; i += blockDim.x) s_hx[i] = 0.0;
+            __syncthreads();
+            row_sums<double>(ne, erow, getx, ent64, s_hx, ld);
+            auto getx_g = [&](int v, double *o) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) o[k] = __ldcg(A.x + 3 * v + k);
+            };
+            contact_pass<double, double>(A, getx_g, A.qd);
+            if (!grid_reduce<1>(dummy, A.res, nred, A.bar, A.dflag, dummy)) return;
+            double v[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                const int a = r0 + i;
+                RT rv[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double rh = A.b[3 * a + k] - s_hx[k * ld + i] - __ldcg(A.qd + 3 * a + k);
+                    A.qd[3 * a + k] = 0.0;
+                    v[1] += rh * rh;
+                    rv[k] = (RT)rh;
+                    s_r[k * ld + i] = rv[k];
+                }
+                v[0] += precond(i, rv);
+            }
+            if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
+            ++folds;
+            beta = t2[0] / rz_old;
+            rz = t2[0];
+            rr = t2[1];
+            rr_ref = rr;
+            done = rr <= A.tol2 * bb;
+        }
+        if (done) break;
+        if (it >= A.maxit) {
+            maxit_hit = 1;
+            break;
+        }
+    }
+finish:
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            A.x[3 * (r0 + i) + k] = s_x[k * ld + i] + (mixed ? (double)s_xl[k * ld + i] : 0.0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.dflag[F_ITERS] = it;
+        A.dflag[F_MAXIT] = maxit_hit;
+        A.dflag[F_DONE] = 1;
+        if (bad) A.dflag[F_ERR] |= ERR_NONFINITE;
+        A.dscal[S_RR] = rr;
+        A.dscal[S_BB] = bb;
+        A.dscal[S_RZ] = rz;
+        A.dscal[S_T_SPMV] = 1e-6 * (double)tA;
+        A.dscal[S_T_RED1] = 1e-6 * (double)tA2;
+        A.dscal[S_T_UPD] = 1e-6 * (double)tB;
+        A.dscal[S_T_RED2] = 1e-6 * (double)tB2;
+        A.dscal[S_T_STAGE] = 1e-6 * (double)tS;
+        A.dscal[S_T_ROWS] = 1e-6 * (double)tR;
+        A.dscal[S_T_CONTACT] = 1e-6 * (double)tC;
+    }
+}
+
+// Row ranges of the CTAs (about equal block counts), each CTA's vertex
+// window (its rows and all their neighbours) and the CTA-local row of every
+// full-row entry.
+static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *max_win)
+{
+    const std::vector<int> &fr = S.h_frowptr;
+    const std::vector<int> &fn = S.h_fnbr;
+    std::vector<int> part(grid + 1, S.nv);
+    part[0] = 0;
+    const double per = (double)S.nfull / grid;
+    int r = 0;
+    for (int c = 1; c < grid; ++c) {
+        const double target = per * c;
+        while (r < S.nv && fr[r] < target) ++r;
+        part[c] = std::max(part[c - 1], r);
+    }
+    part[grid] = S.nv;
+    std::vector<int> win(2 * grid);
+    std::vector<unsigned short> erow(S.nfull);
+    int mr = 0, me = 0, mw = 0;
+    for (int c = 0; c < grid; ++c) {
+        const int a = part[c], b = part[c + 1];
+        if (b - a > 65535) return BF_E_CAPACITY;
+        int lo = a, hi = b;
+        for (int v = a; v < b; ++v)
+            for (int e = fr[v]; e < fr[v + 1]; ++e) {
+                erow[e] = (unsigned short)(v - a);
+                lo = std::min(lo, fn[e]);
+                hi = std::max(hi, fn[e] + 1);
+            }
+        if (hi - lo > 65535) return BF_E_CAPACITY;
+        win[2 * c] = lo;
+        win[2 * c + 1] = hi;
+        mr = std::max(mr, b - a);
+        me = std::max(me, fr[b] - fr[a]);
+        mw = std::max(mw, hi - lo);
+    }
+    auto put = [&](auto *&dst, const auto &host) -> int {
+        using T = std::remove_reference_t<decltype(*dst)>;
+        if (dst) dev_free(S, dst);
+        dst = (T *)dev_alloc(S, std::max<size_t>(host.size(), 1) * sizeof(T));
+        if (!dst) return BF_E_OOM;
+        if (!host.empty())
+            cudaMemcpyAsync(dst, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, S.stream);
+        return BF_OK;
+    };
+    int st = put(S.part, part);
+    if (!st) st = put(S.win, win);
+    if (!st) st = put(S.pcg_erow, erow);
+    if (st) return st;
+    *max_rows = mr;
+    *max_ent = me;
+    *max_win = mw;
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+// Chooses the launch: the resident variant when the blocks fit in shared
+// memory at the requested CTAs per SM (falling back to fewer CTAs per SM),
+// else the variant that streams the blocks from global memory.
+template <class MT, class VT>
+static int setup_persistent(Scene &S)
+{
+    using CT = typename std::conditional<(sizeof(MT) >= sizeof(VT)), MT, VT>::type;
+    constexpr bool mixed = sizeof(VT) == 4;
+    int dev = 0, nsm = 0, coop = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return BF_E_CUDA;
+    const int per_sm = std::max(1, S.pcg_ctas_per_sm);
+    for (int res = S.pcg_allow_resident ? 1 : 0; res >= 0; --res) {
+        for (int cps = per_sm; cps >= 1; --cps) {
+            const int grid = nsm * cps;
+            int mr = 0, me = 0, mw = 0;
+            int st = make_partition(S, grid, &mr, &me, &mw);
+            if (st == BF_E_CAPACITY) continue;
+            if (st) return st;
+            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0);
+            if (L.total + 8192 > (size_t)smem_optin) continue;  // static shared memory of the kernel
+            const int block = kPcgMaxThreads;
+            auto kern = res ? k_pcg_persistent<MT, VT, true> : k_pcg_persistent<MT, VT, false>;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
+            if (occ < cps) continue;
+            S.pcg_grid = grid;
+            S.pcg_block = block;
+            S.pcg_smem = (int)L.total;
+            S.pcg_resident = res;
+            S.pcg_max_rows = mr;
+            S.pcg_max_ent = me;
+            S.pcg_max_win = mw;
+            return BF_OK;
+        }
+    }
+    return BF_E_CAPACITY;
+}
+
+template <class MT, class VT>
+static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *p1, VT *qc, VT *z, const double *b,
+                           double *x, double tol, int maxit, int *iters)
+{
+    if (S.pcg_grid == 0) {
+        const int st = setup_persistent<MT, VT>(S);
+        if (st) return st;
+    }
+    const int grid = S.pcg_grid;
+    PcgArgs A;
+    A.nv = S.nv;
+    A.nc = S.nc;
+    A.part = S.part;
+    A.win = S.win;
+    A.frowptr = S.frowptr;
+    A.erow = S.pcg_erow;
+    A.fnbr = S.fnbr;
+    A.fblk = S.fblk;
+    A.val = val;
+    A.cv = S.cv;
+    A.cg = S.cg;
+    A.cw = S.cw;
+    A.cmask = S.cmask;
+    A.pinv = pinv;
+    A.b = b;
+    A.x = x;
+    A.z = z;
+    A.p0 = p0;
+    A.p1 = p1;
+    A.qc = qc;
+    A.qd = S.cg_qc;  // FP64 scratch of the reliable updates (mixed only; qc is FP32 then)
+    A.res = S.dscal + S_RES;
+    A.bar = S.bar;
+    A.tol2 = tol * tol;
+    A.maxit = maxit;
+    A.max_replace = 64;
+    A.max_rows = S.pcg_max_rows;
+    A.max_ent = S.pcg_max_ent;
+    A.max_win = S.pcg_max_win;
+    A.dscal = S.dscal;
+    A.dflag = S.dflag;
+    cudaMemsetAsync(S.bar, 0, 4 * sizeof(unsigned), S.stream);
+    cudaMemsetAsync(S.dscal + S_RES, 0, 24 * sizeof(double), S.stream);  // the three accumulator slots
+    cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
+    void *args[] = {&A};
+    cudaError_t e;
+    {
+        ScopedTimer tm(S, T_PCG_PERSISTENT);
+        const void *kern = S.pcg_resident ? (const void *)k_pcg_persistent<MT, VT, true>
+                                          : (const void *)k_pcg_persistent<MT, VT, false>;
+        e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(S.pcg_block), args, (size_t)S.pcg_smem, S.stream);
+        ++S.n_launch;
+    }
+    if (e != cudaSuccess) return BF_E_CUDA;
+    int st = sync_flags(S);
+    if (st) return st;
+    if (iters) *iters = S.h_flag[F_ITERS];
+    if (S.timers_on) {  // per-phase device time seen by CTA 0 (globaltimer)
+        const int ids[7] = {T_PCG_PH_SPMV, T_PCG_PH_RED1, T_PCG_PH_UPD, T_PCG_PH_RED2, T_PCG_PH_STAGE,
+                            T_PCG_PH_ROWS, T_PCG_PH_CONTACT};
+        const int slots[7] = {S_T_SPMV, S_T_RED1, S_T_UPD, S_T_RED2, S_T_STAGE, S_T_ROWS, S_T_CONTACT};
+        for (int i = 0; i < 7; ++i) {
+            S.t_launch[ids[i]] += S.h_flag[F_ITERS];
+            S.t_ms[ids[i]] += S.h_scal[slots[i]];
+        }
+    }
+    if (S.h_flag[F_ERR] & ERR_BARRIER) return BF_E_CUDA;
+    if (S.h_flag[F_ERR] & ERR_NONFINITE) return BF_E_NONFINITE;
+    return S.h_flag[F_MAXIT] ? BF_E_CG_MAXIT : BF_OK;
+}
+
+// Falls back to the per-phase launches when no persistent configuration
+// fits (a vertex window beyond 16-bit offsets, or too little shared memory).
+int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters)
+{
+    int st;
+    if (S.prm.precision == BF_PREC_MIXED)
+        st = persistent_impl<float, float>(S, S.valf, S.pinvf, S.cg_pf, S.cg_pf2, S.cg_qcf, S.cg_zf, b, x, tol, maxit,
+                                           iters);
+    else
+        st = persistent_impl<double, double>(S, S.val, S.pinv, S.cg_p, S.cg_p2, S.cg_qc, S.cg_z, b, x, tol, maxit,
+                                             iters);
+    if (st == BF_E_CAPACITY && S.pcg_grid == 0) {
+        S.pcg_mode = 0;
+        return run_pcg(S, b, x, tol, maxit, iters);
+    }
+    return st;
+}
+
+}  // namespace bf

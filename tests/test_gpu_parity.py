@@ -365,3 +365,36 @@ def test_empty_and_edge_cases(torch_cuda):
     toi = torch.zeros(0, dtype=torch.float64, device="cuda")
     B.bf_accd(0, toi, toi, 0.1, toi)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, precision):
+    """The persistent cooperative PCG and the one-launch-per-phase PCG run
+    the same recurrences; both solve the oracle's system to the tolerance
+    (mixed precision: FP32 matrix, so the FP64 residual is looser)."""
+    torch = torch_cuda
+    s, x, v, keys, lam, gam = contact_state
+    sim, o = make_pair(s, x, v, keys, lam, gam, precision)
+    xt = o.xtilde()
+    o.mu_init(x, xt)
+    B.bf_mu_init(sim.h, dev(torch, xt), dev(torch, x))
+    o.linearize(x)
+    B.bf_linearize(sim.h, dev(torch, x))
+    _, G_o = o.assemble(xt, x, x)
+    G_g = torch.zeros((s.nv, 3), dtype=torch.float64, device="cuda")
+    B.bf_assemble(sim.h, dev(torch, xt), dev(torch, x), dev(torch, x), G_g)
+    b = -G_o
+    H = o.hess_dense()
+    sols, its = [], []
+    for mode in (1, 0):
+        B.bf_set_pcg_mode(sim.h, mode)
+        xg = torch.zeros_like(G_g)
+        it, _ = B.bf_pcg(sim.h, dev(torch, b), xg, 1e-6, 100000)
+        sols.append(host(xg).reshape(-1))
+        its.append(it)
+    bar = 1e-6 * 1.01 if precision == 0 else 1e-4
+    for p in sols:
+        assert np.linalg.norm(H @ p - b.reshape(-1)) <= bar * np.linalg.norm(b)
+    assert abs(its[0] - its[1]) <= max(2, its[1] // 20)
+    assert np.linalg.norm(sols[0] - sols[1]) <= 1e-4 * np.linalg.norm(sols[1])
+    sim.close()
