@@ -220,6 +220,33 @@ int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double
 int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double s, double *toi,
             void *stream);
 
+/* Allocation-free MaxStepSize over explicit pairs: *alpha = min(1, min_i
+ * TOI_i) over n pairs of one type (0 = PT, 1 = EE), with TOI_i the additive
+ * CCD result that bf_accd returns for the same pair and s (so alpha equals
+ * min(1, min of bf_accd's output) exactly).  x0, x1 (device, n*12), alpha
+ * (device, 1 double).  stream: cudaStream_t or NULL; the call synchronizes
+ * that stream before it returns.
+ *
+ * The paper has no counterpart of this entry point: it exists for callers
+ * that may not allocate device memory once they are running (a host that
+ * hands the library a fixed memory budget, or a real-time loop where an
+ * allocation could block or fail).  It calls no cudaMalloc/cudaFree and no
+ * allocating library routine: its scratch is a static device array of
+ * 8,224 x 8 bytes inside the library, which bounds n to 1,048,576 pairs;
+ * larger n returns BF_E_ARG without launching anything.
+ * - The first call on each device looks up the array's device address and
+ *   caches it, so make that first call (n may be 0) before any stream
+ *   capture.
+ * - The array is shared by all calls on a device and keeps the previous
+ *   call's contents; each call resets the part that must start at zero.
+ *   Calls that overlap on the GPU (other streams, threads or processes
+ *   sharing the context) race on it and may return a wrong alpha: serialize
+ *   them.
+ * Errors: BF_E_ARG (bad type, s outside (0,1), n < 0 or too large, NULL
+ * pointers), BF_E_CUDA. */
+int bf_max_step_size_pairs_noalloc(int32_t type, int32_t n, const double *x0, const double *x1, double s,
+                                   double *alpha, void *stream);
+
 /* Per-kernel CUDA-event timing of the hot kernels during bf_step (off by
  * default).  bf_get_timers fills, per kernel id 0..n-1, launches and total
  * milliseconds (host int64 launches[n], double ms[n]); names[n] points to

@@ -100,6 +100,7 @@ def lib():
         "bf_update_active_set": [_P, _P, _P, C.POINTER(C.c_int32)],
         "bf_max_step_size": [_P, _P, _P, C.POINTER(C.c_double)],
         "bf_accd": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
+        "bf_max_step_size_pairs_noalloc": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_enable_timers": [_P, C.c_int32],
         "bf_get_launch_count": [_P, C.POINTER(C.c_int64)],
         "bf_set_pcg_mode": [_P, C.c_int32],
@@ -337,6 +338,13 @@ def bf_max_step_size(h, x0, x1):
 def bf_accd(ptype, x0, x1, s, toi, stream=None):
     n = toi.numel()
     _check("bf_accd", lib().bf_accd(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(toi), stream))
+
+
+def bf_max_step_size_pairs_noalloc(ptype, n, x0, x1, s, alpha, stream=None):
+    """alpha[0] = min(1, min TOI) over the first n pairs of x0 -> x1, with no
+    device allocation (see include/bf.h for the limits)."""
+    _check("bf_max_step_size_pairs_noalloc",
+           lib().bf_max_step_size_pairs_noalloc(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(alpha), stream))
 
 
 def bf_enable_timers(h, on=True):

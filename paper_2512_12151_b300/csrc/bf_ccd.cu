@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "bf_device.cuh"
 #include "bf_internal.cuh"
@@ -585,6 +586,83 @@ int accd_pairs(int type, int n, const double *x0, const double *x1, double s, do
     return check_cuda(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free narrow phase: alpha = min(1, min_i TOI_i) over explicit
+// pairs, for callers that cannot allocate device memory.  Its scratch (the
+// per-block minima and the arrival counter of the final reduction) is a
+// file-scope device array, so the only device memory the call touches is
+// the caller's inputs and output and this array.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocThreads = 128;
+constexpr int kNoAllocMaxBlocks = 8192;  // -> at most 1,048,576 pairs per call
+constexpr int kNoAllocMaxPairs = kNoAllocThreads * kNoAllocMaxBlocks;
+// [0, kNoAllocMaxBlocks): per-block minimum TOI (bit pattern of a
+// non-negative double); [kNoAllocMaxBlocks]: arrival counter (64 KiB + 256 B)
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocMaxBlocks + 32];
+
+__global__ void __launch_bounds__(kNoAllocThreads) k_min_toi_noalloc(int type, int n, const double *__restrict__ x0,
+                                                                     const double *__restrict__ x1, double s,
+                                                                     int max_iter, unsigned long long *scratch,
+                                                                     double *alpha)
+{
+    __shared__ unsigned long long smin[kNoAllocThreads / 32];
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double t = 1.0;
+    double toi;
+    if (i < n && accd(type, x0 + 12 * (size_t)i, x1 + 12 * (size_t)i, s, 1.0, max_iter, &toi)) t = fmin(t, toi);
+    unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+        b = u < b ? u : b;
+    }
+    if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kNoAllocThreads / 32; ++w) b = smin[w] < b ? smin[w] : b;
+        scratch[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(scratch + kNoAllocMaxBlocks, 1ull) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    unsigned long long m = (unsigned long long)__double_as_longlong(1.0);
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        const unsigned long long u = __ldcg(scratch + k);
+        m = u < m ? u : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+        m = u < m ? u : m;
+    }
+    if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kNoAllocThreads / 32; ++w) m = smin[w] < m ? smin[w] : m;
+        *alpha = __longlong_as_double((long long)m);
+        scratch[kNoAllocMaxBlocks] = 0ull;  // ready for the next call
+    }
+}
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) and cached.
+static int noalloc_scratch(unsigned long long **out)
+{
+    static std::mutex mu;
+    static unsigned long long *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BF_E_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BF_E_CUDA;
+        addr[dev] = (unsigned long long *)p;
+    }
+    *out = addr[dev];
+    return BF_OK;
+}
+
 int ccd_reserve(Scene &S, int npt, int nee, int nhit)
 {
     const int need = std::max(npt, nee);
@@ -873,3 +951,25 @@ int run_update_active_set(Scene &S, const double *x, const double *xhat)
 }
 
 }  // namespace bf
+
+extern "C" int bf_max_step_size_pairs_noalloc(int32_t type, int32_t n, const double *x0, const double *x1, double s,
+                                              double *alpha, void *stream)
+{
+    using namespace bf;
+    if ((type != PT && type != EE) || n < 0 || !alpha || !(s > 0 && s < 1)) return BF_E_ARG;
+    if (n > kNoAllocMaxPairs) return BF_E_ARG;
+    if (n > 0 && (!x0 || !x1)) return BF_E_ARG;
+    unsigned long long *scratch = nullptr;
+    int st = noalloc_scratch(&scratch);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the arrival counter must start at zero (a failed earlier call may have
+    // left it set); no other scratch needs clearing: every block writes its
+    // own minimum before it is read
+    if (cudaMemsetAsync(scratch + kNoAllocMaxBlocks, 0, sizeof(unsigned long long), cs) != cudaSuccess)
+        return BF_E_CUDA;
+    const int blocks = std::max(1, cdiv(n, kNoAllocThreads));
+    k_min_toi_noalloc<<<blocks, kNoAllocThreads, 0, cs>>>(type, n, x0, x1, s, kAccdMaxIter, scratch, alpha);
+    if (cudaGetLastError() != cudaSuccess) return BF_E_CUDA;
+    return check_cuda(cudaStreamSynchronize(cs));
+}
