@@ -157,20 +157,20 @@ const char *bf_status_str(int status);
 /* ---- teacher-forced entry points (same state as a step uses) ----------- */
 /* All positions below are device buffers of n_verts*3 FP64. */
 
-/* x~ = x^t + h v^t + h^2 g from the resident state (Alg. 1 line 1). */
+/* x~ = x^t + h v^t + h^2 g from the resident state (Alg. 1, inertia target). */
 int bf_xtilde(bf_scene *scene, double *xtilde);
 
 /* Section 5.2: mu = c_mu * max_i (grad^2 E)_ii over free DoFs at xhat,
  * from the PSD-projected elastic Hessian plus mass; stores and returns it. */
 int bf_mu_init(bf_scene *scene, const double *xtilde, const double *xhat, double *mu);
 
-/* Alg. 2 lines 2-4: d_i(x) and grad d_i(x) for every pair of C at xlin.
+/* Alg. 2, linearisation: d_i(x) and grad d_i(x) for every pair of C at xlin.
  * dist (device, |C|) and grad (device, |C|*12, vertex order of the pair:
  * PT point, t0, t1, t2 / EE a0, a1, b0, b1 of the internal primitive) may
  * be NULL. */
 int bf_linearize(bf_scene *scene, const double *xlin, double *dist, double *grad);
 
-/* Alg. 2 lines 6-12 at xhat (after bf_linearize): gradient G (device,
+/* Alg. 2, Newton system at xhat (after bf_linearize): gradient G (device,
  * n_verts*3) of the AL energy with Dirichlet rows zeroed, and the
  * assembled H kept in the scene (elastic PSD blocks + mass in upper BSR,
  * contacts as mu gamma_i grad d_i grad d_i^T).  *energy (host, may be

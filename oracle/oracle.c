@@ -866,7 +866,7 @@ double or_mu_init(or_scene *S, const double *xhat, const double *xtilde)
     return S->mu;
 }
 
-/* Alg. 2, lines 2-4: d_i(x) and grad d_i(x) at the intersection-free x. */
+/* Alg. 2, linearisation: d_i(x) and grad d_i(x) at the intersection-free x. */
 void or_linearize(or_scene *S, const double *xlin, double *d, double *g)
 {
     for (int i = 0; i < S->nc; ++i) {
@@ -891,7 +891,7 @@ static double constraint_c(const or_scene *S, int i, const double *xlin, const d
     return S->cd[i] + s - S->delta;
 }
 
-/* Alg. 2 lines 6-12: G and H of E (PSD-projected) plus the AL contact
+/* Alg. 2, Newton system: G and H of E (PSD-projected) plus the AL contact
  * terms with s_i = max(0, c_i - lambda_i/mu); the slack values are kept
  * for the line search.  Dirichlet DoFs are eliminated (section 5.3):
  * their gradient entries are zero and H is applied with their rows and
@@ -952,7 +952,7 @@ void or_hess_apply(const or_scene *S, const double *in, double *out)
                 for (int b = 0; b < 3; ++b) s += S->val[9 * k + 3 * c + b] * xm[3 * S->ci[k] + b];
             out[3 * r + c] = s;
         }
-    /* H += mu gamma_i grad d_i grad d_i^T (Alg. 2 line 9) */
+    /* H += mu gamma_i grad d_i grad d_i^T (Alg. 2, contact Hessian) */
     for (int i = 0; i < S->nc; ++i) {
         int v[4];
         pair_verts(S, S->ctype[i], S->ca[i], S->cb[i], v);
@@ -1080,7 +1080,7 @@ double or_energy_L(or_scene *S, const double *xtilde, const double *xlin, const 
  * 2^-max_ls (the paper's strict "<" can loop forever once p ~ 0); a failed
  * line search ends the Newton loop without a step; the Newton loop is
  * capped at max_newton iterations.  xhat is updated in place and the
- * multipliers and decay factors of C are updated as in Alg. 2 lines 18-27.
+ * multipliers and decay factors of C are updated as in the multiplier and decay update of Alg. 2.
  * Returns the number of Newton iterations. */
 int32_t or_solve_subproblem(or_scene *S, const double *xtilde, const double *xlin, double *xhat,
                             int32_t *cg_iters, int32_t *ls_fail)
@@ -1112,7 +1112,7 @@ int32_t or_solve_subproblem(or_scene *S, const double *xtilde, const double *xli
         memcpy(xhat, xt, n * sizeof(double));
         if (r == 1.0) break;
     }
-    /* multiplier and decay update (Alg. 2 lines 18-27) */
+    /* multiplier and decay update (Alg. 2) */
     for (int i = 0; i < S->nc; ++i) {
         double c = constraint_c(S, i, xlin, xhat);
         double mu = S->mu;
@@ -1258,8 +1258,8 @@ int32_t or_ccd_hits(or_scene *S, const double *x0, const double *x1, int32_t bru
     return n;
 }
 
-/* Alg. 3 UpdateActiveSet(x, xhat, C).  Reading of line 2: the pairs that
- * "generate intersections" are the CCD hits (t <= 1) along x -> xhat. */
+/* Alg. 3 UpdateActiveSet(x, xhat, C).  Reading of its intersection step: the
+ * intersecting pairs are the CCD hits (t <= 1) along x -> xhat. */
 int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat)
 {
     hitvec hv = {0, 0, 0};
@@ -1275,7 +1275,7 @@ int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat)
         hv.h[nn++] = hv.h[i];
     }
     free(ck);
-    /* T_v = min over new pairs containing v (lines 5-7) */
+    /* T_v = min over new pairs containing v (Alg. 3, per-vertex minimum) */
     double *Tv = (double *)xcalloc(S->nv, sizeof(double));
     for (int v = 0; v < S->nv; ++v) Tv[v] = INFINITY;
     for (int i = 0; i < nn; ++i) {
@@ -1284,7 +1284,7 @@ int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat)
         for (int k = 0; k < 4; ++k)
             if (hv.h[i].toi < Tv[v[k]]) Tv[v[k]] = hv.h[i].toi;
     }
-    /* keep pairs whose T_i equals T_v of one of their vertices (lines 8-13) */
+    /* keep pairs whose T_i equals T_v of one of their vertices (Alg. 3, filter) */
     for (int i = 0; i < nn; ++i) {
         int v[4];
         pair_verts(S, hv.h[i].type, hv.h[i].a, hv.h[i].b, v);
@@ -1299,7 +1299,7 @@ int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat)
     }
     free(Tv);
     free(hv.h);
-    /* prune gamma < 0.01 (lines 14-18) */
+    /* prune gamma < 0.01 (Alg. 3, decay pruning) */
     int m = 0;
     for (int i = 0; i < S->nc; ++i) {
         if (S->cgam[i] < 0.01) continue;

@@ -9,6 +9,18 @@
  *
  * Everything is FP64, compiled with -ffp-contract=off.  Each routine cites
  * the paper passage it follows (section, equation or algorithm).
+ *
+ * Pins (tests that check this code against facts fixed outside it): energy,
+ * stress and Hessian by finite differences and the small-strain limit; the
+ * eigensolver and PSD projection against a dense library eigensolver and an
+ * independent analytic eigensystem; distances by brute-force minimisation;
+ * ACCD by closed-form cases and root bracketing; lumped mass and mu_init in
+ * closed form; PCG against a dense solve; the AL subproblem against an
+ * independent constrained solve (KKT point); the active-set filter and decay
+ * on hand-built cases; the time step by free fall, momentum, the beta product,
+ * the moving-boundary bound and penetration-free states.  Whole trajectories
+ * of contact scenes have no value fixed outside this code: parity unpinned
+ * beyond the invariants above.
  */
 #ifndef BF_ORACLE_H
 #define BF_ORACLE_H

@@ -182,7 +182,7 @@ __device__ __forceinline__ void gather12(const double *__restrict__ x, int4 v, d
 }
 
 // ---------------------------------------------------------------------------
-// Alg. 2 lines 2-4: d_i(x), grad d_i(x) (envelope theorem at the closest
+// Alg. 2, linearisation: d_i(x), grad d_i(x) (envelope theorem at the closest
 // points), and the free-vertex mask of each pair
 // ---------------------------------------------------------------------------
 __global__ void k_linearize(int nc, const int *__restrict__ ctype, const int4 *__restrict__ cv,
@@ -792,7 +792,7 @@ __global__ void k_ckeys(int nc, const int *__restrict__ ctype, const int *__rest
     if (i < nc) key[i] = pair_key(ctype[i], ca[i], cb[i]);
 }
 
-// new pairs (not in C) lower the per-vertex minimum TOI T_v (lines 3-7)
+// new pairs (not in C) lower the per-vertex minimum TOI T_v (Alg. 3, per-vertex minimum)
 __global__ void k_new_hits(int nh, const int *__restrict__ ht, const int *__restrict__ ha, const int *__restrict__ hb,
                            const double *__restrict__ htoi, const unsigned long long *__restrict__ ck, int nc,
                            const int *__restrict__ st, const int *__restrict__ se, int *__restrict__ isnew,
@@ -823,7 +823,7 @@ __global__ void k_new_hits(int nh, const int *__restrict__ ht, const int *__rest
     atomicMin(tv + v.w, t);
 }
 
-// keep a new pair whose TOI equals T_v of one of its vertices (lines 8-13)
+// keep a new pair whose TOI equals T_v of one of its vertices (Alg. 3, filter)
 __global__ void k_keep(int nh, const int *__restrict__ ht, const int *__restrict__ ha, const int *__restrict__ hb,
                        const double *__restrict__ htoi, const int *__restrict__ isnew, const int *__restrict__ st,
                        const int *__restrict__ se, const unsigned long long *__restrict__ tv,
@@ -856,7 +856,7 @@ __global__ void k_append(int nk, int nc, const int *__restrict__ kidx, const int
     cgam[o] = 1.0;
 }
 
-// prune gamma < 0.01 (lines 14-18): stable compaction in place via a scan
+// prune gamma < 0.01 (Alg. 3, decay pruning): stable compaction in place via a scan
 __global__ void k_prune_flags(int nc, const double *__restrict__ cgam, int *__restrict__ flag)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

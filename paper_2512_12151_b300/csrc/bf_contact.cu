@@ -80,7 +80,7 @@ void launch_contact_assemble(Scene &S, const double *xlin, const double *xhat)
                                                                        S.cw, S.grad, S.cdiag); ++S.n_launch;
 }
 
-// Alg. 2 lines 18-27: with s_i = max(0, c_i - lambda_i/mu), s_i = 0 gives
+// Alg. 2, multiplier and decay update: with s_i = max(0, c_i - lambda_i/mu), s_i = 0 gives
 // lambda_i <- lambda_i - mu c_i and gamma_i <- 1, otherwise lambda_i <- 0
 // and gamma_i <- Gamma gamma_i.
 __global__ void k_multiplier_update(int nc, const int4 *__restrict__ cv, const double *__restrict__ cd,

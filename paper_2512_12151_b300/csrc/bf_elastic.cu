@@ -399,7 +399,7 @@ double run_mu_max_diag(Scene &S)
     return S.h_scal[S_MAXDIAG];
 }
 
-// x~ = x + h v + h^2 g for free vertices (Alg. 1 line 1); prescribed: x
+// x~ = x + h v + h^2 g for free vertices (Alg. 1, inertia target); prescribed: x
 __global__ void k_xtilde(int nv, const double *__restrict__ x, const double *__restrict__ v,
                          const uint8_t *__restrict__ dir, double h, double gx, double gy, double gz,
                          double *__restrict__ xt)

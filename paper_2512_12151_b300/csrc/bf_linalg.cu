@@ -429,7 +429,7 @@ void launch_blend(Scene &S, double *xk, const double *xh, double alpha, int n)
     k_blend<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, xk, xh, alpha); ++S.n_launch;
 }
 
-// Alg. 1 line 20: v^{t+1} = (x^[k] - x^t) / h, x^{t+1} = x^[k]
+// Alg. 1, end of the time step: v^{t+1} = (x^[k] - x^t) / h, x^{t+1} = x^[k]
 __global__ void k_velocity(int n, const double *__restrict__ xk, const double *__restrict__ xt, double h,
                            double *__restrict__ x, double *__restrict__ v)
 {

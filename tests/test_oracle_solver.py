@@ -253,3 +253,66 @@ def test_moving_boundary_error_bound():
         x, _ = o.get_state()
         err = np.abs(x[s.dirichlet == 1] - tgt).max()
         assert err <= bound * (1 + 1e-9)
+
+
+def test_lumped_mass_and_mu_init_closed_form():
+    """Unjittered 2^3-cell cube (side 0.1, Kuhn split) with a vanishing
+    Young's modulus: every vertex mass is rho V_e / 4 summed over its tets,
+    so the interior vertex (24 tets of volume h^3/6) weighs rho h^3 and the
+    total is rho side^3; the Hessian diagonal is then the mass, and
+    mu_init = 0.1 x max diagonal (section 5.2) = 0.1 rho h^3."""
+    v, t = scenes.cube_mesh(2, 0.1)
+    b = scenes._Builder()
+    b.add_solid(v, t, 0)
+    s = b.build("cube_2", [[1e-9, 0.3, 1000.0]], scenes.Params(), 1)
+    o = O.Oracle(s)
+    m = o.mass()
+    h = 0.05
+    assert np.isclose(m.sum(), 1000.0 * 0.1 ** 3, rtol=1e-12)
+    center = 1 + 3 * 1 + 9 * 1
+    assert np.isclose(m[center], 1000.0 * h ** 3, rtol=1e-12)
+    assert m.argmax() == center
+    # corners: rho h^3 / 4 on the two cell-diagonal corners, rho h^3 / 12 elsewhere
+    corners = [0, 2, 6, 8, 18, 20, 24, 26]
+    assert np.allclose(np.sort(m[corners] / (1000.0 * h ** 3)), [1 / 12] * 6 + [0.25] * 2, rtol=1e-12)
+    x, _ = o.get_state()
+    mu = o.mu_init(x, o.xtilde())
+    assert np.isclose(mu, 0.1 * 1000.0 * h ** 3, rtol=1e-9)
+
+
+def test_update_active_set_keeps_per_vertex_first_hits():
+    """Alg. 3 on a hand-built case: one tet translating 0.2 m down through
+    two stacked static quads (z = 0 and z = -0.05).  Its lowest vertex a
+    meets the upper quad first (t ~ 0.1), the others b, c, d later (t ~ 0.5);
+    all meet the lower quad later still.  Filter: a new pair stays iff its
+    TOI is the minimum over the pairs of one of its vertices.  Expected: the
+    four pairs with the upper quad stay (each is its free vertex's first
+    hit), (a, lower) stays (the lower quad's vertices are first hit by a),
+    and (b|c|d, lower) are dropped (later than both their vertex's first
+    hit and the lower quad's first hit)."""
+    pa, pb, pc, pd = [0.5, -0.5, 0.02], [0.55, -0.5, 0.1], [0.5, -0.45, 0.1], [0.47, -0.53, 0.12]
+    tv = np.array([pa, pb, pc, pd])
+    tet = np.array([[0, 1, 2, 3]], np.int32)
+    if np.linalg.det(tv[1:] - tv[0]) < 0:
+        tet = np.array([[0, 2, 1, 3]], np.int32)
+    b = scenes._Builder()
+    b.add_solid(tv, tet, 0)
+    gv, gt = scenes.ground_quad(1.0, 0.0)
+    b.add_obstacle(gv, gt)  # vertices 4..7, triangle (4, 5, 6) under the tet
+    lv, lt = scenes.ground_quad(1.0, -0.05)
+    b.add_obstacle(lv, lt)  # vertices 8..11, triangle (8, 9, 10) under the tet
+    s = b.build("tet_two_quads", [[1e5, 0.4, 1000.0]], scenes.Params(), 1)
+    o = O.Oracle(s)
+    x0 = s.x0.copy()
+    x1 = x0.copy()
+    x1[:4, 2] -= 0.2
+    keys, toi = o.ccd_hits(x0, x1)
+    got = {tuple(k) for k in keys.tolist()}
+    upper = [(0, v, 4, 5, 6) for v in range(4)]
+    lower = [(0, v, 8, 9, 10) for v in range(4)]
+    assert got == set(upper + lower)  # every vertex crosses both quads, nothing else
+    n = o.update_active_set(x0, x1)
+    kept, lam, gam = o.active_get()
+    assert n == 5
+    assert {tuple(k) for k in kept.tolist()} == set(upper + lower[:1])
+    assert (lam == 0).all() and (gam == 1).all()
