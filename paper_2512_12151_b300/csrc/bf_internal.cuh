@@ -109,6 +109,7 @@ struct Scene {
     int pcg_allow_resident = 1;  // persistent PCG may keep the matrix in shared memory
     int pcg_max_rows = 0, pcg_max_ent = 0, pcg_max_win = 0, pcg_block = 256;
     unsigned short *pcg_erow = nullptr;  // CTA-local row of every full-row entry
+    int pcg_kc = 0;               // persistent PCG: contacts per CTA cached in shared memory
     int *win = nullptr;       // persistent PCG: staged vertex window per CTA
     std::vector<int> h_fnbr;
     // reductions

@@ -1,5 +1,5 @@
 // Persistent block-Jacobi PCG (section 5.1): one cooperative launch per
-// linear solve, all CTAs co-resident.
+// linear solve, one CTA per SM, all CTAs co-resident.
 //
 // Work split: CTA c owns the contiguous vertex rows [part[c], part[c+1]),
 // balanced by block count.  It keeps x, r, the row sums q = (H p) and the
@@ -8,24 +8,38 @@
 // variant), also the blocks of its rows (full-row view: upper blocks and
 // the transposed lower ones), row after row, with its neighbours as 16-bit
 // offsets into the CTA's vertex window, which covers every neighbour of its
-// rows.  Each iteration stages p = z + beta p_old over that window into
-// shared memory (16 bytes per vertex) with coalesced loads; consecutive
-// threads then take consecutive blocks (bank-conflict-free: 9 words per
-// block), reduce the products per row with a segmented warp scan and store
-// each row segment with one shared-memory add, so the SpMV needs no global
-// atomics.  The contact terms
-// mu gamma g g^T p go to a separate vector with global atomics (few pairs,
-// dealt round-robin to the CTAs).
+// rows.  The direction p over that window also stays in shared memory: each
+// iteration updates it in place, p = z + beta p, from the z values of the
+// window (16 bytes per vertex), so every CTA holds bit-identical copies of p
+// on the vertices it shares with others.  Consecutive threads then take
+// consecutive blocks (9 words per block: no bank conflicts), reduce the
+// products per row with a segmented warp scan and add each row segment to
+// shared memory once, so the SpMV needs no global atomics.
+//
+// Contact pairs (rank one: mu gamma g g^T) are dealt round-robin to the
+// CTAs (pair i -> CTA i % gridDim.x), so that each CTA carries an equal share
+// however the pairs cluster on the mesh.  A CTA caches its pairs' gradient,
+// weight and ids in shared memory for the solve, fetches the p values at
+// their vertices together with its window, and adds mu gamma g (g . p) to a
+// global contact vector with atomics; the owners of the rows read (and
+// clear) that vector after the next grid-wide reduction.
 //
 // Two grid-wide reductions per iteration double as the grid barriers:
-//   A: q = H p, p = z + beta p_old (double-buffered p, so no barrier
-//      separates the direction update from the SpMV); reduce p.q -> alpha
+//   A: q = H p (p updated in place first; contact part to the contact
+//      vector); reduce p.q -> alpha
 //   B: x += alpha p, r -= alpha q, z = P r; reduce r.z and r.r -> beta,
 //      convergence test.
-// Every CTA reads the same reduced bits, so all take the same decisions.
-// Every spin has an iteration limit (ERR_BARRIER).  Mixed precision runs the
-// iterations in FP32 (p, q, z, r and the increment of x) with the dot
-// products accumulated in FP64, and makes reliable updates: whenever |r| has
+// Thread 0 of every CTA reads the reduced values and derives the scalars
+// (alpha, beta, the next state) once for its CTA; every CTA reads the same
+// reduced bits, so all take the same decisions.  Every spin has an
+// iteration limit (ERR_BARRIER).
+//
+// Mixed precision runs the iterations in FP32 (p, q, z, r and the increment
+// of x).  Dot products are accumulated without loss beyond FP64-like
+// accuracy: per CTA as compensated FP32 sums (every rounding error of the
+// additions is kept exactly by Knuth's TwoSum and summed separately, the
+// cascaded summation of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005), across CTAs in FP64.  Reliable updates: whenever |r| has
 // dropped by 10x since the last one, or the recurrence signals convergence,
 // x is folded into its FP64 value and r is recomputed as b - H x with FP64
 // vectors (FP32 matrix); convergence is decided on that residual.
@@ -41,7 +55,10 @@
 
 namespace bf {
 
-constexpr int kPcgMaxThreads = 256;
+constexpr int kPcgThreads = 512;  // threads per CTA at one CTA per SM
+constexpr int kPcgMaxWarps = kPcgThreads / 32;
+constexpr int kPcgMaxCached = 256;  // contact pairs per CTA cached in shared memory
+constexpr int kPcgMaxGrid = 1024;  // CTAs of one launch
 
 struct PcgArgs {
     int nv, nc;
@@ -55,13 +72,23 @@ struct PcgArgs {
     const void *pinv;
     const double *b;
     double *x;
-    void *z, *p0, *p1, *qc;
-    double *qd, *res;
+    void *z, *p0, *p1, *qc;  // qc: contact part of H p (atomics)
+    double *qd;               // FP64 contact part of H x (reliable updates)
+    double *res;
     unsigned *bar;
     double tol2;
-    int maxit, max_replace, max_rows, max_ent, max_win;
+    int maxit, max_replace, max_rows, max_ent, max_win, kc;
     double *dscal;
     int *dflag;
+};
+
+enum { PCG_RUN = 0, PCG_DONE, PCG_MAXIT, PCG_BAD, PCG_FOLD, PCG_ABORT };
+
+// scalar state of the recurrence, maintained by thread 0 of each CTA
+struct PcgCtl {
+    double alpha, beta, rz, rz_old, rr, rr_ref, bb;
+    float al, bt;
+    int it, folds, state;
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
@@ -78,89 +105,138 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Block sum of K doubles with few FP64 instructions: every thread parks its
-// values in shared memory, the first (up to four) warps each add a share
-// (lane-strided, then 5 shuffle levels) and thread 0 adds the shares.  The
-// result is valid in thread 0.
-template <int K>
-__device__ __forceinline__ void cta_sum(double (&v)[K])
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error e = a + b - s
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    __shared__ double sh[K][kPcgMaxThreads];
-    __shared__ double q4[K][4];
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+
+// compensated FP32 accumulator: the value is s + c
+struct AccF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float e;
+        two_sum(s, v, s, e);
+        c += e;
+    }
+    __device__ __forceinline__ void add(double v)  // an FP64 value as two FP32 parts
+    {
+        const float hi = (float)v;
+        add(hi);
+        add((float)(v - (double)hi));
+    }
+};
+
+__device__ __forceinline__ void acc_add(AccF &a, float v) { a.add(v); }
+__device__ __forceinline__ void acc_add(AccF &a, double v) { a.add(v); }
+__device__ __forceinline__ void acc_add(double &a, double v) { a += v; }
+
+// butterfly sum of compensated pairs over a warp (the same result in every
+// lane: TwoSum is exact whatever the operand order)
+__device__ __forceinline__ void warp_sum2(float &s, float &c)
+{
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float co = __shfl_xor_sync(0xffffffffu, c, o);
+        float e;
+        two_sum(s, so, s, e);
+        c = (c + co) + e;
+    }
+}
+
+// block sum of K compensated accumulators; the FP64 result is valid in warp 0
+template <int K>
+__device__ __forceinline__ void block_sum(AccF (&a)[K], double (&out)[K], float2 *sh)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        warp_sum2(a[k].s, a[k].c);
+        if (lane == 0) sh[k * kPcgMaxWarps + w] = make_float2(a[k].s, a[k].c);
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 v = lane < nw ? sh[k * kPcgMaxWarps + lane] : make_float2(0.f, 0.f);
+            float s = v.x, c = v.y;
+            warp_sum2(s, c);
+            out[k] = (double)s + (double)c;
+        }
+    }
+}
+
+// block sum of K FP64 values: every thread parks its values in shared
+// memory (sh: K x blockDim.x), up to four warps each add a share (strided,
+// then shuffles) and thread 0 adds the shares; valid in thread 0
+template <int K>
+__device__ __forceinline__ void block_sum(double (&a)[K], double (&out)[K], double *sh, double *q4)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * blockDim.x + threadIdx.x] = a[k];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = min(4, (int)(blockDim.x + 31) >> 5);  // warps taking part
-    const int quarter = ((int)blockDim.x + nw - 1) / nw;
+    const int nw = min(4, (int)(blockDim.x + 31) >> 5);
+    const int share = ((int)blockDim.x + nw - 1) / nw;
     if (w < nw) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             double t = 0.0;
-            for (int i = lane; i < quarter; i += 32) {
-                const int j = w * quarter + i;
-                if (j < (int)blockDim.x) t += sh[k][j];
+            for (int i = lane; i < share; i += 32) {
+                const int j = w * share + i;
+                if (j < (int)blockDim.x) t += sh[k * blockDim.x + j];
             }
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) q4[k][w] = t;
+            if (lane == 0) q4[4 * k + w] = t;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double t = q4[k][0];
-            for (int i = 1; i < nw; ++i) t += q4[k][i];
-            v[k] = t;
+            double t = q4[4 * k];
+            for (int i = 1; i < nw; ++i) t += q4[4 * k + i];
+            out[k] = t;
         }
 }
 
-// Grid-wide sum of K values that doubles as the grid barrier.
-// Reduction: each CTA adds its block sum to accumulator slot (n % 3) with an
-// FP64 atomic add, n = the count of reductions so far in this launch; CTA 0
-// zeroes slot (n + 1) % 3 before it arrives (that slot was last read before
-// the previous barrier and is next written after this one).  Barrier: one
-// arrival counter whose top bit flips when every CTA has arrived (CTA 0
-// adds 0x80000000 - (gridDim.x - 1), the others 1), with a release on the
-// arrival and acquire loads while spinning (bounded; ERR_BARRIER).
+// Grid-wide sum of K block sums (called by thread 0 of every CTA) that
+// doubles as the grid barrier.  Reduction: each CTA adds its block sum to
+// accumulator slot (n % 3) with an FP64 atomic add, n = the count of
+// reductions so far in this launch; CTA 0 zeroes slot (n + 1) % 3 before it
+// arrives (that slot was last read before the previous barrier and is next
+// written after this one).  Barrier: one arrival counter whose top bit
+// flips when every CTA has arrived (CTA 0 adds 0x80000000 - (gridDim.x - 1),
+// the others 1), with a release on the arrival and acquire loads while
+// spinning (bounded: ERR_BARRIER and false on timeout).
 template <int K>
-__device__ __forceinline__ bool grid_reduce(double (&v)[K], double *acc, unsigned &n, unsigned *bar, int *dflag,
-                                            double (&tot)[K])
+__device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, unsigned n, unsigned *bar, int *dflag,
+                                           double (&tot)[K])
 {
-    __shared__ int s_ok;
-    cta_sum<K>(v);
     const unsigned slot = n % 3u, next = (n + 1u) % 3u;
-    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) atomicAdd(acc + 8 * slot + k, v[k]);
-        if (blockIdx.x == 0)
+    for (int k = 0; k < K; ++k) atomicAdd(acc + 8 * slot + k, v[k]);
+    if (blockIdx.x == 0)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) acc[8 * next + k] = 0.0;
-        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        unsigned old;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
-        int ok = 1;
-        unsigned long long spins = 0;
-        while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
-            if (++spins > (1ull << 28)) {
-                atomicOr(dflag + F_ERR, ERR_BARRIER);
-                ok = 0;
-                break;
-            }
+        for (int k = 0; k < 3; ++k) acc[8 * next + k] = 0.0;
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
+    unsigned long long spins = 0;
+    while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
+        if (++spins > (1ull << 28)) {
+            atomicOr(dflag + F_ERR, ERR_BARRIER);
+            return false;
         }
-        s_ok = ok;
     }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) tot[k] = __ldcg(acc + 8 * slot + k);
-    ++n;
-    const bool ok = s_ok != 0;
-    __syncthreads();
-    return ok;
+    return true;
 }
-
-__device__ __forceinline__ void smem_add(float *p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void smem_add(double *p, double v) { atomicAdd(p, v); }
 
 // Row sums of H u over the CTA's rows, added into s_q (component-major,
 // s_q[c * ldq + row], zeroed by the caller).  Consecutive threads take
@@ -198,46 +274,11 @@ __device__ __forceinline__ void row_sums(int ne, const unsigned short *erow, Get
         }
         const int rn = __shfl_down_sync(0xffffffffu, row, 1);
         if (row >= 0 && (lane == 31 || rn != row)) {
-            smem_add(s_q + row, y0);
-            smem_add(s_q + ldq + row, y1);
-            smem_add(s_q + 2 * ldq + row, y2);
+            atomicAdd(s_q + row, y0);
+            atomicAdd(s_q + ldq + row, y1);
+            atomicAdd(s_q + 2 * ldq + row, y2);
         }
     }
-}
-
-// contact part: y += sum_i mu gamma_i g_i (g_i . u) over the pairs, dealt
-// round-robin to the CTAs (pair i -> CTA i % gridDim.x) so that no CTA
-// carries more than its share; arithmetic in CT, the u^T H_c u share
-// returned in FP64
-template <class CT, class VO, class GetU>
-__device__ __forceinline__ double contact_pass(const PcgArgs &A, GetU getu, VO *y)
-{
-    double dot = 0.0;
-    for (int i = threadIdx.x * gridDim.x + blockIdx.x; i < A.nc; i += gridDim.x * blockDim.x) {
-        const int4 v = A.cv[i];
-        const unsigned char m = A.cmask[i];
-        const int vid[4] = {v.x, v.y, v.z, v.w};
-        const double *g = A.cg + 12 * (size_t)i;
-        CT gl[12], s = CT(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            CT u[3] = {CT(0), CT(0), CT(0)};
-            if (m >> q & 1) getu(vid[q], u);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                gl[3 * q + j] = (CT)g[3 * q + j];
-                s += gl[3 * q + j] * u[j];
-            }
-        }
-        const CT t = (CT)A.cw[i] * s;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (m >> q & 1)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) atomicAdd(y + 3 * vid[q] + j, (VO)(t * gl[3 * q + j]));
-        dot += (double)(t * s);
-    }
-    return dot;
 }
 
 template <class T>
@@ -251,14 +292,19 @@ __device__ __forceinline__ void load3v(const T *src, T *u)
     }
 }
 
+// the direction update p = z + beta p_old, written once so that every CTA
+// rounds it the same way
+__device__ __forceinline__ float dir_update(float z, float bt, float p) { return fmaf(bt, p, z); }
+__device__ __forceinline__ double dir_update(double z, double bt, double p) { return fma(bt, p, z); }
+
 // Shared-memory layout of the persistent PCG (byte offsets, 16-byte aligned
 // sections), shared by the kernel and the host-side sizing.
 struct PcgLayout {
-    size_t x, hx, xl, r, q, pinv, p4, val, nbr, erow, total;
+    size_t x, xl, r, q, pinv, p4, val, nbr, erow, cg, cp, cw, cv, cm, total;
 };
 
 __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
-                                                bool res)
+                                                bool res, int kc)
 {
     PcgLayout L;
     size_t o = 0;
@@ -269,47 +315,66 @@ __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int 
     };
     const int rt = mixed ? 4 : 8;
     L.x = take(3 * (size_t)max_rows * 8);
-    L.hx = take(mixed ? 3 * (size_t)max_rows * 8 : 0);
     L.xl = take(mixed ? 3 * (size_t)max_rows * rt : 0);
     L.r = take(3 * (size_t)max_rows * rt);
-    L.q = take(3 * (size_t)max_rows * ct);
+    L.q = take(3 * (size_t)max_rows * (mixed ? 8 : ct));  // FP64 H x of the reliable updates reuses it
     L.pinv = take(9 * (size_t)max_rows * mt);
     L.p4 = take(4 * (size_t)max_win * ct);
     L.val = take(res ? 9 * (size_t)max_ent * mt : 0);
     L.nbr = take(res ? (size_t)max_ent * 2 : 0);
     L.erow = take(res ? (size_t)max_ent * 2 : 0);
+    L.cg = take(12 * (size_t)kc * ct);
+    L.cp = take(12 * (size_t)kc * ct);
+    L.cw = take((size_t)kc * ct);
+    L.cv = take((size_t)kc * 16);
+    L.cm = take((size_t)kc * 4);
     L.total = o;
     return L;
 }
 
+// bytes of one cached contact pair (gradient, p at its vertices, weight, ids, flags)
+inline size_t pcg_contact_bytes(int ct) { return 25 * (size_t)ct + 20; }
+
 template <class MT, class VT, bool RES>
-__global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 {
     using CT = typename std::conditional<(sizeof(MT) >= sizeof(VT)), MT, VT>::type;
     constexpr bool mixed = sizeof(VT) == 4;
     using RT = typename std::conditional<mixed, float, double>::type;  // r and the iteration part of x
+    using Acc = typename std::conditional<mixed, AccF, double>::type;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PcgCtl ctl;
+    __shared__ float2 red_f[2 * kPcgMaxWarps];
+    __shared__ double red_d[mixed ? 1 : 2 * kPcgThreads];
+    __shared__ double red_q4[8];
     const MT *__restrict__ gval = (const MT *)A.val;
     const MT *__restrict__ gpinv = (const MT *)A.pinv;
     VT *__restrict__ z = (VT *)A.z;
-    VT *__restrict__ qc = (VT *)A.qc;
     VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
+    VT *__restrict__ qc = (VT *)A.qc;
     const int c = blockIdx.x;
     const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
-    const int wlo = A.win[2 * c], whi = A.win[2 * c + 1];
+    const int wlo = A.win[2 * c], whi = A.win[2 * c + 1], nwin = whi - wlo;
     const int E0 = A.frowptr[r0], ne = A.frowptr[r1] - E0;  // the CTA's full-row entries
-    const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, RES);
+    const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;  // pairs c + k grid
+    const int ncached = min(nco, A.kc);
+    const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, RES, A.kc);
     const int ld = A.max_rows;  // per-row arrays are component-major: a[c * ld + row]
     double *s_x = (double *)(smem + L.x);
-    double *s_hx = (double *)(smem + L.hx);
     RT *s_xl = (RT *)(smem + L.xl);
     RT *s_r = (RT *)(smem + L.r);
     CT *s_q = (CT *)(smem + L.q);
+    double *s_hx = (double *)(smem + L.q);
     MT *s_pinv = (MT *)(smem + L.pinv);
     CT *s_p4 = (CT *)(smem + L.p4);
     MT *s_val = (MT *)(smem + L.val);
     unsigned short *s_nbr = (unsigned short *)(smem + L.nbr);
     unsigned short *s_erow = (unsigned short *)(smem + L.erow);
+    CT *s_cg = (CT *)(smem + L.cg);
+    CT *s_cp = (CT *)(smem + L.cp);
+    CT *s_cw = (CT *)(smem + L.cw);
+    int4 *s_cv = (int4 *)(smem + L.cv);
+    int *s_cm = (int *)(smem + L.cm);
     const unsigned short *erow = RES ? s_erow : A.erow + E0;
     for (int i = threadIdx.x; i < 9 * nr; i += blockDim.x) s_pinv[i] = gpinv[9 * (size_t)r0 + i];
     if (RES) {
@@ -331,7 +396,15 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
             s_erow[e] = A.erow[fe];
         }
     }
-    __syncthreads();
+    for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
+        const int i = c + k * (int)gridDim.x;
+        s_cv[k] = A.cv[i];
+        s_cm[k] = A.cmask[i];
+        s_cw[k] = (CT)A.cw[i];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) s_cg[12 * k + j] = (CT)A.cg[12 * (size_t)i + j];
+    }
+    for (int i = threadIdx.x; i < 4 * nwin; i += blockDim.x) s_p4[i] = CT(0);  // p_old = 0
     // block values of local entry pos (row-major, lower blocks transposed);
     // returns the neighbour's window offset
     auto ent = [&](int pos, CT *a) -> int {
@@ -356,8 +429,8 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
             return __ldg(A.fnbr + fe) - wlo;
         }
     };
-    // z = P r for row i, and the row's share of r.z
-    auto precond = [&](int i, const RT *rv) -> double {
+    // z = P r for row i (written to global memory); returns the row's r.z
+    auto precond = [&](int i, const RT *rv) -> CT {
         const int a = r0 + i;
         const MT *P = s_pinv + 9 * i;
         CT zc[3];
@@ -366,69 +439,99 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
             zc[k] = (CT)P[3 * k] * (CT)rv[0] + (CT)P[3 * k + 1] * (CT)rv[1] + (CT)P[3 * k + 2] * (CT)rv[2];
             z[3 * a + k] = (VT)zc[k];
         }
-        if (mixed) return (double)((float)rv[0] * (float)zc[0] + (float)rv[1] * (float)zc[1] + (float)rv[2] * (float)zc[2]);
-        return ((double)rv[0] * (double)zc[0] + (double)rv[1] * (double)zc[1]) + (double)rv[2] * (double)zc[2];
+        return ((CT)rv[0] * zc[0] + (CT)rv[1] * zc[1]) + (CT)rv[2] * zc[2];
     };
-    auto rnorm = [&](const RT *rv) -> double {
-        if (mixed) return (double)((float)rv[0] * (float)rv[0] + (float)rv[1] * (float)rv[1] + (float)rv[2] * (float)rv[2]);
-        return ((double)rv[0] * (double)rv[0] + (double)rv[1] * (double)rv[1]) + (double)rv[2] * (double)rv[2];
-    };
-    double t2[2];
     unsigned nred = 0;  // reductions so far (selects the accumulator slot)
+    // block sum then grid sum; thread 0 runs on_total(tot) (or marks the
+    // CTA aborted), then the CTA synchronises
+    auto reduce = [&](auto &acc, auto on_total) {
+        constexpr int K = (int)std::extent<std::remove_reference_t<decltype(acc)>>::value;
+        double blk[K], tot[K];
+        if constexpr (mixed) block_sum<K>(acc, blk, red_f);
+        else block_sum<K>(acc, blk, red_d, red_q4);
+        if (threadIdx.x == 0) {
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            else ctl.state = PCG_ABORT;
+        }
+        ++nred;
+        __syncthreads();
+    };
     unsigned long long tA = 0, tA2 = 0, tB = 0, tB2 = 0, t0 = 0, tS = 0, tR = 0, tC = 0;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-    // ---- init: r = b, x = 0, z = P r, p_old = 0, qc = 0 --------------------
+    __syncthreads();
+    // ---- init: r = b, x = 0, z = P r, p_old = 0 ------------------------------
     {
-        double v[2] = {0.0, 0.0};
+        Acc acc[2] = {};
         for (int i = threadIdx.x; i < nr; i += blockDim.x) {
             const int a = r0 + i;
             RT rv[3];
+            double bb = 0.0;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                rv[k] = (RT)A.b[3 * a + k];
+                const double bk = A.b[3 * a + k];
+                rv[k] = (RT)bk;
                 s_r[k * ld + i] = rv[k];
                 s_x[k * ld + i] = 0.0;
                 if (mixed) s_xl[k * ld + i] = RT(0);
                 s_q[k * ld + i] = CT(0);
                 qc[3 * a + k] = VT(0);
-                pb[0][3 * a + k] = VT(0);
                 if (mixed) A.qd[3 * a + k] = 0.0;
-                v[1] += A.b[3 * a + k] * A.b[3 * a + k];  // |b|^2 in FP64
+                if (A.nc > 0) pb[0][3 * a + k] = VT(0);
+                bb += bk * bk;  // |b|^2 in FP64
             }
-            v[0] += precond(i, rv);
+            acc_add(acc[0], precond(i, rv));
+            acc_add(acc[1], bb);
         }
-        if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
+        reduce(acc, [&](const double *t) {
+            ctl.rz = t[0];
+            ctl.bb = t[1];
+            ctl.rr = t[1];
+            ctl.rr_ref = t[1];
+            ctl.beta = 0.0;
+            ctl.bt = 0.f;
+            ctl.it = 0;
+            ctl.folds = 0;
+            if (t[1] > 0.0 && isfinite(t[1]) && isfinite(t[0])) ctl.state = PCG_RUN;
+            else ctl.state = t[1] == 0.0 ? PCG_DONE : PCG_BAD;
+        });
     }
-    double rz = t2[0];
-    const double bb = t2[1];
-    double rr = bb, beta = 0.0, rr_ref = bb;
-    int it = 0, parity = 0, folds = 0, maxit_hit = 0, bad = 0;
-    if (!(bb > 0.0) || !isfinite(bb) || !isfinite(rz)) {
-        bad = !(bb == 0.0);
-        goto finish;
-    }
-    for (;;) {
+    int parity = 0;
+    while (ctl.state == PCG_RUN) {
         VT *pold = pb[parity], *pnew = pb[parity ^ 1];
-        double pq[1];
-        // ---- phase A: q = H p, p = z + beta p_old ---------------------------
+        // ---- phase A: p = z + beta p over the window, q = H p ----------------
         {
             if (timer) t0 = globaltimer();
-            const CT bt = (CT)beta;
-            {  // stage p over the window (coalesced loads issued together)
-                const int nf = 3 * (whi - wlo);
-                const VT *zw = z + 3 * wlo, *pw = pold + 3 * wlo;
-                for (int f0 = threadIdx.x; f0 < nf; f0 += 8 * blockDim.x) {
+            const CT bt = mixed ? (CT)ctl.bt : (CT)ctl.beta;
+            {  // window z and the contacts' p: coalesced loads issued together
+                const int nf = 3 * nwin, ncf = 12 * ncached, ntot = nf + ncf;
+                const VT *zw = z + 3 * wlo;
+                for (int f0 = threadIdx.x; f0 < ntot; f0 += 8 * blockDim.x) {
                     VT zz[8], pp[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int f = f0 + k * blockDim.x;
-                        zz[k] = f < nf ? __ldcg(zw + f) : VT(0);
-                        pp[k] = f < nf ? __ldcg(pw + f) : VT(0);
+                        zz[k] = VT(0);
+                        pp[k] = VT(0);
+                        if (f < nf) {
+                            zz[k] = __ldcg(zw + f);
+                        } else if (f < ntot) {
+                            const int g = f - nf, kk = g / 12, q = (g % 12) / 3, j = g % 3;
+                            if (s_cm[kk] >> q & 1) {
+                                const int v = (&s_cv[kk].x)[q];
+                                zz[k] = __ldcg(z + 3 * v + j);
+                                pp[k] = __ldcg(pold + 3 * v + j);
+                            }
+                        }
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int f = f0 + k * blockDim.x;
-                        if (f < nf) s_p4[4 * (f / 3) + f % 3] = (CT)zz[k] + bt * (CT)pp[k];
+                        if (f < nf) {
+                            CT *d = s_p4 + 4 * (f / 3) + f % 3;
+                            *d = dir_update((CT)zz[k], bt, *d);
+                        } else if (f < ntot) {
+                            s_cp[f - nf] = dir_update((CT)zz[k], bt, (CT)pp[k]);
+                        }
                     }
                 }
             }
@@ -437,44 +540,88 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
             auto getp = [&](int vr, CT *o) { load3v(s_p4 + 4 * vr, o); };
             row_sums<CT>(ne, erow, getp, ent, s_q, ld);
             if (timer) tR += globaltimer() - t0;
-            auto getp_g = [&](int v, CT *o) {
+            // this CTA's contact pairs: y += mu gamma g (g . p) into qc
+            CT cdot = CT(0);
+            for (int k = threadIdx.x; k < nco; k += blockDim.x) {
+                CT g[12], u[12], w;
+                int vid[4], m;
+                if (k < ncached) {
+                    const int4 v = s_cv[k];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = s_cm[k];
+                    w = s_cw[k];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) o[k] = (CT)__ldcg(z + 3 * v + k) + bt * (CT)__ldcg(pold + 3 * v + k);
-            };
-            double v1[1] = {contact_pass<CT, VT>(A, getp_g, qc)};
+                    for (int j = 0; j < 12; ++j) {
+                        g[j] = s_cg[12 * k + j];
+                        u[j] = s_cp[12 * k + j];
+                    }
+                } else {
+                    const int i = c + k * (int)gridDim.x;
+                    const int4 v = A.cv[i];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = A.cmask[i];
+                    w = (CT)A.cw[i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
+                            u[3 * q + j] = (m >> q & 1) ? dir_update((CT)__ldcg(z + 3 * vid[q] + j), bt,
+                                                                     (CT)__ldcg(pold + 3 * vid[q] + j))
+                                                        : CT(0);
+                        }
+                }
+                CT s = CT(0);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) s += g[j] * u[j];
+                const CT t = w * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (m >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) atomicAdd(qc + 3 * vid[q] + j, (VT)(t * g[3 * q + j]));
+                cdot += t * s;
+            }
             __syncthreads();
             if (timer) tC += globaltimer() - t0;
-            CT pqs = CT(0);
+            Acc acc[1] = {};
+            acc_add(acc[0], cdot);  // p^T H_c p of this CTA's pairs
             for (int i = threadIdx.x; i < nr; i += blockDim.x) {
                 const int a = r0 + i;
                 CT p[3];
                 load3v(s_p4 + 4 * (a - wlo), p);
+                if (A.nc > 0)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) pnew[3 * a + k] = (VT)p[k];
-                pqs += p[0] * s_q[i] + p[1] * s_q[ld + i] + p[2] * s_q[2 * ld + i];
+                    for (int k = 0; k < 3; ++k) pnew[3 * a + k] = (VT)p[k];  // read by other CTAs' pairs
+                acc_add(acc[0], (p[0] * s_q[i] + p[1] * s_q[ld + i]) + p[2] * s_q[2 * ld + i]);
             }
-            v1[0] += (double)pqs;
             if (timer) {
                 const unsigned long long t1 = globaltimer();
                 tA += t1 - t0;
                 t0 = t1;
             }
-            if (!grid_reduce<1>(v1, A.res, nred, A.bar, A.dflag, pq)) return;
+            reduce(acc, [&](const double *t) {
+                const double pq = t[0];
+                if (!(pq > 0.0) || !isfinite(pq)) {
+                    // a zero direction after convergence is benign
+                    ctl.state = ctl.rr > A.tol2 * ctl.bb ? PCG_BAD : PCG_DONE;
+                } else {
+                    ctl.alpha = ctl.rz / pq;
+                    ctl.al = (float)ctl.alpha;
+                }
+            });
             if (timer) {
                 const unsigned long long t1 = globaltimer();
                 tA2 += t1 - t0;
                 t0 = t1;
             }
         }
-        if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
-            bad = rr > A.tol2 * bb;  // a zero direction after convergence is benign
-            goto finish;
-        }
+        if (ctl.state != PCG_RUN) break;
         // ---- phase B: x, r, z updates ---------------------------------------
         {
-            const double alpha = rz / pq[0];
-            const RT al = (RT)alpha;
-            double v[2] = {0.0, 0.0};
+            const double alpha = ctl.alpha;
+            const RT al = mixed ? (RT)ctl.al : (RT)alpha;
+            Acc acc[2] = {};
             for (int i = threadIdx.x; i < nr; i += blockDim.x) {
                 const int a = r0 + i;
                 VT qg[3];
@@ -487,35 +634,43 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
                 for (int k = 0; k < 3; ++k) {
                     if (mixed) s_xl[k * ld + i] += al * (RT)pc[k];
                     else s_x[k * ld + i] += alpha * (double)pc[k];
-                    const RT qv = (RT)s_q[k * ld + i] + (RT)qg[k];
-                    rv[k] = s_r[k * ld + i] - al * qv;
+                    rv[k] = s_r[k * ld + i] - al * ((RT)s_q[k * ld + i] + (RT)qg[k]);
                     s_r[k * ld + i] = rv[k];
                     s_q[k * ld + i] = CT(0);
                     qc[3 * a + k] = VT(0);
                 }
-                v[0] += precond(i, rv);
-                v[1] += rnorm(rv);
+                acc_add(acc[0], precond(i, rv));
+                acc_add(acc[1], ((CT)rv[0] * (CT)rv[0] + (CT)rv[1] * (CT)rv[1]) + (CT)rv[2] * (CT)rv[2]);
             }
             if (timer) {
                 const unsigned long long t1 = globaltimer();
                 tB += t1 - t0;
                 t0 = t1;
             }
-            if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
+            reduce(acc, [&](const double *t) {
+                ++ctl.it;
+                ctl.rz_old = ctl.rz;
+                ctl.beta = t[0] / ctl.rz_old;
+                ctl.bt = (float)ctl.beta;
+                ctl.rz = t[0];
+                ctl.rr = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1])) {
+                    ctl.state = PCG_BAD;
+                    return;
+                }
+                const bool done = ctl.rr <= A.tol2 * ctl.bb;
+                if (mixed && ctl.folds < A.max_replace && (done || ctl.rr <= 0.01 * ctl.rr_ref))
+                    ctl.state = PCG_FOLD;
+                else if (done)
+                    ctl.state = PCG_DONE;
+                else if (ctl.it >= A.maxit)
+                    ctl.state = PCG_MAXIT;
+            });
             if (timer) tB2 += globaltimer() - t0;
         }
-        ++it;
-        const double rz_old = rz;
-        beta = t2[0] / rz_old;
-        rz = t2[0];
-        rr = t2[1];
         parity ^= 1;
-        if (!isfinite(rr) || !isfinite(rz)) {
-            bad = 1;
-            goto finish;
-        }
-        bool done = rr <= A.tol2 * bb;
-        if (mixed && folds < A.max_replace && (done || rr <= 0.01 * rr_ref)) {
+        if constexpr (mixed) {
+        if (ctl.state == PCG_FOLD) {
             // reliable update: x += x_l in FP64, then r = b - H x with FP64
             // vectors (FP32 matrix); the direction p is kept and beta rescaled
             for (int i = threadIdx.x; i < nr; i += blockDim.x)
@@ -525,9 +680,13 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
                     s_x[k * ld + i] = xv;
                     s_xl[k * ld + i] = RT(0);
                     A.x[3 * (r0 + i) + k] = xv;
+                    s_hx[k * ld + i] = 0.0;
                 }
-            double dummy[1] = {0.0};
-            if (!grid_reduce<1>(dummy, A.res, nred, A.bar, A.dflag, dummy)) return;
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // x visible to every CTA
+            }
+            if (ctl.state == PCG_ABORT) break;
             auto getx = [&](int vr, double *o) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) o[k] = __ldcg(A.x + 3 * (wlo + vr) + k);
@@ -539,56 +698,75 @@ __global__ void __launch_bounds__(kPcgMaxThreads, 2) k_pcg_persistent(PcgArgs A)
                 for (int k = 0; k < 9; ++k) a[k] = (double)t[k];
                 return v;
             };
-            for (int i = threadIdx.x; i < 3 * ld; i += blockDim.x) s_hx[i] = 0.0;
-            __syncthreads();
             row_sums<double>(ne, erow, getx, ent64, s_hx, ld);
-            auto getx_g = [&](int v, double *o) {
+            for (int k = threadIdx.x; k < nco; k += blockDim.x) {
+                const int i = c + k * (int)gridDim.x;
+                const int4 v = A.cv[i];
+                const int mk = A.cmask[i];
+                const int vid[4] = {v.x, v.y, v.z, v.w};
+                double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) o[k] = __ldcg(A.x + 3 * v + k);
-            };
-            contact_pass<double, double>(A, getx_g, A.qd);
-            if (!grid_reduce<1>(dummy, A.res, nred, A.bar, A.dflag, dummy)) return;
-            double v[2] = {0.0, 0.0};
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) s += A.cg[12 * (size_t)i + 3 * q + j] * __ldcg(A.x + 3 * vid[q] + j);
+                const double t = A.cw[i] * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) atomicAdd(A.qd + 3 * vid[q] + j, t * A.cg[12 * (size_t)i + 3 * q + j]);
+            }
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // contact parts complete
+            }
+            if (ctl.state == PCG_ABORT) break;
+            AccF acc[2];
             for (int i = threadIdx.x; i < nr; i += blockDim.x) {
                 const int a = r0 + i;
                 RT rv[3];
+                double rr = 0.0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const double rh = A.b[3 * a + k] - s_hx[k * ld + i] - __ldcg(A.qd + 3 * a + k);
                     A.qd[3 * a + k] = 0.0;
-                    v[1] += rh * rh;
+                    rr += rh * rh;
                     rv[k] = (RT)rh;
                     s_r[k * ld + i] = rv[k];
                 }
-                v[0] += precond(i, rv);
+                acc_add(acc[0], (float)precond(i, rv));
+                acc_add(acc[1], rr);
             }
-            if (!grid_reduce<2>(v, A.res, nred, A.bar, A.dflag, t2)) return;
-            ++folds;
-            beta = t2[0] / rz_old;
-            rz = t2[0];
-            rr = t2[1];
-            rr_ref = rr;
-            done = rr <= A.tol2 * bb;
+            __syncthreads();  // s_hx (aliasing s_q) read by every thread before it is zeroed
+            for (int i = threadIdx.x; i < 3 * ld; i += blockDim.x) s_q[i] = CT(0);
+            reduce(acc, [&](const double *t) {
+                ++ctl.folds;
+                ctl.beta = t[0] / ctl.rz_old;
+                ctl.bt = (float)ctl.beta;
+                ctl.rz = t[0];
+                ctl.rr = t[1];
+                ctl.rr_ref = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
+                else if (ctl.rr <= A.tol2 * ctl.bb) ctl.state = PCG_DONE;
+                else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
+                else ctl.state = PCG_RUN;
+            });
         }
-        if (done) break;
-        if (it >= A.maxit) {
-            maxit_hit = 1;
-            break;
         }
     }
-finish:
     for (int i = threadIdx.x; i < nr; i += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             A.x[3 * (r0 + i) + k] = s_x[k * ld + i] + (mixed ? (double)s_xl[k * ld + i] : 0.0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.dflag[F_ITERS] = it;
-        A.dflag[F_MAXIT] = maxit_hit;
+        A.dflag[F_ITERS] = ctl.it;
+        A.dflag[F_MAXIT] = ctl.state == PCG_MAXIT;
         A.dflag[F_DONE] = 1;
-        if (bad) A.dflag[F_ERR] |= ERR_NONFINITE;
-        A.dscal[S_RR] = rr;
-        A.dscal[S_BB] = bb;
-        A.dscal[S_RZ] = rz;
+        if (ctl.state == PCG_BAD) A.dflag[F_ERR] |= ERR_NONFINITE;
+        A.dscal[S_RR] = ctl.rr;
+        A.dscal[S_BB] = ctl.bb;
+        A.dscal[S_RZ] = ctl.rz;
         A.dscal[S_T_SPMV] = 1e-6 * (double)tA;
         A.dscal[S_T_RED1] = 1e-6 * (double)tA2;
         A.dscal[S_T_UPD] = 1e-6 * (double)tB;
@@ -655,9 +833,11 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
     return check_cuda(cudaStreamSynchronize(S.stream));
 }
 
+
 // Chooses the launch: the resident variant when the blocks fit in shared
 // memory at the requested CTAs per SM (falling back to fewer CTAs per SM),
-// else the variant that streams the blocks from global memory.
+// else the variant that streams the blocks from global memory.  Shared
+// memory left over caches contact pairs (up to kPcgMaxCached per CTA).
 template <class MT, class VT>
 static int setup_persistent(Scene &S)
 {
@@ -669,18 +849,25 @@ static int setup_persistent(Scene &S)
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return BF_E_CUDA;
-    const int per_sm = std::max(1, S.pcg_ctas_per_sm);
+    const int per_sm = std::min(4, std::max(1, S.pcg_ctas_per_sm));
     for (int res = S.pcg_allow_resident ? 1 : 0; res >= 0; --res) {
+        auto kern = res ? k_pcg_persistent<MT, VT, true> : k_pcg_persistent<MT, VT, false>;
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BF_E_CUDA;
         for (int cps = per_sm; cps >= 1; --cps) {
             const int grid = nsm * cps;
+            if (grid > kPcgMaxGrid) continue;
+            const int block = (kPcgThreads / cps) & ~31;
             int mr = 0, me = 0, mw = 0;
             int st = make_partition(S, grid, &mr, &me, &mw);
             if (st == BF_E_CAPACITY) continue;
             if (st) return st;
-            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0);
-            if (L.total + 8192 > (size_t)smem_optin) continue;  // static shared memory of the kernel
-            const int block = kPcgMaxThreads;
-            auto kern = res ? k_pcg_persistent<MT, VT, true> : k_pcg_persistent<MT, VT, false>;
+            const size_t avail = (size_t)smem_optin - fa.sharedSizeBytes;
+            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, 0);
+            if (L0.total > avail) continue;
+            int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(sizeof(CT)));
+            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, kc).total > avail) --kc;
+            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, kc);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
@@ -692,6 +879,7 @@ static int setup_persistent(Scene &S)
             S.pcg_max_rows = mr;
             S.pcg_max_ent = me;
             S.pcg_max_win = mw;
+            S.pcg_kc = kc;
             return BF_OK;
         }
     }
@@ -737,6 +925,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.max_rows = S.pcg_max_rows;
     A.max_ent = S.pcg_max_ent;
     A.max_win = S.pcg_max_win;
+    A.kc = S.pcg_kc;
     A.dscal = S.dscal;
     A.dflag = S.dflag;
     cudaMemsetAsync(S.bar, 0, 4 * sizeof(unsigned), S.stream);

@@ -27,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=14)
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--timers", action="store_true", help="also report the per-phase time of CTA 0")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,6 +49,7 @@ def main(argv=None):
     B.bf_assemble(sim.h, xt, xd, xd, G)
     b = -G
     B.bf_set_pcg_mode(sim.h, 1)
+    B.bf_enable_timers(sim.h, args.timers)
     iters, ms = [], []
     for _ in range(args.solves):
         p = torch.zeros_like(xd)
@@ -58,11 +60,16 @@ def main(argv=None):
         ms.append(1e3 * (time.perf_counter() - t0))
         iters.append(it)
     info = sim.info()
+    phases = {}
+    if args.timers:
+        phases = {k[len("pcg_phase_"):]: round(1e3 * v[1] / v[0], 3)
+                  for k, v in B.bf_get_timers(sim.h).items() if k.startswith("pcg_phase_") and v[0]}
     print(json.dumps({"workload": "eight_cubes 16^3 Newton system after %d steps" % args.steps,
                       "precision": "mixed" if args.precision else "fp64", "nv": s.nv, "nnzb": info["nnzb"],
                       "contacts": len(keys), "iterations": iters, "ms_per_solve": [round(v, 3) for v in ms],
                       "us_per_iteration": [round(1e3 * m / max(i, 1), 3) for m, i in zip(ms, iters)],
-                      "pcg_config": B.bf_get_pcg_config(sim.h)}))
+                      "pcg_config": B.bf_get_pcg_config(sim.h),
+                      **({"us_per_iteration_by_phase_cta0": phases} if args.timers else {})}))
     sim.close()
     return 0
 
