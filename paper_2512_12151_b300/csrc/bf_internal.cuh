@@ -108,7 +108,9 @@ struct Scene {
     int pcg_ctas_per_sm = 1;  // persistent PCG: CTAs per SM (capped by occupancy)
     int pcg_allow_resident = 1;  // persistent PCG may keep the matrix in shared memory
     int pcg_max_rows = 0, pcg_max_ent = 0, pcg_max_win = 0, pcg_block = 256;
-    unsigned short *pcg_erow = nullptr;  // CTA-local row of every full-row entry
+    unsigned short *pcg_eslot = nullptr;  // persistent PCG: shared-memory slot of every full-row entry
+    int *pcg_rinfo = nullptr, *pcg_lvl = nullptr, *pcg_lvlptr = nullptr;  // rows by length, level offsets
+    int pcg_max_len = 0;
     int pcg_kc = 0;               // persistent PCG: contacts per CTA cached in shared memory
     int *win = nullptr;       // persistent PCG: staged vertex window per CTA
     std::vector<int> h_fnbr;

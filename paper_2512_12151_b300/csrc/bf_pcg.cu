@@ -11,10 +11,10 @@
 // rows.  The direction p over that window also stays in shared memory: each
 // iteration updates it in place, p = z + beta p, from the z values of the
 // window (16 bytes per vertex), so every CTA holds bit-identical copies of p
-// on the vertices it shares with others.  Consecutive threads then take
-// consecutive blocks (9 words per block: no bank conflicts), reduce the
-// products per row with a segmented warp scan and add each row segment to
-// shared memory once, so the SpMV needs no global atomics.
+// on the vertices it shares with others.  Each thread then takes a run of
+// consecutive blocks (stored interleaved, so that a warp reads consecutive
+// 9-word blocks: no bank conflicts), sums them per row in registers and adds
+// each row piece to shared memory once, so the SpMV needs no global atomics.
 //
 // Contact pairs (rank one: mu gamma g g^T) are dealt round-robin to the
 // CTAs (pair i -> CTA i % gridDim.x), so that each CTA carries an equal share
@@ -63,7 +63,8 @@ constexpr int kPcgMaxGrid = 1024;  // CTAs of one launch
 struct PcgArgs {
     int nv, nc;
     const int *part, *win, *frowptr;
-    const unsigned short *erow;
+    const unsigned short *eslot;     // shared-memory slot of every full-row entry (resident variant)
+    const int *rinfo, *lvl, *lvlptr;  // rows by decreasing length; level offsets per CTA
     const int *fnbr, *fblk;
     const void *val;
     const int4 *cv;
@@ -77,7 +78,7 @@ struct PcgArgs {
     double *res;
     unsigned *bar;
     double tol2;
-    int maxit, max_replace, max_rows, max_ent, max_win, kc;
+    int maxit, max_replace, max_rows, max_ent, max_win, max_len, kc;
     double *dscal;
     int *dflag;
 };
@@ -238,46 +239,31 @@ __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, un
     return true;
 }
 
-// Row sums of H u over the CTA's rows, added into s_q (component-major,
-// s_q[c * ldq + row], zeroed by the caller).  Consecutive threads take
-// consecutive entries; the products are reduced per row with a segmented
-// warp scan and each row segment is added to shared memory once.
-// getu(v_rel, out) loads u at window offset v_rel; ent(pos, a) loads the 9
-// block values of entry pos and returns the neighbour's window offset.
+// Row sums of H u over the CTA's rows, stored into s_q (component-major,
+// s_q[c * ldq + row]).  One thread per row; rows are taken in the CTA's
+// order of decreasing length, so the threads of a warp run loops of about
+// the same length.  rinfo[t] = (local row << 8) | row length of the t-th
+// row in that order; ent(t, row, j, a) loads the 9 values of the row's j-th
+// block and returns the neighbour's window offset; getu(v_rel, out) loads u
+// there.  Every row is written, so s_q needs no clearing.
 template <class CT, class GetU, class Ent>
-__device__ __forceinline__ void row_sums(int ne, const unsigned short *erow, GetU getu, Ent ent, CT *s_q, int ldq)
+__device__ __forceinline__ void row_sums(int nr, const int *rinfo, GetU getu, Ent ent, CT *s_q, int ldq)
 {
-    const int lane = threadIdx.x & 31;
-    for (int base = 0; base < ne; base += blockDim.x) {  // same trip count in every thread
-        const int e = base + threadIdx.x;
-        int row = -1;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const int info = rinfo[t];
+        const int row = info >> 8, len = info & 255;
         CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
-        if (e < ne) {
-            row = erow[e];
+#pragma unroll 2
+        for (int j = 0; j < len; ++j) {
             CT a[9], u[3];
-            getu(ent(e, a), u);
-            y0 = a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
-            y1 = a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
-            y2 = a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
+            getu(ent(t, row, j, a), u);
+            y0 += a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
+            y1 += a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
+            y2 += a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
         }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const CT t0 = __shfl_up_sync(0xffffffffu, y0, o);
-            const CT t1 = __shfl_up_sync(0xffffffffu, y1, o);
-            const CT t2 = __shfl_up_sync(0xffffffffu, y2, o);
-            const int ru = __shfl_up_sync(0xffffffffu, row, o);
-            if (lane >= o && ru == row) {
-                y0 += t0;
-                y1 += t1;
-                y2 += t2;
-            }
-        }
-        const int rn = __shfl_down_sync(0xffffffffu, row, 1);
-        if (row >= 0 && (lane == 31 || rn != row)) {
-            atomicAdd(s_q + row, y0);
-            atomicAdd(s_q + ldq + row, y1);
-            atomicAdd(s_q + 2 * ldq + row, y2);
-        }
+        s_q[row] = y0;
+        s_q[ldq + row] = y1;
+        s_q[2 * ldq + row] = y2;
     }
 }
 
@@ -300,11 +286,11 @@ __device__ __forceinline__ double dir_update(double z, double bt, double p) { re
 // Shared-memory layout of the persistent PCG (byte offsets, 16-byte aligned
 // sections), shared by the kernel and the host-side sizing.
 struct PcgLayout {
-    size_t x, xl, r, q, pinv, p4, val, nbr, erow, cg, cp, cw, cv, cm, total;
+    size_t x, xl, r, q, pinv, p4, val, nbr, rinfo, lvl, cg, cp, cw, cv, cm, total;
 };
 
 __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
-                                                bool res, int kc)
+                                                int max_len, bool res, int kc)
 {
     PcgLayout L;
     size_t o = 0;
@@ -322,7 +308,8 @@ __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int 
     L.p4 = take(4 * (size_t)max_win * ct);
     L.val = take(res ? 9 * (size_t)max_ent * mt : 0);
     L.nbr = take(res ? (size_t)max_ent * 2 : 0);
-    L.erow = take(res ? (size_t)max_ent * 2 : 0);
+    L.rinfo = take((size_t)max_rows * 4);
+    L.lvl = take(((size_t)max_len + 1) * 4);
     L.cg = take(12 * (size_t)kc * ct);
     L.cp = take(12 * (size_t)kc * ct);
     L.cw = take((size_t)kc * ct);
@@ -358,7 +345,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     const int E0 = A.frowptr[r0], ne = A.frowptr[r1] - E0;  // the CTA's full-row entries
     const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;  // pairs c + k grid
     const int ncached = min(nco, A.kc);
-    const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, RES, A.kc);
+    const PcgLayout L =
+        pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, A.max_len, RES, A.kc);
     const int ld = A.max_rows;  // per-row arrays are component-major: a[c * ld + row]
     double *s_x = (double *)(smem + L.x);
     RT *s_xl = (RT *)(smem + L.xl);
@@ -369,20 +357,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     CT *s_p4 = (CT *)(smem + L.p4);
     MT *s_val = (MT *)(smem + L.val);
     unsigned short *s_nbr = (unsigned short *)(smem + L.nbr);
-    unsigned short *s_erow = (unsigned short *)(smem + L.erow);
+    int *s_rinfo = (int *)(smem + L.rinfo);
+    int *s_lvl = (int *)(smem + L.lvl);
     CT *s_cg = (CT *)(smem + L.cg);
     CT *s_cp = (CT *)(smem + L.cp);
     CT *s_cw = (CT *)(smem + L.cw);
     int4 *s_cv = (int4 *)(smem + L.cv);
     int *s_cm = (int *)(smem + L.cm);
-    const unsigned short *erow = RES ? s_erow : A.erow + E0;
     for (int i = threadIdx.x; i < 9 * nr; i += blockDim.x) s_pinv[i] = gpinv[9 * (size_t)r0 + i];
     if (RES) {
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             const int fe = E0 + e;
             const int fb = A.fblk[fe];
+            const int slot = A.eslot[fe];
             const MT *src = gval + 9 * (size_t)(fb & 0x7fffffff);
-            MT *dst = s_val + 9 * e;
+            MT *dst = s_val + 9 * slot;
             if (fb < 0) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
@@ -392,10 +381,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 #pragma unroll
                 for (int i = 0; i < 9; ++i) dst[i] = src[i];
             }
-            s_nbr[e] = (unsigned short)(A.fnbr[fe] - wlo);
-            s_erow[e] = A.erow[fe];
+            s_nbr[slot] = (unsigned short)(A.fnbr[fe] - wlo);
         }
+        for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
     }
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) s_rinfo[t] = A.rinfo[r0 + t];
     for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
         const int i = c + k * (int)gridDim.x;
         s_cv[k] = A.cv[i];
@@ -405,16 +395,18 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
         for (int j = 0; j < 12; ++j) s_cg[12 * k + j] = (CT)A.cg[12 * (size_t)i + j];
     }
     for (int i = threadIdx.x; i < 4 * nwin; i += blockDim.x) s_p4[i] = CT(0);  // p_old = 0
-    // block values of local entry pos (row-major, lower blocks transposed);
+    // values of the j-th block of local row `row` (row-major, lower blocks
+    // transposed; in shared memory at level j, position t of the row order);
     // returns the neighbour's window offset
-    auto ent = [&](int pos, CT *a) -> int {
+    auto ent = [&](int t, int row, int j, CT *a) -> int {
         if (RES) {
-            const MT *t = s_val + 9 * pos;
+            const int slot = s_lvl[j] + t;
+            const MT *v = s_val + 9 * slot;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) a[i] = (CT)t[i];
-            return s_nbr[pos];
+            for (int i = 0; i < 9; ++i) a[i] = (CT)v[i];
+            return s_nbr[slot];
         } else {
-            const int fe = E0 + pos;
+            const int fe = __ldg(A.frowptr + r0 + row) + j;
             const int fb = __ldg(A.fblk + fe);
             const MT *src = gval + 9 * (size_t)(fb & 0x7fffffff);
             if (fb < 0) {
@@ -473,7 +465,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 s_r[k * ld + i] = rv[k];
                 s_x[k * ld + i] = 0.0;
                 if (mixed) s_xl[k * ld + i] = RT(0);
-                s_q[k * ld + i] = CT(0);
                 qc[3 * a + k] = VT(0);
                 if (mixed) A.qd[3 * a + k] = 0.0;
                 if (A.nc > 0) pb[0][3 * a + k] = VT(0);
@@ -538,7 +529,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             __syncthreads();
             if (timer) tS += globaltimer() - t0;
             auto getp = [&](int vr, CT *o) { load3v(s_p4 + 4 * vr, o); };
-            row_sums<CT>(ne, erow, getp, ent, s_q, ld);
+            row_sums<CT>(nr, s_rinfo, getp, ent, s_q, ld);
             if (timer) tR += globaltimer() - t0;
             // this CTA's contact pairs: y += mu gamma g (g . p) into qc
             CT cdot = CT(0);
@@ -636,7 +627,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                     else s_x[k * ld + i] += alpha * (double)pc[k];
                     rv[k] = s_r[k * ld + i] - al * ((RT)s_q[k * ld + i] + (RT)qg[k]);
                     s_r[k * ld + i] = rv[k];
-                    s_q[k * ld + i] = CT(0);
                     qc[3 * a + k] = VT(0);
                 }
                 acc_add(acc[0], precond(i, rv));
@@ -680,7 +670,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                     s_x[k * ld + i] = xv;
                     s_xl[k * ld + i] = RT(0);
                     A.x[3 * (r0 + i) + k] = xv;
-                    s_hx[k * ld + i] = 0.0;
                 }
             {
                 AccF none[1];
@@ -691,14 +680,14 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) o[k] = __ldcg(A.x + 3 * (wlo + vr) + k);
             };
-            auto ent64 = [&](int pos, double *a) -> int {
-                CT t[9];
-                const int v = ent(pos, t);
+            auto ent64 = [&](int t, int row, int j, double *a) -> int {
+                CT tv[9];
+                const int v = ent(t, row, j, tv);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) a[k] = (double)t[k];
+                for (int k = 0; k < 9; ++k) a[k] = (double)tv[k];
                 return v;
             };
-            row_sums<double>(ne, erow, getx, ent64, s_hx, ld);
+            row_sums<double>(nr, s_rinfo, getx, ent64, s_hx, ld);
             for (int k = threadIdx.x; k < nco; k += blockDim.x) {
                 const int i = c + k * (int)gridDim.x;
                 const int4 v = A.cv[i];
@@ -738,8 +727,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 acc_add(acc[0], (float)precond(i, rv));
                 acc_add(acc[1], rr);
             }
-            __syncthreads();  // s_hx (aliasing s_q) read by every thread before it is zeroed
-            for (int i = threadIdx.x; i < 3 * ld; i += blockDim.x) s_q[i] = CT(0);
             reduce(acc, [&](const double *t) {
                 ++ctl.folds;
                 ctl.beta = t[0] / ctl.rz_old;
@@ -778,9 +765,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 }
 
 // Row ranges of the CTAs (about equal block counts), each CTA's vertex
-// window (its rows and all their neighbours) and the CTA-local row of every
-// full-row entry.
-static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *max_win)
+// window (its rows and all their neighbours), and the jagged shared-memory
+// layout of each CTA's blocks: rows in order of decreasing length (ties by
+// row), level j holding the j-th block of every row longer than j, so the
+// j-th block of the t-th row sits at slot lvl[j] + t.
+static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *max_win, int *max_len)
 {
     const std::vector<int> &fr = S.h_frowptr;
     const std::vector<int> &fn = S.h_fnbr;
@@ -794,25 +783,45 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
         part[c] = std::max(part[c - 1], r);
     }
     part[grid] = S.nv;
-    std::vector<int> win(2 * grid);
-    std::vector<unsigned short> erow(S.nfull);
-    int mr = 0, me = 0, mw = 0;
+    std::vector<int> win(2 * grid), rinfo(S.nv), lvl, lvlptr(grid + 1, 0);
+    std::vector<unsigned short> eslot(S.nfull);
+    int mr = 0, me = 0, mw = 0, ml = 0;
+    std::vector<int> order;
     for (int c = 0; c < grid; ++c) {
         const int a = part[c], b = part[c + 1];
-        if (b - a > 65535) return BF_E_CAPACITY;
+        if (b - a > 65535 || fr[b] - fr[a] > 65535) return BF_E_CAPACITY;
         int lo = a, hi = b;
         for (int v = a; v < b; ++v)
             for (int e = fr[v]; e < fr[v + 1]; ++e) {
-                erow[e] = (unsigned short)(v - a);
                 lo = std::min(lo, fn[e]);
                 hi = std::max(hi, fn[e] + 1);
             }
         if (hi - lo > 65535) return BF_E_CAPACITY;
         win[2 * c] = lo;
         win[2 * c + 1] = hi;
+        order.resize(b - a);
+        for (int v = a; v < b; ++v) order[v - a] = v;
+        auto len = [&](int v) { return fr[v + 1] - fr[v]; };
+        std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return len(u) > len(v); });
+        const int lmax = b > a ? len(order[0]) : 0;
+        if (lmax > 255) return BF_E_CAPACITY;
+        std::vector<int> at(lmax + 1, 0);  // level offsets
+        for (int j = 0; j < lmax; ++j) {
+            int n = 0;
+            while (n < b - a && len(order[n]) > j) ++n;
+            at[j + 1] = at[j] + n;
+        }
+        for (int t = 0; t < b - a; ++t) {
+            const int v = order[t];
+            rinfo[a + t] = (v - a) << 8 | len(v);
+            for (int j = 0; j < len(v); ++j) eslot[fr[v] + j] = (unsigned short)(at[j] + t);
+        }
+        lvl.insert(lvl.end(), at.begin(), at.end());
+        lvlptr[c + 1] = (int)lvl.size();
         mr = std::max(mr, b - a);
         me = std::max(me, fr[b] - fr[a]);
         mw = std::max(mw, hi - lo);
+        ml = std::max(ml, lmax);
     }
     auto put = [&](auto *&dst, const auto &host) -> int {
         using T = std::remove_reference_t<decltype(*dst)>;
@@ -825,11 +834,15 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
     };
     int st = put(S.part, part);
     if (!st) st = put(S.win, win);
-    if (!st) st = put(S.pcg_erow, erow);
+    if (!st) st = put(S.pcg_eslot, eslot);
+    if (!st) st = put(S.pcg_rinfo, rinfo);
+    if (!st) st = put(S.pcg_lvl, lvl);
+    if (!st) st = put(S.pcg_lvlptr, lvlptr);
     if (st) return st;
     *max_rows = mr;
     *max_ent = me;
     *max_win = mw;
+    *max_len = ml;
     return check_cuda(cudaStreamSynchronize(S.stream));
 }
 
@@ -858,16 +871,16 @@ static int setup_persistent(Scene &S)
             const int grid = nsm * cps;
             if (grid > kPcgMaxGrid) continue;
             const int block = (kPcgThreads / cps) & ~31;
-            int mr = 0, me = 0, mw = 0;
-            int st = make_partition(S, grid, &mr, &me, &mw);
+            int mr = 0, me = 0, mw = 0, ml = 0;
+            int st = make_partition(S, grid, &mr, &me, &mw, &ml);
             if (st == BF_E_CAPACITY) continue;
             if (st) return st;
             const size_t avail = (size_t)smem_optin - fa.sharedSizeBytes;
-            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, 0);
+            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, 0);
             if (L0.total > avail) continue;
             int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(sizeof(CT)));
-            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, kc).total > avail) --kc;
-            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, res != 0, kc);
+            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc).total > avail) --kc;
+            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
@@ -879,6 +892,7 @@ static int setup_persistent(Scene &S)
             S.pcg_max_rows = mr;
             S.pcg_max_ent = me;
             S.pcg_max_win = mw;
+            S.pcg_max_len = ml;
             S.pcg_kc = kc;
             return BF_OK;
         }
@@ -901,7 +915,10 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.part = S.part;
     A.win = S.win;
     A.frowptr = S.frowptr;
-    A.erow = S.pcg_erow;
+    A.eslot = S.pcg_eslot;
+    A.rinfo = S.pcg_rinfo;
+    A.lvl = S.pcg_lvl;
+    A.lvlptr = S.pcg_lvlptr;
     A.fnbr = S.fnbr;
     A.fblk = S.fblk;
     A.val = val;
@@ -925,6 +942,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.max_rows = S.pcg_max_rows;
     A.max_ent = S.pcg_max_ent;
     A.max_win = S.pcg_max_win;
+    A.max_len = S.pcg_max_len;
     A.kc = S.pcg_kc;
     A.dscal = S.dscal;
     A.dflag = S.dflag;
