@@ -266,6 +266,12 @@ static int step_once(Scene &S, bf_step_stats *out)
             k_apply_targets<<<cdiv(S.ndir, kThreads), kThreads, 0, S.stream>>>(S.ndir, S.dir_ids, S.targets, S.xh); ++S.n_launch;
         }
     S.delta = S.prm.delta;
+    S.bvh_tri.topo_valid = S.bvh_edge.topo_valid = 0;  // one tree topology per time step
+    S.bvh_reuse = true;
+    struct ReuseOff {
+        Scene &s;
+        ~ReuseOff() { s.bvh_reuse = false; }
+    } reuse_off{S};
     mu_init(S, S.xtilde, S.xh);
     if (!(S.mu > 0.0) || !std::isfinite(S.mu)) return BF_E_NONFINITE;
     double beta = 1.0, asum = 0.0;

@@ -340,7 +340,8 @@ __device__ __forceinline__ int lcp(const unsigned *__restrict__ m, int n, int i,
     return __clz(a ^ b);
 }
 
-__global__ void k_radix_tree(int n, const unsigned *__restrict__ m, int2 *__restrict__ child, int *__restrict__ parent)
+__global__ void k_radix_tree(int n, const unsigned *__restrict__ m, int2 *__restrict__ child, int *__restrict__ parent,
+                             int *__restrict__ rend)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
@@ -363,13 +364,42 @@ __global__ void k_radix_tree(int n, const unsigned *__restrict__ m, int2 *__rest
     const int left = (min(i, j) == gamma) ? (n - 1 + gamma) : gamma;
     const int right = (max(i, j) == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
     child[i] = make_int2(left, right);
+    rend[i] = max(i, j);  // the node covers leaves [min(i, j), max(i, j)]
     parent[left] = i;
     parent[right] = i;
 }
 
+// Packed internal node for traversal: both children's boxes in FP32,
+// rounded outwards (a conservative superset of the FP64 boxes), their node
+// indices and the last leaf position under each:
+//   a = (L.lo.x, L.lo.y, L.lo.z, L.hi.x), b = (L.hi.y, L.hi.z, R.lo.x, R.lo.y),
+//   c = (R.lo.z, R.hi.x, R.hi.y, R.hi.z), d = (left, right, last(L), last(R)).
+__device__ __forceinline__ void pack_node(float4 *node, int par, int2 ch, int n, const int *__restrict__ rend,
+                                          const double *lo, const double *hi)
+{
+    float b[12];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int cid = k ? ch.y : ch.x;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            b[6 * k + c] = __double2float_rd(__ldcg(lo + 3 * (size_t)cid + c));
+            b[6 * k + 3 + c] = __double2float_ru(__ldcg(hi + 3 * (size_t)cid + c));
+        }
+    }
+    const int lastl = ch.x >= n - 1 ? ch.x - (n - 1) : rend[ch.x];
+    const int lastr = ch.y >= n - 1 ? ch.y - (n - 1) : rend[ch.y];
+    float4 *o = node + 4 * (size_t)par;
+    o[0] = make_float4(b[0], b[1], b[2], b[3]);
+    o[1] = make_float4(b[4], b[5], b[6], b[7]);
+    o[2] = make_float4(b[8], b[9], b[10], b[11]);
+    o[3] = make_float4(__int_as_float(ch.x), __int_as_float(ch.y), __int_as_float(lastl), __int_as_float(lastr));
+}
+
 __global__ void k_refit(int n, const int *__restrict__ prim, const int2 *__restrict__ child,
-                        const int *__restrict__ parent, int *__restrict__ flags, const double *__restrict__ plo,
-                        const double *__restrict__ phi, double *lo, double *hi)
+                        const int *__restrict__ parent, const int *__restrict__ rend, int *__restrict__ flags,
+                        const double *__restrict__ plo, const double *__restrict__ phi, double *lo, double *hi,
+                        float4 *node_out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -395,6 +425,7 @@ __global__ void k_refit(int n, const int *__restrict__ prim, const int2 *__restr
             lo[3 * (size_t)par + c] = fmin(__ldcg(lo + 3 * (size_t)ch.x + c), __ldcg(lo + 3 * (size_t)ch.y + c));
             hi[3 * (size_t)par + c] = fmax(__ldcg(hi + 3 * (size_t)ch.x + c), __ldcg(hi + 3 * (size_t)ch.y + c));
         }
+        pack_node(node_out, par, ch, n, rend, lo, hi);
         node = par;
     }
 }
@@ -411,7 +442,8 @@ static int bvh_reserve(Scene &S, LBVH &T, int n)
 {
     if (n <= T.cap) return BF_OK;
     int cap = std::max(n, 16);
-    void *old[] = {T.morton, T.morton_alt, T.prim, T.prim_alt, T.child, T.parent, T.flags, T.lo, T.hi, T.plo, T.phi};
+    void *old[] = {T.morton, T.morton_alt, T.prim, T.prim_alt, T.child, T.parent, T.flags, T.lo, T.hi, T.plo, T.phi,
+                   T.rend, T.node};
     for (void *p : old)
         if (p) dev_free(S, p);
     T.morton = (unsigned *)dev_alloc(S, cap * sizeof(unsigned));
@@ -425,16 +457,23 @@ static int bvh_reserve(Scene &S, LBVH &T, int n)
     T.hi = (double *)dev_alloc(S, 2 * 3 * (size_t)cap * sizeof(double));
     T.plo = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
     T.phi = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
+    T.rend = (int *)dev_alloc(S, cap * sizeof(int));
+    T.node = (float4 *)dev_alloc(S, 4 * (size_t)cap * sizeof(float4));
     if (!T.morton || !T.morton_alt || !T.prim || !T.prim_alt || !T.child || !T.parent || !T.flags || !T.lo || !T.hi ||
-        !T.plo || !T.phi)
+        !T.plo || !T.phi || !T.rend || !T.node)
         return BF_E_OOM;
     T.cap = cap;
+    T.topo_valid = 0;
     return BF_OK;
 }
 
+// Builds the tree over the swept boxes along x0 -> x1, or, when the scene
+// allows it (within one time step) and the topology of an earlier build is
+// still held, only refits its boxes: any topology gives the same candidates.
 template <int NV>
 static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0, const double *x1)
 {
+    if (T.n != n) T.topo_valid = 0;
     T.n = n;
     if (n == 0) return BF_OK;
     int st = bvh_reserve(S, T, n);
@@ -442,6 +481,12 @@ static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0,
     ScopedTimer tm(S, T_BVH);
     const int nb = cdiv(n, kThreads);
     k_prim_boxes<NV><<<nb, kThreads, 0, S.stream>>>(n, ids, x0, x1, T.plo, T.phi); ++S.n_launch;
+    if (S.bvh_reuse && T.topo_valid) {
+        cudaMemsetAsync(T.flags, 0, (n + 1) * sizeof(int), S.stream);
+        k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.rend, T.flags, T.plo, T.phi, T.lo, T.hi,
+                                               T.node); ++S.n_launch;
+        return BF_OK;
+    }
     int init[6];
     for (int c = 0; c < 3; ++c) {
         init[c] = 0x7f800000;           // +inf as ordered int
@@ -461,9 +506,11 @@ static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0,
         std::swap(T.morton, T.morton_alt);
         std::swap(T.prim, T.prim_alt);
     }
-    if (n > 1) k_radix_tree<<<cdiv(n - 1, kThreads), kThreads, 0, S.stream>>>(n, T.morton, T.child, T.parent); ++S.n_launch;
+    if (n > 1) k_radix_tree<<<cdiv(n - 1, kThreads), kThreads, 0, S.stream>>>(n, T.morton, T.child, T.parent, T.rend); ++S.n_launch;
     cudaMemsetAsync(T.flags, 0, (n + 1) * sizeof(int), S.stream);
-    k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.flags, T.plo, T.phi, T.lo, T.hi); ++S.n_launch;
+    k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.rend, T.flags, T.plo, T.phi, T.lo, T.hi,
+                                           T.node); ++S.n_launch;
+    T.topo_valid = 1;
     return BF_OK;
 }
 
@@ -472,15 +519,34 @@ __device__ __forceinline__ bool box_overlap(const double *l1, const double *h1, 
     return !(l1[0] > h2[0] || l2[0] > h1[0] || l1[1] > h2[1] || l2[1] > h1[1] || l1[2] > h2[2] || l2[2] > h1[2]);
 }
 
-// queries: vertices against the triangle tree (type PT) or edges against
-// the edge tree (type EE, b > a only)
-template <int TYPE>
-__global__ void k_query(int nq, const int *__restrict__ qids, const double *__restrict__ x0,
-                        const double *__restrict__ x1, int n, const int2 *__restrict__ child,
-                        const int *__restrict__ prim, const double *__restrict__ lo, const double *__restrict__ hi,
-                        const int *__restrict__ st, const int *__restrict__ se, const uint8_t *__restrict__ dir,
-                        int2 *__restrict__ cand, int cap, int *count, int *dflag)
+__device__ __forceinline__ bool box_overlap_f(const float *ql, const float *qh, float4 a, float4 b, float4 c, int k)
 {
+    // child k of a packed node: k = 0 -> (a.xyz, a.w b.xy), k = 1 -> (b.zw c.x, c.yzw)
+    const float l0 = k ? b.z : a.x, l1 = k ? b.w : a.y, l2 = k ? c.x : a.z;
+    const float h0 = k ? c.y : a.w, h1 = k ? c.z : b.x, h2 = k ? c.w : b.y;
+    return !(ql[0] > h0 || l0 > qh[0] || ql[1] > h1 || l1 > qh[1] || ql[2] > h2 || l2 > qh[2]);
+}
+
+constexpr int kQueryThreads = 128;
+constexpr int kQueryStack = 64;
+
+// Queries: surface vertices against the triangle tree (type PT), or each
+// edge leaf against the edge leaves after it in the tree's leaf order (type
+// EE; subtrees whose last leaf is not after the query leaf are skipped, so
+// every edge pair is met once).  Internal nodes are culled with their FP32
+// outward-rounded boxes; a leaf is accepted only by the exact FP64
+// closed-box test, so the candidates are exactly the pairs whose swept boxes
+// overlap.  The traversal stack lives in shared memory.
+template <int TYPE>
+__global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__restrict__ qids,
+                                                         const double *__restrict__ x0, const double *__restrict__ x1,
+                                                         int n, const float4 *__restrict__ node,
+                                                         const int *__restrict__ prim, const double *__restrict__ lo,
+                                                         const double *__restrict__ hi, const int *__restrict__ st,
+                                                         const int *__restrict__ se, const uint8_t *__restrict__ dir,
+                                                         int2 *__restrict__ cand, int cap, int *count, int *dflag)
+{
+    __shared__ int stack[kQueryStack * kQueryThreads];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq || n == 0) return;
     double ql[3], qh[3];
@@ -494,50 +560,75 @@ __global__ void k_query(int nq, const int *__restrict__ qids, const double *__re
             ql[c] = fmin(a, b);
             qh[c] = fmax(a, b);
         }
-    } else {
-        qa = q;
-        qv0 = se[2 * q];
-        qv1 = se[2 * q + 1];
+    } else {  // q is a leaf position of the edge tree
+        qa = prim[q];
+        qv0 = se[2 * qa];
+        qv1 = se[2 * qa + 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double a = x0[3 * qv0 + c], b = x1[3 * qv0 + c], a2 = x0[3 * qv1 + c], b2 = x1[3 * qv1 + c];
-            ql[c] = fmin(fmin(a, b), fmin(a2, b2));
-            qh[c] = fmax(fmax(a, b), fmax(a2, b2));
+            ql[c] = lo[3 * (size_t)(n - 1 + q) + c];
+            qh[c] = hi[3 * (size_t)(n - 1 + q) + c];
         }
     }
+    float fl[3], fh[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        fl[c] = __double2float_rd(ql[c]);
+        fh[c] = __double2float_ru(qh[c]);
+    }
     const bool qdir = TYPE == PT ? dir[qv0] != 0 : (dir[qv0] && dir[qv1]);
-    int stack[64];
+    // a leaf (node index >= n - 1): exact test, pair filters, emit
+    auto leaf = [&](int nodeid) {
+        const int k = nodeid - (n - 1);
+        if (TYPE == EE && k <= q) return;
+        const double *l2 = lo + 3 * (size_t)nodeid, *h2 = hi + 3 * (size_t)nodeid;
+        if (ql[0] > h2[0] || l2[0] > qh[0] || ql[1] > h2[1] || l2[1] > qh[1] || ql[2] > h2[2] || l2[2] > qh[2])
+            return;
+        const int b = prim[k];
+        bool ok;
+        if (TYPE == PT) {
+            const int t0 = st[3 * b], t1 = st[3 * b + 1], t2 = st[3 * b + 2];
+            ok = qv0 != t0 && qv0 != t1 && qv0 != t2 && !(qdir && dir[t0] && dir[t1] && dir[t2]);
+        } else {
+            const int e0 = se[2 * b], e1 = se[2 * b + 1];
+            ok = e0 != qv0 && e0 != qv1 && e1 != qv0 && e1 != qv1 && !(qdir && dir[e0] && dir[e1]);
+        }
+        if (ok) {
+            const int idx = atomicAdd(count, 1);
+            if (idx < cap) cand[idx] = TYPE == PT ? make_int2(qa, b) : make_int2(min(qa, b), max(qa, b));
+        }
+    };
+    if (n == 1) {
+        leaf(0);
+        return;
+    }
+    int *stk = stack + threadIdx.x;
     int sp = 0;
-    stack[sp++] = 0;
+    stk[0] = 0;
+    sp = 1;
     for (int visits = 0; sp > 0; ++visits) {
-        if (visits > 2 * n + 64) {  // a tree has 2n - 1 nodes
+        if (visits > 2 * n + 64) {  // a tree has n - 1 internal nodes
             atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
             return;
         }
-        const int node = stack[--sp];
-        if (!box_overlap(ql, qh, lo + 3 * (size_t)node, hi + 3 * (size_t)node)) continue;
-        if (node >= n - 1) {
-            const int b = prim[node - (n - 1)];
-            bool ok;
-            if (TYPE == PT) {
-                const int t0 = st[3 * b], t1 = st[3 * b + 1], t2 = st[3 * b + 2];
-                ok = qv0 != t0 && qv0 != t1 && qv0 != t2 && !(qdir && dir[t0] && dir[t1] && dir[t2]);
+        const int nd = stk[--sp * kQueryThreads];
+        const float4 *p = node + 4 * (size_t)nd;
+        const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+        const int ch[2] = {__float_as_int(d.x), __float_as_int(d.y)};
+        const int last[2] = {__float_as_int(d.z), __float_as_int(d.w)};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (TYPE == EE && last[k] <= q) continue;
+            if (!box_overlap_f(fl, fh, a, b, c, k)) continue;
+            if (ch[k] >= n - 1) {
+                leaf(ch[k]);
             } else {
-                const int e0 = se[2 * b], e1 = se[2 * b + 1];
-                ok = b > qa && e0 != qv0 && e0 != qv1 && e1 != qv0 && e1 != qv1 && !(qdir && dir[e0] && dir[e1]);
+                if (sp >= kQueryStack) {
+                    atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
+                    return;
+                }
+                stk[sp++ * kQueryThreads] = ch[k];
             }
-            if (ok) {
-                const int idx = atomicAdd(count, 1);
-                if (idx < cap) cand[idx] = make_int2(qa, b);
-            }
-        } else {
-            const int2 ch = child[node];
-            if (sp + 2 > 64) {
-                atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
-                return;
-            }
-            stack[sp++] = ch.x;
-            stack[sp++] = ch.y;
         }
     }
 }
@@ -713,17 +804,15 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         cudaMemsetAsync(S.dflag + F_NCAND_PT, 0, 2 * sizeof(int), S.stream);
         if (S.nsv && S.nst)
             {
-                k_query<PT><<<cdiv(S.nsv, 128), 128, 0, S.stream>>>(S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.child,
-                                                                S.bvh_tri.prim, S.bvh_tri.lo, S.bvh_tri.hi, S.st,
-                                                                S.se, S.dir, S.cand_pt, S.cand_cap,
-                                                                S.dflag + F_NCAND_PT, S.dflag); ++S.n_launch;
+                k_query<PT><<<cdiv(S.nsv, kQueryThreads), kQueryThreads, 0, S.stream>>>(
+                    S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.node, S.bvh_tri.prim, S.bvh_tri.lo, S.bvh_tri.hi, S.st,
+                    S.se, S.dir, S.cand_pt, S.cand_cap, S.dflag + F_NCAND_PT, S.dflag); ++S.n_launch;
             }
         if (S.nse > 1)
             {
-                k_query<EE><<<cdiv(S.nse, 128), 128, 0, S.stream>>>(S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.child,
-                                                                S.bvh_edge.prim, S.bvh_edge.lo, S.bvh_edge.hi, S.st,
-                                                                S.se, S.dir, S.cand_ee, S.cand_cap,
-                                                                S.dflag + F_NCAND_EE, S.dflag); ++S.n_launch;
+                k_query<EE><<<cdiv(S.nse, kQueryThreads), kQueryThreads, 0, S.stream>>>(
+                    S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.node, S.bvh_edge.prim, S.bvh_edge.lo,
+                    S.bvh_edge.hi, S.st, S.se, S.dir, S.cand_ee, S.cand_cap, S.dflag + F_NCAND_EE, S.dflag); ++S.n_launch;
             }
         st = sync_flags(S);
         if (st) return st;

@@ -55,6 +55,9 @@ struct LBVH {
     int *flags = nullptr;
     double *lo = nullptr, *hi = nullptr;  // 3 per node
     double *plo = nullptr, *phi = nullptr;  // exact primitive boxes, 3 per primitive
+    int *rend = nullptr;       // last leaf position under each internal node
+    float4 *node = nullptr;    // packed internal nodes for traversal (4 float4 each)
+    int topo_valid = 0;        // the topology may be refitted instead of rebuilt
 };
 
 struct Scene {
@@ -136,6 +139,7 @@ struct Scene {
     unsigned long long *ckey = nullptr, *ckey_sorted = nullptr;
     // CCD work
     LBVH bvh_tri, bvh_edge;
+    bool bvh_reuse = false;  // within a time step: refit the trees instead of rebuilding them
     int cand_cap = 0;
     int2 *cand_pt = nullptr, *cand_ee = nullptr;
     int hit_cap = 0;
