@@ -332,101 +332,71 @@ __global__ void k_morton(int n, const double *__restrict__ lo, const double *__r
     prim[i] = i;
 }
 
-__device__ __forceinline__ int lcp(const unsigned *__restrict__ m, int n, int i, int j)
-{
-    if (j < 0 || j >= n) return -1;
-    const unsigned a = m[i], b = m[j];
-    if (a == b) return 32 + __clz((unsigned)(i ^ j));
-    return __clz(a ^ b);
-}
-
-__global__ void k_radix_tree(int n, const unsigned *__restrict__ m, int2 *__restrict__ child, int *__restrict__ parent,
-                             int *__restrict__ rend)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    const int d = (lcp(m, n, i, i + 1) - lcp(m, n, i, i - 1)) > 0 ? 1 : -1;
-    const int dmin = lcp(m, n, i, i - d);
-    int lmax = 2;
-    while (lcp(m, n, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (lcp(m, n, i, i + (l + t) * d) > dmin) l += t;
-    const int j = i + l * d;
-    const int dnode = lcp(m, n, i, j);
-    int s = 0;
-    for (int div = 2;; div <<= 1) {
-        const int t = (l + div - 1) / div;
-        if (lcp(m, n, i, i + (s + t) * d) > dnode) s += t;
-        if (t <= 1) break;
-    }
-    const int gamma = i + s * d + (d < 0 ? -1 : 0);
-    const int left = (min(i, j) == gamma) ? (n - 1 + gamma) : gamma;
-    const int right = (max(i, j) == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
-    child[i] = make_int2(left, right);
-    rend[i] = max(i, j);  // the node covers leaves [min(i, j), max(i, j)]
-    parent[left] = i;
-    parent[right] = i;
-}
-
-// Packed internal node for traversal: both children's boxes in FP32,
-// rounded outwards (a conservative superset of the FP64 boxes), their node
-// indices and the last leaf position under each:
-//   a = (L.lo.x, L.lo.y, L.lo.z, L.hi.x), b = (L.hi.y, L.hi.z, R.lo.x, R.lo.y),
-//   c = (R.lo.z, R.hi.x, R.hi.y, R.hi.z), d = (left, right, last(L), last(R)).
-__device__ __forceinline__ void pack_node(float4 *node, int par, int2 ch, int n, const int *__restrict__ rend,
-                                          const double *lo, const double *hi)
-{
-    float b[12];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int cid = k ? ch.y : ch.x;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            b[6 * k + c] = __double2float_rd(__ldcg(lo + 3 * (size_t)cid + c));
-            b[6 * k + 3 + c] = __double2float_ru(__ldcg(hi + 3 * (size_t)cid + c));
-        }
-    }
-    const int lastl = ch.x >= n - 1 ? ch.x - (n - 1) : rend[ch.x];
-    const int lastr = ch.y >= n - 1 ? ch.y - (n - 1) : rend[ch.y];
-    float4 *o = node + 4 * (size_t)par;
-    o[0] = make_float4(b[0], b[1], b[2], b[3]);
-    o[1] = make_float4(b[4], b[5], b[6], b[7]);
-    o[2] = make_float4(b[8], b[9], b[10], b[11]);
-    o[3] = make_float4(__int_as_float(ch.x), __int_as_float(ch.y), __int_as_float(lastl), __int_as_float(lastr));
-}
-
-__global__ void k_refit(int n, const int *__restrict__ prim, const int2 *__restrict__ child,
-                        const int *__restrict__ parent, const int *__restrict__ rend, int *__restrict__ flags,
-                        const double *__restrict__ plo, const double *__restrict__ phi, double *lo, double *hi,
-                        float4 *node_out)
+// Implicit complete binary tree over the Morton-sorted leaves, padded to
+// N = 2^L leaves: heap node h has children 2h and 2h + 1, leaf k is node
+// N + k, the root is node 1.  Every node stores its box in FP32 rounded
+// outwards (float4 pair: lo.xyz, hi.xyz), so an internal box contains the
+// exact FP64 boxes below it; padding leaves are empty boxes.  Leaf boxes are
+// also kept exactly (FP64, in leaf order) for the final test.
+__global__ void k_leaves(int n, int N, const int *__restrict__ prim, const double *__restrict__ plo,
+                         const double *__restrict__ phi, double *__restrict__ llo, double *__restrict__ lhi,
+                         float4 *__restrict__ node)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int node = n - 1 + k;
-    const int p = prim[k];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lo[3 * (size_t)node + c] = plo[3 * (size_t)p + c];
-        hi[3 * (size_t)node + c] = phi[3 * (size_t)p + c];
-    }
-    for (int level = 0; node != 0; ++level) {
-        if (level > 96) {  // deeper than any radix tree over 30-bit codes + index bits
-            atomicOr(flags + n, 1);
-            return;
-        }
-        const int par = parent[node];
-        __threadfence();
-        if (atomicAdd(flags + par, 1) == 0) return;  // the sibling finishes the parent
-        __threadfence();
-        const int2 ch = child[par];
+    if (k >= N) return;
+    float l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (k < n) {
+        const int p = prim[k];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            lo[3 * (size_t)par + c] = fmin(__ldcg(lo + 3 * (size_t)ch.x + c), __ldcg(lo + 3 * (size_t)ch.y + c));
-            hi[3 * (size_t)par + c] = fmax(__ldcg(hi + 3 * (size_t)ch.x + c), __ldcg(hi + 3 * (size_t)ch.y + c));
+            const double a = plo[3 * (size_t)p + c], b = phi[3 * (size_t)p + c];
+            llo[3 * (size_t)k + c] = a;
+            lhi[3 * (size_t)k + c] = b;
+            l[c] = __double2float_rd(a);
+            h[c] = __double2float_ru(b);
         }
-        pack_node(node_out, par, ch, n, rend, lo, hi);
-        node = par;
+    }
+    node[2 * (size_t)(N + k)] = make_float4(l[0], l[1], l[2], 0.f);
+    node[2 * (size_t)(N + k) + 1] = make_float4(h[0], h[1], h[2], 0.f);
+}
+
+constexpr int kLevelChunk = 512;  // nodes of one level combined by one block
+
+// Combines `levels` levels upwards: block b takes nodes [cnt + b M, cnt +
+// (b + 1) M) of the level whose nodes are [cnt, 2 cnt) (M = chunk) and
+// writes their ancestors up to M / 2^levels nodes per block.
+__global__ void __launch_bounds__(256) k_levels(int cnt, int M, int levels, float4 *__restrict__ node)
+{
+    __shared__ float bl[3][kLevelChunk], bh[3][kLevelChunk];
+    const int first = cnt + blockIdx.x * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const float4 a = node[2 * (size_t)(first + i)], b = node[2 * (size_t)(first + i) + 1];
+        bl[0][i] = a.x; bl[1][i] = a.y; bl[2][i] = a.z;
+        bh[0][i] = b.x; bh[1][i] = b.y; bh[2][i] = b.z;
+    }
+    int base = first, m = M;
+    for (int lv = 0; lv < levels; ++lv) {
+        __syncthreads();
+        m >>= 1;
+        base >>= 1;
+        float l[3], h[3];
+        const int i = threadIdx.x;
+        if (i < m)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                l[c] = fminf(bl[c][2 * i], bl[c][2 * i + 1]);
+                h[c] = fmaxf(bh[c][2 * i], bh[c][2 * i + 1]);
+            }
+        __syncthreads();
+        if (i < m) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                bl[c][i] = l[c];
+                bh[c][i] = h[c];
+            }
+            node[2 * (size_t)(base + i)] = make_float4(l[0], l[1], l[2], 0.f);
+            node[2 * (size_t)(base + i) + 1] = make_float4(h[0], h[1], h[2], 0.f);
+        }
     }
 }
 
@@ -442,34 +412,47 @@ static int bvh_reserve(Scene &S, LBVH &T, int n)
 {
     if (n <= T.cap) return BF_OK;
     int cap = std::max(n, 16);
-    void *old[] = {T.morton, T.morton_alt, T.prim, T.prim_alt, T.child, T.parent, T.flags, T.lo, T.hi, T.plo, T.phi,
-                   T.rend, T.node};
+    void *old[] = {T.morton, T.morton_alt, T.prim, T.prim_alt, T.lo, T.hi, T.plo, T.phi, T.node};
     for (void *p : old)
         if (p) dev_free(S, p);
     T.morton = (unsigned *)dev_alloc(S, cap * sizeof(unsigned));
     T.morton_alt = (unsigned *)dev_alloc(S, cap * sizeof(unsigned));
     T.prim = (int *)dev_alloc(S, cap * sizeof(int));
     T.prim_alt = (int *)dev_alloc(S, cap * sizeof(int));
-    T.child = (int2 *)dev_alloc(S, cap * sizeof(int2));
-    T.parent = (int *)dev_alloc(S, 2 * cap * sizeof(int));
-    T.flags = (int *)dev_alloc(S, (cap + 1) * sizeof(int));
-    T.lo = (double *)dev_alloc(S, 2 * 3 * (size_t)cap * sizeof(double));
-    T.hi = (double *)dev_alloc(S, 2 * 3 * (size_t)cap * sizeof(double));
+    T.lo = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
+    T.hi = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
     T.plo = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
     T.phi = (double *)dev_alloc(S, 3 * (size_t)cap * sizeof(double));
-    T.rend = (int *)dev_alloc(S, cap * sizeof(int));
-    T.node = (float4 *)dev_alloc(S, 4 * (size_t)cap * sizeof(float4));
-    if (!T.morton || !T.morton_alt || !T.prim || !T.prim_alt || !T.child || !T.parent || !T.flags || !T.lo || !T.hi ||
-        !T.plo || !T.phi || !T.rend || !T.node)
+    int np2 = 1;
+    while (np2 < cap) np2 <<= 1;
+    T.node = (float4 *)dev_alloc(S, 2 * 2 * (size_t)np2 * sizeof(float4));
+    if (!T.morton || !T.morton_alt || !T.prim || !T.prim_alt || !T.lo || !T.hi || !T.plo || !T.phi || !T.node)
         return BF_E_OOM;
     T.cap = cap;
     T.topo_valid = 0;
     return BF_OK;
 }
 
-// Builds the tree over the swept boxes along x0 -> x1, or, when the scene
-// allows it (within one time step) and the topology of an earlier build is
-// still held, only refits its boxes: any topology gives the same candidates.
+// node boxes of the implicit tree from the sorted leaves
+static void bvh_fill(Scene &S, LBVH &T)
+{
+    const int n = T.n, N = T.npad;
+    k_leaves<<<cdiv(N, kThreads), kThreads, 0, S.stream>>>(n, N, T.prim, T.plo, T.phi, T.lo, T.hi, T.node);
+    ++S.n_launch;
+    for (int cnt = N; cnt > 1;) {
+        const int M = std::min(cnt, kLevelChunk);
+        int lv = 0;
+        while ((1 << lv) < M) ++lv;
+        k_levels<<<cnt / M, 256, 0, S.stream>>>(cnt, M, lv, T.node);
+        ++S.n_launch;
+        cnt /= M;
+    }
+}
+
+// Builds the tree over the swept boxes along x0 -> x1: Morton order of the
+// box centres (radix sort), then the node boxes.  Within one time step, when
+// the scene allows it, the leaf order of the step's first build is kept and
+// only the boxes are recomputed: any leaf order gives the same candidates.
 template <int NV>
 static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0, const double *x1)
 {
@@ -478,53 +461,40 @@ static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0,
     if (n == 0) return BF_OK;
     int st = bvh_reserve(S, T, n);
     if (st) return st;
+    T.npad = 1;
+    while (T.npad < n) T.npad <<= 1;
     ScopedTimer tm(S, T_BVH);
     const int nb = cdiv(n, kThreads);
     k_prim_boxes<NV><<<nb, kThreads, 0, S.stream>>>(n, ids, x0, x1, T.plo, T.phi); ++S.n_launch;
-    if (S.bvh_reuse && T.topo_valid) {
-        cudaMemsetAsync(T.flags, 0, (n + 1) * sizeof(int), S.stream);
-        k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.rend, T.flags, T.plo, T.phi, T.lo, T.hi,
-                                               T.node); ++S.n_launch;
-        return BF_OK;
+    if (!(S.bvh_reuse && T.topo_valid)) {
+        int init[6];
+        for (int c = 0; c < 3; ++c) {
+            init[c] = 0x7f800000;           // +inf as ordered int
+            init[3 + c] = (int)0x807fffff;  // -inf as ordered int
+        }
+        int *bnd = (int *)S.bounds;
+        cudaMemcpyAsync(bnd, init, sizeof(init), cudaMemcpyHostToDevice, S.stream);
+        k_centroid_bounds<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd); ++S.n_launch;
+        k_morton<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd, T.morton, T.prim); ++S.n_launch;
+        cub::DoubleBuffer<unsigned> keys(T.morton, T.morton_alt);
+        cub::DoubleBuffer<int> vals(T.prim, T.prim_alt);
+        size_t bytes = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, vals, n, 0, 30, S.stream);
+        cub_tmp_ensure(S, bytes);
+        cub::DeviceRadixSort::SortPairs(S.cub_tmp, bytes, keys, vals, n, 0, 30, S.stream);
+        if (keys.Current() != T.morton) {
+            std::swap(T.morton, T.morton_alt);
+            std::swap(T.prim, T.prim_alt);
+        }
+        T.topo_valid = 1;
     }
-    int init[6];
-    for (int c = 0; c < 3; ++c) {
-        init[c] = 0x7f800000;           // +inf as ordered int
-        init[3 + c] = (int)0x807fffff;  // -inf as ordered int
-    }
-    int *bnd = (int *)S.bounds;
-    cudaMemcpyAsync(bnd, init, sizeof(init), cudaMemcpyHostToDevice, S.stream);
-    k_centroid_bounds<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd); ++S.n_launch;
-    k_morton<<<nb, kThreads, 0, S.stream>>>(n, T.plo, T.phi, bnd, T.morton, T.prim); ++S.n_launch;
-    cub::DoubleBuffer<unsigned> keys(T.morton, T.morton_alt);
-    cub::DoubleBuffer<int> vals(T.prim, T.prim_alt);
-    size_t bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, vals, n, 0, 30, S.stream);
-    cub_tmp_ensure(S, bytes);
-    cub::DeviceRadixSort::SortPairs(S.cub_tmp, bytes, keys, vals, n, 0, 30, S.stream);
-    if (keys.Current() != T.morton) {
-        std::swap(T.morton, T.morton_alt);
-        std::swap(T.prim, T.prim_alt);
-    }
-    if (n > 1) k_radix_tree<<<cdiv(n - 1, kThreads), kThreads, 0, S.stream>>>(n, T.morton, T.child, T.parent, T.rend); ++S.n_launch;
-    cudaMemsetAsync(T.flags, 0, (n + 1) * sizeof(int), S.stream);
-    k_refit<<<nb, kThreads, 0, S.stream>>>(n, T.prim, T.child, T.parent, T.rend, T.flags, T.plo, T.phi, T.lo, T.hi,
-                                           T.node); ++S.n_launch;
-    T.topo_valid = 1;
+    bvh_fill(S, T);
     return BF_OK;
 }
 
-__device__ __forceinline__ bool box_overlap(const double *l1, const double *h1, const double *l2, const double *h2)
+__device__ __forceinline__ bool box_overlap_f(const float *ql, const float *qh, float4 l, float4 h)
 {
-    return !(l1[0] > h2[0] || l2[0] > h1[0] || l1[1] > h2[1] || l2[1] > h1[1] || l1[2] > h2[2] || l2[2] > h1[2]);
-}
-
-__device__ __forceinline__ bool box_overlap_f(const float *ql, const float *qh, float4 a, float4 b, float4 c, int k)
-{
-    // child k of a packed node: k = 0 -> (a.xyz, a.w b.xy), k = 1 -> (b.zw c.x, c.yzw)
-    const float l0 = k ? b.z : a.x, l1 = k ? b.w : a.y, l2 = k ? c.x : a.z;
-    const float h0 = k ? c.y : a.w, h1 = k ? c.z : b.x, h2 = k ? c.w : b.y;
-    return !(ql[0] > h0 || l0 > qh[0] || ql[1] > h1 || l1 > qh[1] || ql[2] > h2 || l2 > qh[2]);
+    return !(ql[0] > h.x || l.x > qh[0] || ql[1] > h.y || l.y > qh[1] || ql[2] > h.z || l.z > qh[2]);
 }
 
 constexpr int kQueryThreads = 128;
@@ -533,14 +503,15 @@ constexpr int kQueryStack = 64;
 // Queries: surface vertices against the triangle tree (type PT), or each
 // edge leaf against the edge leaves after it in the tree's leaf order (type
 // EE; subtrees whose last leaf is not after the query leaf are skipped, so
-// every edge pair is met once).  Internal nodes are culled with their FP32
-// outward-rounded boxes; a leaf is accepted only by the exact FP64
-// closed-box test, so the candidates are exactly the pairs whose swept boxes
-// overlap.  The traversal stack lives in shared memory.
+// every edge pair is met once).  Nodes are culled with their FP32
+// outward-rounded boxes (both children of a node from one 64-byte fetch); a
+// leaf is accepted only by the exact FP64 closed-box test, so the candidates
+// are exactly the pairs whose swept boxes overlap.  The traversal stack
+// lives in shared memory.
 template <int TYPE>
 __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__restrict__ qids,
                                                          const double *__restrict__ x0, const double *__restrict__ x1,
-                                                         int n, const float4 *__restrict__ node,
+                                                         int n, int N, const float4 *__restrict__ node,
                                                          const int *__restrict__ prim, const double *__restrict__ lo,
                                                          const double *__restrict__ hi, const int *__restrict__ st,
                                                          const int *__restrict__ se, const uint8_t *__restrict__ dir,
@@ -566,8 +537,8 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
         qv1 = se[2 * qa + 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ql[c] = lo[3 * (size_t)(n - 1 + q) + c];
-            qh[c] = hi[3 * (size_t)(n - 1 + q) + c];
+            ql[c] = lo[3 * (size_t)q + c];
+            qh[c] = hi[3 * (size_t)q + c];
         }
     }
     float fl[3], fh[3];
@@ -577,11 +548,10 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
         fh[c] = __double2float_ru(qh[c]);
     }
     const bool qdir = TYPE == PT ? dir[qv0] != 0 : (dir[qv0] && dir[qv1]);
-    // a leaf (node index >= n - 1): exact test, pair filters, emit
-    auto leaf = [&](int nodeid) {
-        const int k = nodeid - (n - 1);
-        if (TYPE == EE && k <= q) return;
-        const double *l2 = lo + 3 * (size_t)nodeid, *h2 = hi + 3 * (size_t)nodeid;
+    // leaf position k: exact test, pair filters, emit
+    auto leaf = [&](int k) {
+        if (k >= n || (TYPE == EE && k <= q)) return;
+        const double *l2 = lo + 3 * (size_t)k, *h2 = hi + 3 * (size_t)k;
         if (ql[0] > h2[0] || l2[0] > qh[0] || ql[1] > h2[1] || l2[1] > qh[1] || ql[2] > h2[2] || l2[2] > qh[2])
             return;
         const int b = prim[k];
@@ -598,36 +568,39 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
             if (idx < cap) cand[idx] = TYPE == PT ? make_int2(qa, b) : make_int2(min(qa, b), max(qa, b));
         }
     };
-    if (n == 1) {
+    if (N == 1) {
         leaf(0);
         return;
     }
+    const int L = 31 - __clz(N);  // leaves are nodes [N, 2N)
     int *stk = stack + threadIdx.x;
-    int sp = 0;
-    stk[0] = 0;
-    sp = 1;
+    stk[0] = 1;
+    int sp = 1;
     for (int visits = 0; sp > 0; ++visits) {
-        if (visits > 2 * n + 64) {  // a tree has n - 1 internal nodes
+        if (visits > N + 64) {  // the tree has N - 1 internal nodes
             atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
             return;
         }
-        const int nd = stk[--sp * kQueryThreads];
-        const float4 *p = node + 4 * (size_t)nd;
-        const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
-        const int ch[2] = {__float_as_int(d.x), __float_as_int(d.y)};
-        const int last[2] = {__float_as_int(d.z), __float_as_int(d.w)};
+        const int h = stk[--sp * kQueryThreads];
+        const int lc = 32 - __clz(h);  // level of the children (root = level 0)
+        const float4 *p = node + 4 * (size_t)h;  // children 2h, 2h + 1: 4 consecutive float4
+        const float4 l0 = __ldg(p), h0 = __ldg(p + 1), l1 = __ldg(p + 2), h1 = __ldg(p + 3);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            if (TYPE == EE && last[k] <= q) continue;
-            if (!box_overlap_f(fl, fh, a, b, c, k)) continue;
-            if (ch[k] >= n - 1) {
-                leaf(ch[k]);
+            const int cnode = 2 * h + k;
+            if (TYPE == EE) {  // skip subtrees whose last leaf is not after q
+                const int span = 1 << (L - lc);
+                if ((cnode - (1 << lc) + 1) * span - 1 <= q) continue;
+            }
+            if (!box_overlap_f(fl, fh, k ? l1 : l0, k ? h1 : h0)) continue;
+            if (lc == L) {
+                leaf(cnode - N);
             } else {
                 if (sp >= kQueryStack) {
                     atomicOr(dflag + F_ERR, ERR_CAND_OVERFLOW);
                     return;
                 }
-                stk[sp++ * kQueryThreads] = ch[k];
+                stk[sp++ * kQueryThreads] = cnode;
             }
         }
     }
@@ -805,13 +778,14 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         if (S.nsv && S.nst)
             {
                 k_query<PT><<<cdiv(S.nsv, kQueryThreads), kQueryThreads, 0, S.stream>>>(
-                    S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.node, S.bvh_tri.prim, S.bvh_tri.lo, S.bvh_tri.hi, S.st,
+                    S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.npad, S.bvh_tri.node, S.bvh_tri.prim, S.bvh_tri.lo,
+                    S.bvh_tri.hi, S.st,
                     S.se, S.dir, S.cand_pt, S.cand_cap, S.dflag + F_NCAND_PT, S.dflag); ++S.n_launch;
             }
         if (S.nse > 1)
             {
                 k_query<EE><<<cdiv(S.nse, kQueryThreads), kQueryThreads, 0, S.stream>>>(
-                    S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.node, S.bvh_edge.prim, S.bvh_edge.lo,
+                    S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.npad, S.bvh_edge.node, S.bvh_edge.prim, S.bvh_edge.lo,
                     S.bvh_edge.hi, S.st, S.se, S.dir, S.cand_ee, S.cand_cap, S.dflag + F_NCAND_EE, S.dflag); ++S.n_launch;
             }
         st = sync_flags(S);

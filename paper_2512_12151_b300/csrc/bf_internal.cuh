@@ -46,18 +46,13 @@ enum TimerId { T_ELASTIC = 0, T_SPMV, T_PCG_UPDATE, T_PCG_DIR, T_CONTACT, T_ENER
                T_PCG_PH_STAGE, T_PCG_PH_ROWS, T_PCG_PH_CONTACT, T_N };
 
 struct LBVH {
-    int n = 0, cap = 0;
-    // leaves: sorted primitive ids; nodes 0..n-2 internal, n-1..2n-2 leaves
+    int n = 0, cap = 0, npad = 0;  // leaves, capacity, leaves padded to a power of two
     unsigned *morton = nullptr, *morton_alt = nullptr;
-    int *prim = nullptr, *prim_alt = nullptr;
-    int2 *child = nullptr;
-    int *parent = nullptr;
-    int *flags = nullptr;
-    double *lo = nullptr, *hi = nullptr;  // 3 per node
+    int *prim = nullptr, *prim_alt = nullptr;  // primitive of each leaf (Morton order)
+    double *lo = nullptr, *hi = nullptr;    // exact leaf boxes in leaf order, 3 each
     double *plo = nullptr, *phi = nullptr;  // exact primitive boxes, 3 per primitive
-    int *rend = nullptr;       // last leaf position under each internal node
-    float4 *node = nullptr;    // packed internal nodes for traversal (4 float4 each)
-    int topo_valid = 0;        // the topology may be refitted instead of rebuilt
+    float4 *node = nullptr;  // implicit tree: node h at node[2h] (lo), node[2h + 1] (hi), FP32 outward-rounded
+    int topo_valid = 0;      // the leaf order may be kept and only the boxes recomputed
 };
 
 struct Scene {
