@@ -168,6 +168,12 @@ def dist_init(args):
     return ws, rank, local
 
 
+def _reduce_device():
+    """CUDA for NCCL process groups, host memory for gloo"""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -179,7 +185,7 @@ def allmax(ws, v):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -189,7 +195,7 @@ def allsum(ws, v):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 

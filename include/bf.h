@@ -52,7 +52,8 @@ extern "C" {
 #define BF_E_OUTER_MAXIT (-7)  /* Alg. 1 loop hit max_outer */
 #define BF_E_NONFINITE (-8)    /* NaN / Inf detected in a solve */
 #define BF_E_CAPACITY (-9)     /* a work buffer overflowed and could not grow */
-#define BF_E_NOT_FOUND (-10)   /* a pair key names no surface primitive pair */
+#define BF_E_NOT_FOUND (-10)   /* a pair key (or batch ticket) names nothing known */
+#define BF_E_BUDGET (-11)      /* batch admission refused: the HBM budget would be exceeded */
 
 #define BF_PREC_FP64 0  /* everything FP64 */
 #define BF_PREC_MIXED 1 /* FP32 Hessian blocks / SpMV / preconditioner; FP64 gradient,
@@ -110,6 +111,9 @@ int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_
                     void *stream, bf_scene **out);
 int bf_scene_destroy(bf_scene *scene);
 int bf_set_stream(bf_scene *scene, void *stream);
+
+/* Device bytes the scene holds (all its allocations); *bytes host. */
+int bf_scene_bytes(bf_scene *scene, int64_t *bytes);
 
 /* ---- time stepping (Alg. 1) ------------------------------------------- */
 
@@ -270,6 +274,46 @@ int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
  * creation (sorts and scans done by CUB are not counted); *n host. */
 int bf_get_launch_count(bf_scene *scene, int64_t *n);
 int bf_get_timers(bf_scene *scene, int32_t cap, int64_t *launches, double *ms, const char **names);
+
+/* ---- Batches: many independent scenes advanced concurrently ------------
+ * The paper advances one scene; this runner serves many.  A batch owns
+ * n_workers host threads, each with its own CUDA stream.  bf_batch_admit
+ * binds a created scene to the stream of the least-loaded worker and
+ * queues n_steps time steps (Alg. 1 each, exactly as bf_step); workers
+ * advance their scenes one step per turn, round robin, so scenes admitted
+ * while others run join at the next turn and the kernels of different
+ * scenes overlap on the device.  Admission returns BF_E_BUDGET, and queues
+ * nothing, when the device bytes (bf_scene_bytes) of the batch's unfinished
+ * scenes plus this one would exceed hbm_budget_bytes; the caller may retry
+ * after a ticket finishes.  Times are seconds since bf_batch_create.
+ * Ownership: the caller keeps every scene and must not call it, nor destroy
+ * it, while its ticket is unfinished; bf_batch_release (finished tickets
+ * only) and bf_batch_destroy put the scene back on the default stream.
+ * Scenes admitted to a batch should use the default allocator or one that
+ * is not bound to a stream.  A failing step (status < 0) finishes its
+ * ticket with that status. */
+typedef struct bf_batch bf_batch;
+int bf_batch_create(int32_t n_workers, int64_t hbm_budget_bytes, bf_batch **out);
+/* Stops the workers after their current step and frees the batch; unfinished
+ * tickets are abandoned (their scenes stay valid). */
+int bf_batch_destroy(bf_batch *batch);
+/* *ticket (host) identifies the job. */
+int bf_batch_admit(bf_batch *batch, bf_scene *scene, int32_t n_steps, int64_t *ticket);
+/* Waits until the ticket finished or timeout_ms passed (< 0: no limit);
+ * *done (host) = 1 when finished. */
+int bf_batch_wait(bf_batch *batch, int64_t ticket, int32_t timeout_ms, int32_t *done);
+/* Progress of a ticket (all host, any may be NULL): steps done, status of
+ * the last step, admission time, completion time of each step and its
+ * statistics (up to cap entries). */
+int bf_batch_result(bf_batch *batch, int64_t ticket, int32_t cap, int32_t *steps_done, int32_t *status,
+                    double *t_admit, double *t_steps, bf_step_stats *stats);
+/* Forgets a finished ticket. */
+int bf_batch_release(bf_batch *batch, int64_t ticket);
+/* info[6] (host int64): resident bytes of unfinished scenes, budget,
+ * workers, queued scenes, finished tickets, tickets issued. */
+int bf_batch_info(bf_batch *batch, int64_t *info);
+/* Seconds since bf_batch_create (the clock of t_admit and t_steps). */
+double bf_batch_now(bf_batch *batch);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,8 @@ BF_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "device allocation failed", -3: "CUDA error",
           -4: "PCG reached max_cg", -5: "Newton loop reached max_newton", -6: "line search failed",
           -7: "time step reached max_outer", -8: "non-finite value", -9: "work buffer capacity exceeded",
-          -10: "pair key not found"}
+          -10: "pair key or ticket not found", -11: "HBM budget exceeded"}
+BF_E_BUDGET = -11
 
 
 class BfError(RuntimeError):
@@ -106,6 +107,15 @@ def lib():
         "bf_set_pcg_mode": [_P, C.c_int32],
         "bf_get_pcg_config": [_P, _P],
         "bf_get_timers": [_P, C.c_int32, _P, _P, _P],
+        "bf_scene_bytes": [_P, C.POINTER(C.c_int64)],
+        "bf_batch_create": [C.c_int32, C.c_int64, C.POINTER(_P)],
+        "bf_batch_destroy": [_P],
+        "bf_batch_admit": [_P, _P, C.c_int32, C.POINTER(C.c_int64)],
+        "bf_batch_wait": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_int32)],
+        "bf_batch_result": [_P, C.c_int64, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                            C.POINTER(C.c_double), _P, _P],
+        "bf_batch_release": [_P, C.c_int64],
+        "bf_batch_info": [_P, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -113,6 +123,8 @@ def lib():
         f.restype = C.c_int
     L.bf_status_str.argtypes = [C.c_int]
     L.bf_status_str.restype = C.c_char_p
+    L.bf_batch_now.argtypes = [_P]
+    L.bf_batch_now.restype = C.c_double
     _lib = L
     return L
 
@@ -374,6 +386,61 @@ def bf_get_timers(h):
     names = (C.c_char_p * cap)()
     n = lib().bf_get_timers(h, cap, _np_ptr(launches), _np_ptr(ms), names)
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def bf_scene_bytes(h):
+    n = C.c_int64()
+    _check("bf_scene_bytes", lib().bf_scene_bytes(h, C.byref(n)))
+    return n.value
+
+
+def bf_batch_create(n_workers, hbm_budget_bytes):
+    b = _P()
+    _check("bf_batch_create", lib().bf_batch_create(n_workers, int(hbm_budget_bytes), C.byref(b)))
+    return b
+
+
+def bf_batch_destroy(b):
+    _check("bf_batch_destroy", lib().bf_batch_destroy(b))
+
+
+def bf_batch_admit(b, h, n_steps):
+    """ticket, or None when the HBM budget refuses the scene"""
+    t = C.c_int64()
+    st = lib().bf_batch_admit(b, h, n_steps, C.byref(t))
+    _check("bf_batch_admit", st, (BF_OK, BF_E_BUDGET))
+    return None if st == BF_E_BUDGET else t.value
+
+
+def bf_batch_wait(b, ticket, timeout_ms=-1):
+    done = C.c_int32()
+    _check("bf_batch_wait", lib().bf_batch_wait(b, ticket, timeout_ms, C.byref(done)))
+    return bool(done.value)
+
+
+def bf_batch_result(b, ticket, cap):
+    n, status, t_admit = C.c_int32(), C.c_int32(), C.c_double()
+    t_steps = np.zeros(max(cap, 1))
+    stats = (bf_step_stats * max(cap, 1))()
+    _check("bf_batch_result", lib().bf_batch_result(b, ticket, cap, C.byref(n), C.byref(status), C.byref(t_admit),
+                                                    _np_ptr(t_steps), stats))
+    k = min(n.value, cap)
+    return {"steps_done": n.value, "status": status.value, "t_admit": t_admit.value,
+            "t_steps": t_steps[:k].copy(), "stats": [stats[i].as_dict() for i in range(k)]}
+
+
+def bf_batch_release(b, ticket):
+    _check("bf_batch_release", lib().bf_batch_release(b, ticket))
+
+
+def bf_batch_info(b):
+    info = np.zeros(6, np.int64)
+    _check("bf_batch_info", lib().bf_batch_info(b, _np_ptr(info)))
+    return dict(zip(("resident_bytes", "budget", "workers", "queued", "finished", "issued"), info.tolist()))
+
+
+def bf_batch_now(b):
+    return lib().bf_batch_now(b)
 
 
 class Sim:

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -30,14 +31,40 @@ static bf_scene *owner_of(Scene &S) { return reinterpret_cast<bf_scene *>(&S); }
 // ---------------------------------------------------------------------------
 // memory
 // ---------------------------------------------------------------------------
+// Without a caller allocator, scene memory comes from the device's
+// stream-ordered pool (cudaMallocAsync on the scene's stream), which keeps
+// freed blocks for reuse instead of returning them at every synchronisation,
+// so that creating and destroying scenes while others run (a serving loop)
+// neither synchronises the device nor pays for fresh allocations.
+static void pool_keep_memory()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    });
+}
+
 void *dev_alloc(Scene &S, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
     void *p = nullptr;
-    if (S.has_alloc) p = S.alloc.alloc(bytes, S.alloc.ctx);
-    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
-    if (p) S.owned.push_back(p);
+    if (S.has_alloc) {
+        p = S.alloc.alloc(bytes, S.alloc.ctx);
+    } else {
+        pool_keep_memory();
+        if (cudaMallocAsync(&p, bytes, S.stream) != cudaSuccess) p = nullptr;
+    }
+    if (p) {
+        S.owned.push_back(p);
+        S.owned_bytes.push_back(bytes);
+        S.bytes += bytes;
+    }
     return p;
 }
 
@@ -45,9 +72,14 @@ void dev_free(Scene &S, void *p)
 {
     if (!p) return;
     auto it = std::find(S.owned.begin(), S.owned.end(), p);
-    if (it != S.owned.end()) S.owned.erase(it);
+    if (it != S.owned.end()) {
+        const size_t k = it - S.owned.begin();
+        S.bytes -= S.owned_bytes[k];
+        S.owned_bytes.erase(S.owned_bytes.begin() + k);
+        S.owned.erase(it);
+    }
     if (S.has_alloc) S.alloc.free(p, S.alloc.ctx);
-    else cudaFree(p);
+    else cudaFreeAsync(p, S.stream);
 }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_E_CUDA; }
@@ -736,6 +768,14 @@ int bf_set_stream(bf_scene *scene, void *stream)
     return BF_OK;
 }
 
+int bf_scene_bytes(bf_scene *scene, int64_t *bytes)
+{
+    SCENE_OR_ARG(scene);
+    if (!bytes) return BF_E_ARG;
+    *bytes = (int64_t)S.bytes;
+    return BF_OK;
+}
+
 int bf_step(bf_scene *scene, int32_t n_steps, bf_step_stats *stats)
 {
     SCENE_OR_ARG(scene);
@@ -901,7 +941,8 @@ const char *bf_status_str(int status)
     case BF_E_OUTER_MAXIT: return "time step reached max_outer";
     case BF_E_NONFINITE: return "non-finite value";
     case BF_E_CAPACITY: return "work buffer capacity exceeded";
-    case BF_E_NOT_FOUND: return "pair key not found";
+    case BF_E_NOT_FOUND: return "pair key or ticket not found";
+    case BF_E_BUDGET: return "HBM budget exceeded";
     default: return "unknown status";
     }
 }

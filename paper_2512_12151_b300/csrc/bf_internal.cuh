@@ -65,6 +65,8 @@ struct Scene {
     bf_allocator alloc{};
     bool has_alloc = false;
     std::vector<void *> owned;
+    std::vector<size_t> owned_bytes;  // size of each owned allocation
+    size_t bytes = 0;                 // device bytes the scene holds
 
     // host topology
     std::vector<int> h_sv, h_st, h_se, h_rowptr, h_col;

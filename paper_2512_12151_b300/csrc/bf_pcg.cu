@@ -59,6 +59,7 @@ constexpr int kPcgThreads = 512;  // threads per CTA at one CTA per SM
 constexpr int kPcgMaxWarps = kPcgThreads / 32;
 constexpr int kPcgMaxCached = 256;  // contact pairs per CTA cached in shared memory
 constexpr int kPcgMaxGrid = 1024;  // CTAs of one launch
+constexpr int kPcgEntriesPerCta = 3072;  // target full-row blocks per CTA for small systems
 
 struct PcgArgs {
     int nv, nc;
@@ -868,7 +869,10 @@ static int setup_persistent(Scene &S)
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BF_E_CUDA;
         for (int cps = per_sm; cps >= 1; --cps) {
-            const int grid = nsm * cps;
+            // small systems take fewer CTAs (about kPcgEntriesPerCta blocks
+            // each), which keeps the barriers short and leaves SMs to other
+            // scenes running concurrently
+            const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nfull, kPcgEntriesPerCta)));
             if (grid > kPcgMaxGrid) continue;
             const int block = (kPcgThreads / cps) & ~31;
             int mr = 0, me = 0, mw = 0, ml = 0;
@@ -881,7 +885,9 @@ static int setup_persistent(Scene &S)
             int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(sizeof(CT)));
             while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc).total > avail) --kc;
             const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc);
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            // the attribute is an upper bound shared by every scene: set it to
+            // the most any launch may ask for, so concurrent set-ups agree
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
             if (occ < cps) continue;

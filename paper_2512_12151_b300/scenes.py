@@ -200,6 +200,30 @@ def eight_cubes(seed: int = 0, cells: int = 16, side: float = 0.1, precision: in
                    Params(precision=precision), 50, {"seed": seed, "cells": cells})
 
 
+def batch_scene(seed: int, t_lo: float = 1e3, t_hi: float = 2e4, precision: int = 1, side: float = 0.1) -> Scene:
+    """One scene of a batch of independent scenes of uneven size: target
+    tet count T ~ log-uniform [t_lo, t_hi], a single cube or a stack of two
+    (probability 1/2 each), n = max(2, round((T / (6 k))^(1/3))) cells per
+    cube edge (k cubes), E ~ log-uniform [1e4, 1e6] Pa, nu ~ U(0.3, 0.45),
+    rho = 1000 kg/m^3; cubes of side 0.1 m, the lower one 1 cm above a
+    static 2 m x 2 m ground quad, the upper one 1 mm above it; h = 0.01 s,
+    10 steps."""
+    rng = np.random.default_rng(seed)
+    target = math.exp(rng.uniform(math.log(t_lo), math.log(t_hi)))
+    k = 1 + int(rng.random() < 0.5)
+    cells = max(2, int(round((target / (6 * k)) ** (1.0 / 3.0))))
+    E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
+    nu = rng.uniform(0.3, 0.45)
+    b = _Builder()
+    for j in range(k):
+        v, t = _jittered_cube(rng, cells, side, (-side / 2, -side / 2, 0.01 + j * (side + 1e-3)))
+        b.add_solid(v, t, 0)
+    gv, gt = ground_quad(1.0)
+    b.add_obstacle(gv, gt)
+    return b.build(f"batch_{seed}_{k}x{cells}^3", [[E, nu, 1000.0]], Params(precision=precision), 10,
+                   {"seed": seed, "cells": cells, "cubes": k, "E": E, "nu": nu, "target_tets": target})
+
+
 def single_cube(seed: int = 0, cells: int = 2, side: float = 0.1, z: float = 0.5,
                 v0=(0.0, 0.0, 0.0), with_ground: bool = False, gravity=(0.0, 0.0, -9.8),
                 xy=(0.0, 0.0)) -> Scene:

@@ -1,0 +1,182 @@
+"""Many independent scenes through the native batch runner (bf_batch_*):
+batched runs, a served request stream, the one-scene-at-a-time baseline,
+and the size-balanced split of scenes across GPUs.
+
+Host orchestration only: every time step runs in the library (the batch
+runner's worker threads call the same step as bf_step, on their own CUDA
+streams).  Scenes are created without the torch allocator, so their memory
+comes from the device's stream-ordered pool and they can move between
+streams.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+
+import numpy as np
+
+from . import binding as B
+from . import scenes
+
+
+def create(scene, params=None):
+    """(handle, keep-alive) of a scene on the default stream, pool memory"""
+    return B.bf_scene_create(scene, params if params is not None else scene.params, None, None)
+
+
+def shard(sizes, world):
+    """Size-balanced split of scene indices over `world` ranks: largest
+    first, each to the currently least-loaded rank (ties: lower rank)."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def _latencies(res):
+    """per-step latencies of one finished ticket: step completion minus the
+    previous step's completion (the first: minus admission)"""
+    t = res["t_steps"]
+    prev = np.concatenate([[res["t_admit"]], t[:-1]])
+    return t - prev
+
+
+def _summary(lat, steps, elapsed):
+    lat = np.asarray(lat)
+    return {"steps": int(steps), "seconds": elapsed, "steps_per_s": steps / elapsed if elapsed > 0 else None,
+            "p50_step_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_step_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None}
+
+
+def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30):
+    """Creates every scene (untimed), then admits them all at once to a batch
+    and runs them to completion.  Returns throughput and per-step latency
+    (from the admission of all scenes)."""
+    handles = [create(s) for s in scene_list]
+    b = B.bf_batch_create(n_workers, budget_bytes)
+    try:
+        t0 = B.bf_batch_now(b)
+        tickets = []
+        for (h, _), s in zip(handles, scene_list):
+            t = B.bf_batch_admit(b, h, n_steps or s.n_steps)
+            if t is None:
+                raise RuntimeError("batch admission refused by the HBM budget")
+            tickets.append(t)
+        for t in tickets:
+            B.bf_batch_wait(b, t)
+        lat, steps, t_end, bad = [], 0, t0, 0
+        for t, s in zip(tickets, scene_list):
+            r = B.bf_batch_result(b, t, n_steps or s.n_steps)
+            bad += r["status"] != 0
+            lat.extend(_latencies(r))
+            steps += r["steps_done"]
+            t_end = max(t_end, float(r["t_steps"][-1]) if len(r["t_steps"]) else t_end)
+            B.bf_batch_release(b, t)
+        out = _summary(lat, steps, t_end - t0)
+        out.update({"workers": n_workers, "scenes": len(scene_list), "failed": bad})
+        return out, handles
+    finally:
+        B.bf_batch_destroy(b)
+
+
+def run_sequential(scene_list, n_steps=None):
+    """The baseline: one scene at a time, every step on the default stream."""
+    handles = [create(s) for s in scene_list]
+    lat, steps, bad = [], 0, 0
+    t0 = time.perf_counter()
+    for (h, _), s in zip(handles, scene_list):
+        for _ in range(n_steps or s.n_steps):
+            a = time.perf_counter()
+            st, _ = B.bf_step(h, 1, ok=tuple(B.STATUS))
+            lat.append(time.perf_counter() - a)
+            steps += 1
+            if st != 0:
+                bad += 1
+                break
+    out = _summary(lat, steps, time.perf_counter() - t0)
+    out.update({"scenes": len(scene_list), "failed": bad})
+    return out, handles
+
+
+def destroy(handles):
+    for h, _ in handles:
+        B.bf_scene_destroy(h)
+
+
+def poisson_requests(n, rate, seed=0, t_lo=2e3, t_hi=2e5, precision=1):
+    """n requests: seeded exponential inter-arrival gaps (mean 1/rate s), each
+    a batch_scene drawn log-uniformly in [t_lo, t_hi] tets"""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    return [(float(a), int(rng.integers(1 << 30)), t_lo, t_hi, precision) for a in arrivals]
+
+
+def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002):
+    """Serves a request stream: at each arrival time the request's scene is
+    generated and created, then admitted to the running batch (waiting
+    while the HBM budget refuses it); finished scenes are released and
+    destroyed as they complete.  Returns aggregate steps/s (first arrival to
+    last completion), per-step latency p50/p99 (completion of a step minus
+    completion of the scene's previous step, or its admission) and the
+    admission wait (admission minus arrival) p50/p99."""
+    b = B.bf_batch_create(n_workers, budget_bytes)
+    live = {}  # ticket -> (handle, keep, arrival)
+    lat, waits, steps, bad = [], [], 0, 0
+    lock = threading.Lock()
+
+    def reap(block=False):
+        nonlocal steps, bad
+        for t in list(live):
+            if block:
+                B.bf_batch_wait(b, t)
+            elif not B.bf_batch_wait(b, t, 0):
+                continue
+            r = B.bf_batch_result(b, t, n_steps)
+            h, _keep, _arr = live.pop(t)
+            with lock:
+                lat.extend(_latencies(r))
+                steps += r["steps_done"]
+                bad += r["status"] != 0
+            B.bf_batch_release(b, t)
+            B.bf_scene_destroy(h)
+
+    try:
+        t0 = B.bf_batch_now(b)
+        last_done = t0
+        for arrival, seed, t_lo, t_hi, prec in requests:
+            while B.bf_batch_now(b) - t0 < arrival:
+                reap()
+                time.sleep(min(poll_s, max(0.0, arrival - (B.bf_batch_now(b) - t0))))
+            s = scenes.batch_scene(seed, t_lo, t_hi, precision=prec)
+            h, keep = create(s)
+            while True:
+                t = B.bf_batch_admit(b, h, n_steps)
+                if t is not None:
+                    break
+                reap()
+                time.sleep(poll_s)
+            waits.append(B.bf_batch_now(b) - t0 - arrival)
+            live[t] = (h, keep, arrival)
+            reap()
+        for t in list(live):
+            B.bf_batch_wait(b, t)
+        last_done = B.bf_batch_now(b)
+        reap(block=True)
+        out = _summary(lat, steps, last_done - t0 - requests[0][0] if requests else 0.0)
+        w = np.asarray(waits)
+        out.update({"requests": len(requests), "failed": bad, "workers": n_workers,
+                    "admission_wait_p50_ms": float(np.percentile(w, 50) * 1e3) if len(w) else None,
+                    "admission_wait_p99_ms": float(np.percentile(w, 99) * 1e3) if len(w) else None,
+                    "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None})
+        return out
+    finally:
+        for t, (h, _k, _a) in list(live.items()):
+            B.bf_batch_wait(b, t)
+        B.bf_batch_destroy(b)
+        for t, (h, _k, _a) in list(live.items()):
+            B.bf_scene_destroy(h)

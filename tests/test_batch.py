@@ -1,0 +1,77 @@
+"""The native batch runner (bf_batch_*): a scene advanced inside a batch of
+other scenes gives the same result as alone (within the mixed-precision
+step tolerance, 1e-4 x bounding-box diagonal; in practice only the order
+of floating-point atomics differs), admission honours the HBM budget, and
+tickets report their steps."""
+import numpy as np
+import pytest
+
+from paper_2512_12151_b300 import binding as B
+from paper_2512_12151_b300 import scenes, serving
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def test_alone_equals_in_the_mix(torch_cuda):
+    seeds = [3, 7, 11, 19, 23, 31, 37]
+    target = scenes.batch_scene(seeds[0])
+    h, keep = serving.create(target)
+    st, stats = B.bf_step(h, 10)
+    xa, va = B.bf_get_state(h, target.nv)
+    B.bf_scene_destroy(h)
+    assert max(s["n_contacts"] for s in stats) > 0  # the scene reaches the ground
+    mix = [scenes.batch_scene(s) for s in seeds]
+    out, handles = serving.run_batched(mix, n_steps=10, n_workers=3)
+    try:
+        xm, vm = B.bf_get_state(handles[0][0], target.nv)
+    finally:
+        serving.destroy(handles)
+    assert out["failed"] == 0 and out["steps"] == 10 * len(seeds)
+    tol = 1e-4 * target.bbox_diag()
+    assert np.abs(xa - xm).max() <= tol, np.abs(xa - xm).max()
+    assert np.abs(va - vm).max() <= tol / target.params.dt
+
+
+def test_budget_tickets_and_results(torch_cuda):
+    s = scenes.batch_scene(5)
+    h, keep = serving.create(s)
+    nbytes = B.bf_scene_bytes(h)
+    assert nbytes > 0
+    b = B.bf_batch_create(2, nbytes - 1)
+    try:
+        assert B.bf_batch_admit(b, h, 3) is None  # refused: over budget
+        assert B.bf_batch_info(b)["resident_bytes"] == 0
+    finally:
+        B.bf_batch_destroy(b)
+    b = B.bf_batch_create(2, 4 * nbytes)
+    try:
+        t = B.bf_batch_admit(b, h, 3)
+        assert t is not None
+        assert B.bf_batch_info(b)["resident_bytes"] == nbytes
+        assert B.bf_batch_wait(b, t, 600000)
+        r = B.bf_batch_result(b, t, 3)
+        assert r["steps_done"] == 3 and r["status"] == 0
+        assert len(r["stats"]) == 3 and all(x["outer_iters"] >= 2 for x in r["stats"])
+        ts = r["t_steps"]
+        assert r["t_admit"] <= ts[0] <= ts[1] <= ts[2] <= B.bf_batch_now(b)
+        assert B.bf_batch_info(b)["resident_bytes"] == 0
+        B.bf_batch_release(b, t)
+        with pytest.raises(B.BfError):
+            B.bf_batch_result(b, t, 3)
+    finally:
+        B.bf_batch_destroy(b)
+        B.bf_scene_destroy(h)
+
+
+def test_serve_small_stream(torch_cuda):
+    reqs = serving.poisson_requests(12, rate=200.0, seed=1, t_lo=1e3, t_hi=6e3)
+    out = serving.serve(reqs, n_steps=3, n_workers=4)
+    assert out["failed"] == 0 and out["steps"] == 36
+    assert out["p99_step_ms"] >= out["p50_step_ms"] > 0
