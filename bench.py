@@ -240,7 +240,15 @@ def run_reference(args):
     return 0
 
 
+def _progress(msg):
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
+
+
 def main():
+    import faulthandler
+    import signal
+    faulthandler.register(signal.SIGUSR1, all_threads=True)  # `kill -USR1` prints every thread's stack
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=47)
@@ -249,6 +257,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--batched-scenes", type=int, default=256,
+                    help="independent scenes of 1k-20k tets for the batched line (0: skip)")
+    ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the served stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +323,7 @@ def main():
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
     timed_stats = stats_all[W:]
     sim.close()
+    _progress(f"pass 1 (device-timed steps): {value:.1f} steps/s")
 
     # ---- pass 2: same steps with per-kernel CUDA events (roofline) -------
     s2, sim2 = make(seed)
@@ -324,6 +339,7 @@ def main():
     torch.cuda.synchronize()
     timers = B.bf_get_timers(sim2.h)
     pcg_cfg = B.bf_get_pcg_config(sim2.h)
+    _progress("pass 2 (per-kernel timers) done")
     sim2.close()
     peak, peak_kind = load_peaks()
     mixed = args.precision == 1
@@ -389,6 +405,31 @@ def main():
         e2e = {"value": steps_all / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
+    # ---- batched scenes, the plain FP64 path one at a time, served stream --
+    batched = plain = served = None
+    _progress("device passes done")
+    if args.batched_scenes > 0:
+        from paper_2512_12151_b300 import serving
+        torch.cuda.synchronize()
+        seeds = range(rank * 100000, rank * 100000 + args.batched_scenes)
+        mix = [scenes.batch_scene(i, precision=1) for i in seeds]
+        _progress(f"batched: {len(mix)} scenes generated")
+        batched, hs = serving.run_batched(mix, n_steps=10, n_workers=args.batch_workers)
+        serving.destroy(hs)
+        _progress(f"batched: {batched['steps_per_s']:.1f} steps/s")
+        fp64 = [scenes.batch_scene(i, precision=0) for i in seeds]
+        plain, hs = serving.run_sequential(fp64, n_steps=10)
+        serving.destroy(hs)
+        _progress(f"plain FP64 one at a time: {plain['steps_per_s']:.1f} steps/s")
+        batched["steps_per_s"] = allsum(ws, batched["steps"]) / allmax(ws, batched["seconds"])
+        plain["steps_per_s"] = allsum(ws, plain["steps"]) / allmax(ws, plain["seconds"])
+    if args.serve_requests > 0:
+        from paper_2512_12151_b300 import serving
+        reqs = serving.poisson_requests(args.serve_requests, args.serve_rate, seed=1000 + rank)
+        served = serving.serve(reqs, n_steps=10, n_workers=args.batch_workers)
+        _progress(f"served: {served['steps_per_s']:.1f} steps/s")
+        served["steps_per_s"] = allsum(ws, served["steps"]) / allmax(ws, served["seconds"])
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         v, n, el = oracle_sample(args.cpu_seconds, seed)
@@ -409,6 +450,19 @@ def main():
                            "mean_cg_iters_per_step": statistics.mean(st["cg_iters"] for st in timed_stats),
                            "mean_contacts": nc_mean},
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "batched": None if batched is None else dict(
+                    batched, workload=f"{args.batched_scenes} independent scenes per GPU (seeded): 1k-20k tets "
+                    "log-uniform, one cube or a stack of two on a ground quad, E log-uniform 1e4-1e6 Pa, "
+                    "nu U(0.3, 0.45), h = 0.01 s, 10 steps each, mixed precision, "
+                    f"{args.batch_workers} streams (native batch runner)", unit="steps/s"),
+                "plain_fp64_one_at_a_time": None if plain is None else dict(
+                    plain, workload="the same scenes in FP64, one scene at a time on one stream", unit="steps/s"),
+                "batched_vs_plain_fp64": (batched["steps_per_s"] / plain["steps_per_s"]) if batched and plain
+                else None,
+                "serving": None if served is None else dict(
+                    served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
+                    f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "
+                    "mixed precision, HBM budget 150 GB, scene creation inside the served loop", unit="steps/s"),
                 "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line))
     if ws > 1:

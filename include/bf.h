@@ -201,7 +201,11 @@ int bf_energy(bf_scene *scene, const double *xtilde, const double *xlin, const d
               double *L);
 
 /* Alg. 2 SolveSubproblem: xhat (device, in/out) from xhat, updating the
- * multipliers and decay factors of C.  newton/cg (host, may be NULL). */
+ * multipliers and decay factors of C.  Newton ends when the line search
+ * accepts the full step (r = 1 among r = 1, 1/2, ..., 2^-max_ls, accepted
+ * when L(xhat + r p) <= L(xhat) + 1e-12 max(|L(xhat)|, |L| at the first
+ * Newton iterate of the time step, or of this call)) or after max_newton
+ * iterations.  newton/cg (host, may be NULL). */
 int bf_solve_subproblem(bf_scene *scene, const double *xtilde, const double *xlin, double *xhat,
                         int32_t *newton, int32_t *cg);
 

@@ -47,6 +47,7 @@ struct or_scene {
     double *clam, *cgam, *cd, *cg, *cs;
     or_params p;
     double mu, delta;
+    double L_scale; /* |L| at the time step's first Newton iterate (< 0: unset) */
 };
 
 /* ------------------------------------------------------------------ */
@@ -644,6 +645,7 @@ or_scene *or_create(int32_t nv, const double *rest, const double *x0, const doub
     S->cg = (double *)xcalloc(12 * S->ccap, sizeof(double));
     S->mu = 0.0;
     S->delta = prm->delta;
+    S->L_scale = -1.0;
     return S;
 }
 
@@ -1076,14 +1078,28 @@ double or_energy_L(or_scene *S, const double *xtilde, const double *xlin, const 
 
 /* Alg. 2 SolveSubproblem.  Readings: the line search holds s fixed at the
  * values of the current Newton iteration and accepts
- * L(xhat + r p) <= L(xhat) + 1e-12 |L(xhat)| for r = 1, 1/2, ...,
- * 2^-max_ls (the paper's strict "<" can loop forever once p ~ 0); a failed
+ * L(xhat + r p) <= L(xhat) + 1e-12 max(|L(xhat)|, L_s) for r = 1, 1/2,
+ * ..., 2^-max_ls, L_s being |L| at the first Newton iterate of the time step
+ * (of this call when called alone).  The paper's strict "<" can loop forever
+ * once p ~ 0, and a tolerance relative to |L(xhat)| alone rejects full steps
+ * by round-off once L has converged to about zero, as in free fall, where
+ * a later subproblem starts at its optimum.  A failed
  * line search ends the Newton loop without a step; the Newton loop is
  * capped at max_newton iterations.  xhat is updated in place and the
  * multipliers and decay factors of C are updated as in the multiplier and decay update of Alg. 2.
  * Returns the number of Newton iterations. */
+static int32_t solve_subproblem(or_scene *S, const double *xtilde, const double *xlin, double *xhat,
+                                int32_t *cg_iters, int32_t *ls_fail);
+
 int32_t or_solve_subproblem(or_scene *S, const double *xtilde, const double *xlin, double *xhat,
                             int32_t *cg_iters, int32_t *ls_fail)
+{
+    S->L_scale = -1.0;
+    return solve_subproblem(S, xtilde, xlin, xhat, cg_iters, ls_fail);
+}
+
+static int32_t solve_subproblem(or_scene *S, const double *xtilde, const double *xlin, double *xhat,
+                                int32_t *cg_iters, int32_t *ls_fail)
 {
     int n = 3 * S->nv;
     double *g = (double *)xcalloc(n, sizeof(double)), *b = (double *)xcalloc(n, sizeof(double));
@@ -1099,12 +1115,14 @@ int32_t or_solve_subproblem(or_scene *S, const double *xtilde, const double *xli
         int it = or_pcg(S, b, pdir, S->p.cg_tol, S->p.max_cg);
         cgsum += it < 0 ? -it : it;
         double L0 = or_energy_L(S, xtilde, xlin, xhat, sfix);
+        if (S->L_scale < 0.0) S->L_scale = fabs(L0);
+        double ls_tol = 1e-12 * fmax(fabs(L0), S->L_scale);
         double r = 1.0;
         int ok = 0;
         for (int j = 0; j <= S->p.max_ls; ++j) {
             for (int i = 0; i < n; ++i) xt[i] = xhat[i] + r * pdir[i];
             double L1 = or_energy_L(S, xtilde, xlin, xt, sfix);
-            if (L1 <= L0 + 1e-12 * fabs(L0)) { ok = 1; break; }
+            if (L1 <= L0 + ls_tol) { ok = 1; break; }
             r *= 0.5;
         }
         ++newton;
@@ -1381,6 +1399,7 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
                 if (S->dir[v])
                     for (int c = 0; c < 3; ++c) xh[3 * v + c] = S->targets[3 * v + c];
         S->delta = S->p.delta;
+        S->L_scale = -1.0; /* set by the step's first Newton iterate */
         or_mu_init(S, xh, xtilde);
         double beta = 1.0, asum = 0.0;
         int k = 0, stall = 0;
@@ -1388,7 +1407,7 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
             if (k >= S->p.max_outer) { status = -7; break; }
             memcpy(xhn, xh, n * sizeof(double));
             int32_t cgi = 0, lsf = 0;
-            st.newton_iters += or_solve_subproblem(S, xtilde, xk, xhn, &cgi, &lsf);
+            st.newton_iters += solve_subproblem(S, xtilde, xk, xhn, &cgi, &lsf);
             st.cg_iters += cgi;
             st.ls_fail += lsf;
             or_update_active_set(S, xk, xh);

@@ -238,8 +238,12 @@ struct SolveStats {
 };
 
 // Alg. 2 SolveSubproblem (xhat in/out).  Line search: r = 1, 1/2, ...,
-// 2^-max_ls with L(xhat + r p) <= L(xhat) + 1e-12 |L(xhat)| and the slacks
-// of the current Newton iteration held fixed.
+// 2^-max_ls with L(xhat + r p) <= L(xhat) + 1e-12 max(|L(xhat)|, L_s) and
+// the slacks of the current Newton iteration held fixed; L_s (S.L_scale) is
+// |L| at the first Newton iterate of the time step (of the call when called
+// alone), so that round-off cannot reject full steps once L has converged to
+// about zero, as in free fall, where a later subproblem starts at its
+// optimum.
 static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, double *xhat, SolveStats &ss)
 {
     const int n = 3 * S.nv;
@@ -258,12 +262,14 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
         else if (st) return st;
         const double L0 = run_energy(S, xtilde, xlin, xhat);
         if (!std::isfinite(L0)) return BF_E_NONFINITE;
+        if (S.L_scale < 0.0) S.L_scale = std::fabs(L0);
+        const double ls_tol = 1e-12 * std::max(std::fabs(L0), S.L_scale);
         double r = 1.0;
         bool ok = false;
         for (int j = 0; j <= S.prm.max_ls; ++j) {
             launch_axpy_to(S, S.xtmp, xhat, r, S.pdir, n);
             const double L1 = run_energy(S, xtilde, xlin, S.xtmp);
-            if (std::isfinite(L1) && L1 <= L0 + 1e-12 * std::fabs(L0)) {
+            if (std::isfinite(L1) && L1 <= L0 + ls_tol) {
                 ok = true;
                 break;
             }
@@ -298,6 +304,7 @@ static int step_once(Scene &S, bf_step_stats *out)
             k_apply_targets<<<cdiv(S.ndir, kThreads), kThreads, 0, S.stream>>>(S.ndir, S.dir_ids, S.targets, S.xh); ++S.n_launch;
         }
     S.delta = S.prm.delta;
+    S.L_scale = -1.0;  // set by the step's first Newton iterate
     S.bvh_tri.topo_valid = S.bvh_edge.topo_valid = 0;  // one tree topology per time step
     S.bvh_reuse = true;
     struct ReuseOff {
@@ -1043,6 +1050,7 @@ int bf_solve_subproblem(bf_scene *scene, const double *xtilde, const double *xli
     SCENE_OR_ARG(scene);
     if (!xtilde || !xlin || !xhat || !(S.mu > 0)) return BF_E_ARG;
     SolveStats ss;
+    S.L_scale = -1.0;  // called alone: the scale comes from this call's first iterate
     const int st = solve_subproblem(S, xtilde, xlin, xhat, ss);
     if (newton) *newton = ss.newton;
     if (cg) *cg = ss.cg;

@@ -60,6 +60,7 @@ struct Scene {
     int nsv = 0, nst = 0, nse = 0, nnzb = 0;
     bf_params prm{};
     double mu = 0.0, delta = 0.0;
+    double L_scale = -1.0;  // |L| at the time step's first Newton iterate (< 0: unset)
     int has_targets = 0;
     cudaStream_t stream = nullptr;
     bf_allocator alloc{};

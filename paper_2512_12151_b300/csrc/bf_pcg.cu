@@ -47,6 +47,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -206,6 +208,8 @@ __device__ __forceinline__ void block_sum(double (&a)[K], double (&out)[K], doub
         }
 }
 
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
+
 // Grid-wide sum of K block sums (called by thread 0 of every CTA) that
 // doubles as the grid barrier.  Reduction: each CTA adds its block sum to
 // accumulator slot (n % 3) with an FP64 atomic add, n = the count of
@@ -228,11 +232,16 @@ __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, un
     const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
     unsigned old;
     asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
-    unsigned long long spins = 0;
+    unsigned spins = 0;
+    unsigned long long t_start = 0;
     while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
-        if (++spins > (1ull << 28)) {
-            atomicOr(dflag + F_ERR, ERR_BARRIER);
-            return false;
+        if ((++spins & 255u) == 0u) {  // give up after kBarrierTimeoutNs
+            const unsigned long long t = globaltimer();
+            if (t_start == 0) t_start = t;
+            else if (t - t_start > kBarrierTimeoutNs) {
+                atomicOr(dflag + F_ERR, ERR_BARRIER);
+                return false;
+            }
         }
     }
 #pragma unroll
@@ -906,6 +915,48 @@ static int setup_persistent(Scene &S)
     return BF_E_CAPACITY;
 }
 
+// Persistent kernels launched from different streams (scenes of a batch)
+// may run at the same time only if all their CTAs fit on the device
+// together: each CTA spins at grid barriers for the others, so two grids
+// that each hold part of the SMs while waiting for the rest would wait for
+// each other.  A process-wide budget of SM slots per device enforces that;
+// ordinary kernels always finish, so they only delay a grid.
+constexpr int kSlotsPerSm = 12;  // a CTA of a grid at c CTAs per SM takes 12 / c slots
+
+struct CoopSlots {
+    std::mutex mu;
+    std::condition_variable cv;
+    int used = 0;
+};
+
+static CoopSlots &coop_slots(int dev)
+{
+    static CoopSlots slots[64];
+    return slots[dev & 63];
+}
+
+class CoopGuard {
+  public:
+    CoopGuard(int dev, int units, int capacity) : c_(coop_slots(dev)), units_(std::min(units, capacity))
+    {
+        std::unique_lock<std::mutex> lk(c_.mu);
+        c_.cv.wait(lk, [&] { return c_.used + units_ <= capacity; });
+        c_.used += units_;
+    }
+    ~CoopGuard()
+    {
+        {
+            std::lock_guard<std::mutex> lk(c_.mu);
+            c_.used -= units_;
+        }
+        c_.cv.notify_all();
+    }
+
+  private:
+    CoopSlots &c_;
+    int units_;
+};
+
 template <class MT, class VT>
 static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *p1, VT *qc, VT *z, const double *b,
                            double *x, double tol, int maxit, int *iters)
@@ -957,6 +1008,11 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
     void *args[] = {&A};
     cudaError_t e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cps = std::max(1, kPcgThreads / S.pcg_block);
+    CoopGuard slots(dev, grid * (kSlotsPerSm / std::min(cps, kSlotsPerSm)), nsm * kSlotsPerSm);  // held until done
     {
         ScopedTimer tm(S, T_PCG_PERSISTENT);
         const void *kern = S.pcg_resident ? (const void *)k_pcg_persistent<MT, VT, true>

@@ -205,7 +205,8 @@ def batch_scene(seed: int, t_lo: float = 1e3, t_hi: float = 2e4, precision: int 
     tet count T ~ log-uniform [t_lo, t_hi], a single cube or a stack of two
     (probability 1/2 each), n = max(2, round((T / (6 k))^(1/3))) cells per
     cube edge (k cubes), E ~ log-uniform [1e4, 1e6] Pa, nu ~ U(0.3, 0.45),
-    rho = 1000 kg/m^3; cubes of side 0.1 m, the lower one 1 cm above a
+    rho = 1000 kg/m^3; cubes of side 0.1 m centred at a seeded xy position
+    U(-0.3, 0.3)^2 with a seeded yaw U(0, 2 pi), the lower one 1 cm above a
     static 2 m x 2 m ground quad, the upper one 1 mm above it; h = 0.01 s,
     10 steps."""
     rng = np.random.default_rng(seed)
@@ -214,9 +215,11 @@ def batch_scene(seed: int, t_lo: float = 1e3, t_hi: float = 2e4, precision: int 
     cells = max(2, int(round((target / (6 * k)) ** (1.0 / 3.0))))
     E = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
     nu = rng.uniform(0.3, 0.45)
+    cx, cy = rng.uniform(-0.3, 0.3, size=2)
+    yaw = rng.uniform(0.0, 2 * math.pi)
     b = _Builder()
     for j in range(k):
-        v, t = _jittered_cube(rng, cells, side, (-side / 2, -side / 2, 0.01 + j * (side + 1e-3)))
+        v, t = _jittered_cube(rng, cells, side, (cx - side / 2, cy - side / 2, 0.01 + j * (side + 1e-3)), yaw)
         b.add_solid(v, t, 0)
     gv, gt = ground_quad(1.0)
     b.add_obstacle(gv, gt)

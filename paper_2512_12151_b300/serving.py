@@ -53,7 +53,14 @@ def _summary(lat, steps, elapsed):
             "p99_step_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None}
 
 
-def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30):
+def _wait(b, t, deadline):
+    """waits for a ticket, raising once the monotonic deadline has passed"""
+    while not B.bf_batch_wait(b, t, 1000):
+        if time.monotonic() > deadline:
+            raise TimeoutError(f"batch ticket {t} did not finish in time")
+
+
+def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30, timeout_s=900.0):
     """Creates every scene (untimed), then admits them all at once to a batch
     and runs them to completion.  Returns throughput and per-step latency
     (from the admission of all scenes)."""
@@ -67,8 +74,9 @@ def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30):
             if t is None:
                 raise RuntimeError("batch admission refused by the HBM budget")
             tickets.append(t)
+        deadline = time.monotonic() + timeout_s
         for t in tickets:
-            B.bf_batch_wait(b, t)
+            _wait(b, t, deadline)
         lat, steps, t_end, bad = [], 0, t0, 0
         for t, s in zip(tickets, scene_list):
             r = B.bf_batch_result(b, t, n_steps or s.n_steps)
@@ -116,7 +124,7 @@ def poisson_requests(n, rate, seed=0, t_lo=2e3, t_hi=2e5, precision=1):
     return [(float(a), int(rng.integers(1 << 30)), t_lo, t_hi, precision) for a in arrivals]
 
 
-def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002):
+def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002, timeout_s=900.0):
     """Serves a request stream: at each arrival time the request's scene is
     generated and created, then admitted to the running batch (waiting
     while the HBM budget refuses it); finished scenes are released and
@@ -125,6 +133,7 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
     completion of the scene's previous step, or its admission) and the
     admission wait (admission minus arrival) p50/p99."""
     b = B.bf_batch_create(n_workers, budget_bytes)
+    deadline = time.monotonic() + timeout_s
     live = {}  # ticket -> (handle, keep, arrival)
     lat, waits, steps, bad = [], [], 0, 0
     lock = threading.Lock()
@@ -133,7 +142,7 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
         nonlocal steps, bad
         for t in list(live):
             if block:
-                B.bf_batch_wait(b, t)
+                _wait(b, t, deadline)
             elif not B.bf_batch_wait(b, t, 0):
                 continue
             r = B.bf_batch_result(b, t, n_steps)
@@ -164,7 +173,7 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
             live[t] = (h, keep, arrival)
             reap()
         for t in list(live):
-            B.bf_batch_wait(b, t)
+            _wait(b, t, deadline)
         last_done = B.bf_batch_now(b)
         reap(block=True)
         out = _summary(lat, steps, last_done - t0 - requests[0][0] if requests else 0.0)
@@ -175,8 +184,6 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
                     "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None})
         return out
     finally:
-        for t, (h, _k, _a) in list(live.items()):
-            B.bf_batch_wait(b, t)
-        B.bf_batch_destroy(b)
+        B.bf_batch_destroy(b)  # stops the workers after their current step
         for t, (h, _k, _a) in list(live.items()):
             B.bf_scene_destroy(h)
