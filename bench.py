@@ -462,7 +462,7 @@ def main():
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "
-                    "mixed precision, HBM budget 150 GB, scene creation inside the served loop", unit="steps/s"),
+                    "mixed precision, HBM budget 150 GB, scenes generated and created inside the served loop by 8 host threads", unit="steps/s"),
                 "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line))
     if ws > 1:

@@ -124,66 +124,83 @@ def poisson_requests(n, rate, seed=0, t_lo=2e3, t_hi=2e5, precision=1):
     return [(float(a), int(rng.integers(1 << 30)), t_lo, t_hi, precision) for a in arrivals]
 
 
-def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002, timeout_s=900.0):
-    """Serves a request stream: at each arrival time the request's scene is
-    generated and created, then admitted to the running batch (waiting
-    while the HBM budget refuses it); finished scenes are released and
-    destroyed as they complete.  Returns aggregate steps/s (first arrival to
-    last completion), per-step latency p50/p99 (completion of a step minus
-    completion of the scene's previous step, or its admission) and the
-    admission wait (admission minus arrival) p50/p99."""
+def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002, timeout_s=900.0,
+          n_creators=8):
+    """Serves a request stream: at each arrival time the request is handed
+    to one of `n_creators` host threads, which generates and creates its
+    scene and admits it to the running batch (waiting while the HBM budget
+    refuses it); finished scenes are released and destroyed as they
+    complete.  Returns aggregate steps/s (first arrival to last completion),
+    per-step latency p50/p99 (completion of a step minus completion of the
+    scene's previous step, or its admission) and the admission wait
+    (admission minus arrival, scene creation included) p50/p99."""
+    from concurrent.futures import ThreadPoolExecutor
     b = B.bf_batch_create(n_workers, budget_bytes)
     deadline = time.monotonic() + timeout_s
-    live = {}  # ticket -> (handle, keep, arrival)
+    live = {}  # ticket -> (handle, keep)
     lat, waits, steps, bad = [], [], 0, 0
     lock = threading.Lock()
+    t0 = B.bf_batch_now(b)
+
+    def admit(req):
+        arrival, seed, t_lo, t_hi, prec = req
+        s = scenes.batch_scene(seed, t_lo, t_hi, precision=prec)
+        h, keep = create(s)
+        while True:
+            t = B.bf_batch_admit(b, h, n_steps)
+            if t is not None:
+                break
+            if time.monotonic() > deadline:
+                B.bf_scene_destroy(h)
+                raise TimeoutError("admission kept being refused by the HBM budget")
+            time.sleep(poll_s)
+        with lock:
+            waits.append(B.bf_batch_now(b) - t0 - arrival)
+            live[t] = (h, keep)
 
     def reap(block=False):
         nonlocal steps, bad
-        for t in list(live):
+        with lock:
+            tickets = list(live)
+        for t in tickets:
             if block:
                 _wait(b, t, deadline)
             elif not B.bf_batch_wait(b, t, 0):
                 continue
             r = B.bf_batch_result(b, t, n_steps)
-            h, _keep, _arr = live.pop(t)
             with lock:
+                h, _keep = live.pop(t)
                 lat.extend(_latencies(r))
                 steps += r["steps_done"]
                 bad += r["status"] != 0
             B.bf_batch_release(b, t)
             B.bf_scene_destroy(h)
 
+    pool = ThreadPoolExecutor(max_workers=n_creators)
     try:
-        t0 = B.bf_batch_now(b)
-        last_done = t0
-        for arrival, seed, t_lo, t_hi, prec in requests:
-            while B.bf_batch_now(b) - t0 < arrival:
+        futures = []
+        for req in requests:
+            while B.bf_batch_now(b) - t0 < req[0]:
                 reap()
-                time.sleep(min(poll_s, max(0.0, arrival - (B.bf_batch_now(b) - t0))))
-            s = scenes.batch_scene(seed, t_lo, t_hi, precision=prec)
-            h, keep = create(s)
-            while True:
-                t = B.bf_batch_admit(b, h, n_steps)
-                if t is not None:
-                    break
-                reap()
-                time.sleep(poll_s)
-            waits.append(B.bf_batch_now(b) - t0 - arrival)
-            live[t] = (h, keep, arrival)
-            reap()
-        for t in list(live):
+                time.sleep(min(poll_s, max(0.0, req[0] - (B.bf_batch_now(b) - t0))))
+            futures.append(pool.submit(admit, req))
+        for f in futures:
+            f.result(timeout=max(1.0, deadline - time.monotonic()))
+        with lock:
+            tickets = list(live)
+        for t in tickets:
             _wait(b, t, deadline)
         last_done = B.bf_batch_now(b)
         reap(block=True)
         out = _summary(lat, steps, last_done - t0 - requests[0][0] if requests else 0.0)
         w = np.asarray(waits)
-        out.update({"requests": len(requests), "failed": bad, "workers": n_workers,
+        out.update({"requests": len(requests), "failed": bad, "workers": n_workers, "creators": n_creators,
                     "admission_wait_p50_ms": float(np.percentile(w, 50) * 1e3) if len(w) else None,
                     "admission_wait_p99_ms": float(np.percentile(w, 99) * 1e3) if len(w) else None,
                     "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None})
         return out
     finally:
+        pool.shutdown(wait=True)
         B.bf_batch_destroy(b)  # stops the workers after their current step
-        for t, (h, _k, _a) in list(live.items()):
+        for h, _k in list(live.values()):
             B.bf_scene_destroy(h)
