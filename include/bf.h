@@ -261,11 +261,13 @@ int bf_max_step_size_pairs_noalloc(int32_t type, int32_t n, const double *x0, co
  * static strings.  Returns the number of timed kernels. */
 int bf_enable_timers(bf_scene *scene, int32_t on);
 /* PCG execution.  0 = three launches per iteration with the scalar
- * recurrences kept on the device.  1..15 = one persistent cooperative
- * launch per solve with two grid barriers per iteration and up to `mode`
+ * recurrences kept on the device.  1..4 = one persistent cooperative launch
+ * per solve with two grid-wide reductions per iteration and up to `mode`
  * CTAs per SM (default 1), keeping the matrix in shared memory when it
- * fits; adding 16 forbids the shared-memory copy (blocks streamed from
- * global memory).  Same arithmetic in every mode. */
+ * fits, else streaming it, with the per-row vectors in global memory when
+ * they do not fit in shared memory either; adding 16 forbids the
+ * shared-memory copy of the matrix; adding 32 forces the global-memory
+ * variant.  Same arithmetic in every mode. */
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
 
 /* Configuration of the persistent PCG chosen at the scene's first solve

@@ -1123,11 +1123,12 @@ int bf_enable_timers(bf_scene *scene, int32_t on)
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
 {
     SCENE_OR_ARG(scene);
-    if (mode < 0 || mode > 32) return BF_E_ARG;
+    if (mode < 0 || mode > 63) return BF_E_ARG;
     S.pcg_mode = mode == 0 ? 0 : 1;
     if (mode > 0) {
         S.pcg_ctas_per_sm = mode & 15;
         S.pcg_allow_resident = (mode & 16) ? 0 : 1;
+        S.pcg_force_global = (mode & 32) ? 1 : 0;
         S.pcg_grid = 0;  // recomputed at the next solve
     }
     return BF_OK;

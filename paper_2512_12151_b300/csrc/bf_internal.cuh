@@ -90,7 +90,7 @@ struct Scene {
     std::vector<int> h_frowptr;
     int *part = nullptr;      // persistent PCG: CTA row ranges (grid + 1)
     int pcg_smem = 0;         // dynamic shared memory of the persistent PCG (bytes)
-    int pcg_resident = 0;     // 1: matrix resident in shared memory
+    int pcg_resident = 0;     // persistent PCG mode: 0 streamed via the BSR, 1 resident, 2 global vectors
     double *val = nullptr;  // 9 planes FP64
     float *valf = nullptr;  // 9 planes FP32 (mixed)
     double *grad = nullptr;
@@ -108,10 +108,16 @@ struct Scene {
     int pcg_mode = 1;         // 1 = persistent cooperative kernel, 0 = one launch per phase
     int pcg_ctas_per_sm = 1;  // persistent PCG: CTAs per SM (capped by occupancy)
     int pcg_allow_resident = 1;  // persistent PCG may keep the matrix in shared memory
+    int pcg_force_global = 0;    // persistent PCG: use the global-vectors variant only
     int pcg_max_rows = 0, pcg_max_ent = 0, pcg_max_win = 0, pcg_block = 256;
     unsigned short *pcg_eslot = nullptr;  // persistent PCG: shared-memory slot of every full-row entry
     int *pcg_rinfo = nullptr, *pcg_lvl = nullptr, *pcg_lvlptr = nullptr;  // rows by length, level offsets
     int pcg_max_len = 0;
+    int *pcg_edst = nullptr;              // persistent PCG, global variant: jagged position of each entry
+    unsigned short *pcg_jnbr = nullptr;   // ... window offset of each jagged slot
+    void *pcg_jval = nullptr;             // ... jagged copy of the blocks (9 planes)
+    unsigned char *pcg_gvec = nullptr;    // ... per-CTA vectors
+    size_t pcg_gvec_stride = 0;
     int pcg_kc = 0;               // persistent PCG: contacts per CTA cached in shared memory
     int *win = nullptr;       // persistent PCG: staged vertex window per CTA
     std::vector<int> h_fnbr;

@@ -67,6 +67,11 @@ struct PcgArgs {
     int nv, nc;
     const int *part, *win, *frowptr;
     const unsigned short *eslot;     // shared-memory slot of every full-row entry (resident variant)
+    const void *jval;                // global variant: blocks in jagged order, 9 planes of nfull values
+    const unsigned short *jnbr;      // global variant: window offset of each jagged slot
+    unsigned char *gvec;             // global variant: per-CTA x, x_l, r, q (gvec_stride bytes each)
+    size_t gvec_stride;
+    int nfull;
     const int *rinfo, *lvl, *lvlptr;  // rows by decreasing length; level offsets per CTA
     const int *fnbr, *fblk;
     const void *val;
@@ -299,9 +304,16 @@ struct PcgLayout {
     size_t x, xl, r, q, pinv, p4, val, nbr, rinfo, lvl, cg, cp, cw, cv, cm, total;
 };
 
+// Modes: 0 = blocks read from the BSR values through the full-row map,
+// vectors in shared memory; 1 = blocks resident in shared memory; 2 = blocks
+// streamed from a jagged copy in global memory (coalesced), per-row vectors
+// in global memory (systems whose rows do not fit in shared memory).
+enum { PCG_STREAM = 0, PCG_RESIDENT = 1, PCG_GLOBAL = 2 };
+
 __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
-                                                int max_len, bool res, int kc)
+                                                int max_len, int mode, int kc)
 {
+    const bool res = mode == PCG_RESIDENT, vec = mode != PCG_GLOBAL;
     PcgLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -310,11 +322,11 @@ __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int 
         return at;
     };
     const int rt = mixed ? 4 : 8;
-    L.x = take(3 * (size_t)max_rows * 8);
-    L.xl = take(mixed ? 3 * (size_t)max_rows * rt : 0);
-    L.r = take(3 * (size_t)max_rows * rt);
-    L.q = take(3 * (size_t)max_rows * (mixed ? 8 : ct));  // FP64 H x of the reliable updates reuses it
-    L.pinv = take(9 * (size_t)max_rows * mt);
+    L.x = take(vec ? 3 * (size_t)max_rows * 8 : 0);
+    L.xl = take(vec && mixed ? 3 * (size_t)max_rows * rt : 0);
+    L.r = take(vec ? 3 * (size_t)max_rows * rt : 0);
+    L.q = take(vec ? 3 * (size_t)max_rows * (mixed ? 8 : ct) : 0);  // FP64 H x of the reliable updates reuses it
+    L.pinv = take(vec ? 9 * (size_t)max_rows * mt : 0);
     L.p4 = take(4 * (size_t)max_win * ct);
     L.val = take(res ? 9 * (size_t)max_ent * mt : 0);
     L.nbr = take(res ? (size_t)max_ent * 2 : 0);
@@ -329,12 +341,21 @@ __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int 
     return L;
 }
 
+// the per-CTA vector region of the global variant (same offsets scheme)
+__host__ __device__ inline PcgLayout pcg_vec_layout(bool mixed, int ct, int max_rows)
+{
+    PcgLayout L = pcg_layout(mixed, ct, 4, max_rows, 0, 0, 0, PCG_STREAM, 0);
+    L.total = L.pinv;  // x, x_l, r, q only
+    return L;
+}
+
 // bytes of one cached contact pair (gradient, p at its vertices, weight, ids, flags)
 inline size_t pcg_contact_bytes(int ct) { return 25 * (size_t)ct + 20; }
 
-template <class MT, class VT, bool RES>
+template <class MT, class VT, int MODE>
 __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 {
+    constexpr bool RES = MODE == PCG_RESIDENT, GV = MODE == PCG_GLOBAL;
     using CT = typename std::conditional<(sizeof(MT) >= sizeof(VT)), MT, VT>::type;
     constexpr bool mixed = sizeof(VT) == 4;
     using RT = typename std::conditional<mixed, float, double>::type;  // r and the iteration part of x
@@ -356,14 +377,16 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;  // pairs c + k grid
     const int ncached = min(nco, A.kc);
     const PcgLayout L =
-        pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, A.max_len, RES, A.kc);
+        pcg_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, A.max_len, MODE, A.kc);
+    const PcgLayout Lv = GV ? pcg_vec_layout(mixed, sizeof(CT), A.max_rows) : L;
+    unsigned char *vb = GV ? A.gvec + (size_t)c * A.gvec_stride : smem;  // per-row vectors
     const int ld = A.max_rows;  // per-row arrays are component-major: a[c * ld + row]
-    double *s_x = (double *)(smem + L.x);
-    RT *s_xl = (RT *)(smem + L.xl);
-    RT *s_r = (RT *)(smem + L.r);
-    CT *s_q = (CT *)(smem + L.q);
-    double *s_hx = (double *)(smem + L.q);
-    MT *s_pinv = (MT *)(smem + L.pinv);
+    double *s_x = (double *)(vb + Lv.x);
+    RT *s_xl = (RT *)(vb + Lv.xl);
+    RT *s_r = (RT *)(vb + Lv.r);
+    CT *s_q = (CT *)(vb + Lv.q);
+    double *s_hx = (double *)(vb + Lv.q);
+    const MT *s_pinv = GV ? gpinv + 9 * (size_t)r0 : (const MT *)(smem + L.pinv);
     CT *s_p4 = (CT *)(smem + L.p4);
     MT *s_val = (MT *)(smem + L.val);
     unsigned short *s_nbr = (unsigned short *)(smem + L.nbr);
@@ -374,7 +397,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     CT *s_cw = (CT *)(smem + L.cw);
     int4 *s_cv = (int4 *)(smem + L.cv);
     int *s_cm = (int *)(smem + L.cm);
-    for (int i = threadIdx.x; i < 9 * nr; i += blockDim.x) s_pinv[i] = gpinv[9 * (size_t)r0 + i];
+    if (!GV)
+        for (int i = threadIdx.x; i < 9 * nr; i += blockDim.x) ((MT *)(smem + L.pinv))[i] = gpinv[9 * (size_t)r0 + i];
     if (RES) {
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             const int fe = E0 + e;
@@ -393,8 +417,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             }
             s_nbr[slot] = (unsigned short)(A.fnbr[fe] - wlo);
         }
-        for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
     }
+    if (RES || GV)
+        for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
     for (int t = threadIdx.x; t < nr; t += blockDim.x) s_rinfo[t] = A.rinfo[r0 + t];
     for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
         const int i = c + k * (int)gridDim.x;
@@ -415,6 +440,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 #pragma unroll
             for (int i = 0; i < 9; ++i) a[i] = (CT)v[i];
             return s_nbr[slot];
+        } else if (GV) {  // 9 coalesced planes, streamed past the caches
+            const size_t slot = (size_t)E0 + s_lvl[j] + t;
+            const MT *v = (const MT *)A.jval + slot;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) a[i] = (CT)__ldcs(v + (size_t)i * A.nfull);
+            return __ldcs(A.jnbr + slot);
         } else {
             const int fe = __ldg(A.frowptr + r0 + row) + j;
             const int fb = __ldg(A.fblk + fe);
@@ -794,7 +825,8 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
     }
     part[grid] = S.nv;
     std::vector<int> win(2 * grid), rinfo(S.nv), lvl, lvlptr(grid + 1, 0);
-    std::vector<unsigned short> eslot(S.nfull);
+    std::vector<unsigned short> eslot(S.nfull), jnbr(S.nfull);
+    std::vector<int> edst(S.nfull);
     int mr = 0, me = 0, mw = 0, ml = 0;
     std::vector<int> order;
     for (int c = 0; c < grid; ++c) {
@@ -824,7 +856,12 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
         for (int t = 0; t < b - a; ++t) {
             const int v = order[t];
             rinfo[a + t] = (v - a) << 8 | len(v);
-            for (int j = 0; j < len(v); ++j) eslot[fr[v] + j] = (unsigned short)(at[j] + t);
+            for (int j = 0; j < len(v); ++j) {
+                const int fe = fr[v] + j, slot = at[j] + t;
+                eslot[fe] = (unsigned short)slot;
+                edst[fe] = fr[a] + slot;  // jagged position in global memory
+                jnbr[fr[a] + slot] = (unsigned short)(fn[fe] - lo);
+            }
         }
         lvl.insert(lvl.end(), at.begin(), at.end());
         lvlptr[c + 1] = (int)lvl.size();
@@ -848,6 +885,8 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
     if (!st) st = put(S.pcg_rinfo, rinfo);
     if (!st) st = put(S.pcg_lvl, lvl);
     if (!st) st = put(S.pcg_lvlptr, lvlptr);
+    if (!st) st = put(S.pcg_edst, edst);
+    if (!st) st = put(S.pcg_jnbr, jnbr);
     if (st) return st;
     *max_rows = mr;
     *max_ent = me;
@@ -873,8 +912,13 @@ static int setup_persistent(Scene &S)
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return BF_E_CUDA;
     const int per_sm = std::min(4, std::max(1, S.pcg_ctas_per_sm));
-    for (int res = S.pcg_allow_resident ? 1 : 0; res >= 0; --res) {
-        auto kern = res ? k_pcg_persistent<MT, VT, true> : k_pcg_persistent<MT, VT, false>;
+    const int modes[3] = {PCG_RESIDENT, PCG_STREAM, PCG_GLOBAL};
+    for (int mode : modes) {
+        if (mode == PCG_RESIDENT && !S.pcg_allow_resident) continue;
+        if (mode != PCG_GLOBAL && S.pcg_force_global) continue;
+        const void *kern = mode == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
+                           : mode == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
+                                                : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BF_E_CUDA;
         for (int cps = per_sm; cps >= 1; --cps) {
@@ -889,21 +933,30 @@ static int setup_persistent(Scene &S)
             if (st == BF_E_CAPACITY) continue;
             if (st) return st;
             const size_t avail = (size_t)smem_optin - fa.sharedSizeBytes;
-            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, 0);
+            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, 0);
             if (L0.total > avail) continue;
             int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(sizeof(CT)));
-            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc).total > avail) --kc;
-            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, res != 0, kc);
+            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, kc).total > avail) --kc;
+            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, kc);
             // the attribute is an upper bound shared by every scene: set it to
             // the most any launch may ask for, so concurrent set-ups agree
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
             if (occ < cps) continue;
+            if (mode == PCG_GLOBAL) {  // jagged block copy and per-CTA vectors in global memory
+                const size_t stride = (pcg_vec_layout(mixed, sizeof(CT), mr).total + 255) & ~(size_t)255;
+                if (S.pcg_gvec) dev_free(S, S.pcg_gvec);
+                if (S.pcg_jval) dev_free(S, S.pcg_jval);
+                S.pcg_gvec = (unsigned char *)dev_alloc(S, stride * grid);
+                S.pcg_jval = dev_alloc(S, 9 * (size_t)S.nfull * sizeof(MT));
+                if (!S.pcg_gvec || !S.pcg_jval) return BF_E_OOM;
+                S.pcg_gvec_stride = stride;
+            }
             S.pcg_grid = grid;
             S.pcg_block = block;
             S.pcg_smem = (int)L.total;
-            S.pcg_resident = res;
+            S.pcg_resident = mode;
             S.pcg_max_rows = mr;
             S.pcg_max_ent = me;
             S.pcg_max_win = mw;
@@ -913,6 +966,22 @@ static int setup_persistent(Scene &S)
         }
     }
     return BF_E_CAPACITY;
+}
+
+// global variant: the blocks of every CTA in jagged order, 9 planes
+template <class MT>
+__global__ void k_jagged_gather(int nfull, const int *__restrict__ fblk, const int *__restrict__ edst,
+                                const MT *__restrict__ val, MT *__restrict__ jval)
+{
+    const int fe = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fe >= nfull) return;
+    const int fb = fblk[fe];
+    const MT *src = val + 9 * (size_t)(fb & 0x7fffffff);
+    const size_t d = (size_t)edst[fe];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) jval[(size_t)(3 * i + j) * nfull + d] = fb < 0 ? src[3 * j + i] : src[3 * i + j];
 }
 
 // Persistent kernels launched from different streams (scenes of a batch)
@@ -1000,6 +1069,16 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.max_ent = S.pcg_max_ent;
     A.max_win = S.pcg_max_win;
     A.max_len = S.pcg_max_len;
+    A.jval = S.pcg_jval;
+    A.jnbr = S.pcg_jnbr;
+    A.gvec = S.pcg_gvec;
+    A.gvec_stride = S.pcg_gvec_stride;
+    A.nfull = S.nfull;
+    if (S.pcg_resident == PCG_GLOBAL) {
+        k_jagged_gather<MT><<<cdiv(S.nfull, kThreads), kThreads, 0, S.stream>>>(S.nfull, S.fblk, S.pcg_edst, val,
+                                                                              (MT *)S.pcg_jval);
+        ++S.n_launch;
+    }
     A.kc = S.pcg_kc;
     A.dscal = S.dscal;
     A.dflag = S.dflag;
@@ -1015,8 +1094,9 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     CoopGuard slots(dev, grid * (kSlotsPerSm / std::min(cps, kSlotsPerSm)), nsm * kSlotsPerSm);  // held until done
     {
         ScopedTimer tm(S, T_PCG_PERSISTENT);
-        const void *kern = S.pcg_resident ? (const void *)k_pcg_persistent<MT, VT, true>
-                                          : (const void *)k_pcg_persistent<MT, VT, false>;
+        const void *kern = S.pcg_resident == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
+                           : S.pcg_resident == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
+                                                          : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
         e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(S.pcg_block), args, (size_t)S.pcg_smem, S.stream);
         ++S.n_launch;
     }

@@ -289,6 +289,121 @@ def plate_targets(scene: Scene, step: int) -> np.ndarray:
     return x[scene.dirichlet == 1]
 
 
+def _fibonacci_dirs(n: int, rng) -> np.ndarray:
+    """n roughly uniform unit directions (Fibonacci sphere), jittered"""
+    i = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * i / n
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    r = np.sqrt(1.0 - z * z)
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1) + rng.normal(0.0, 0.08, size=(n, 3))
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _grid_kuhn_mesh(inside, cell: float, origin):
+    """Tets of the grid cells whose centre is inside (boolean array over
+    cells, indexed [i, j, k] along x, y, z), keeping the largest face-
+    connected group of cells; Kuhn split with one diagonal for every cell.
+    Returns (vertices, tets) with unused grid vertices dropped."""
+    from scipy import ndimage
+    lab, n = ndimage.label(inside)
+    if n > 1:
+        sizes = ndimage.sum(inside, lab, index=np.arange(1, n + 1))
+        inside = lab == 1 + int(np.argmax(sizes))
+    ci, cj, ck = np.nonzero(inside)
+    nx, ny, nz = (np.array(inside.shape) + 1)
+    vid = lambda i, j, k: (i * ny + j) * nz + k
+    corners = []
+    for c in range(8):
+        corners.append(vid(ci + (c & 1), cj + ((c >> 1) & 1), ck + ((c >> 2) & 1)))
+    corners = np.stack(corners, axis=1)  # (ncell, 8)
+    tets = corners[:, _KUHN].reshape(-1, 4)
+    used, tets = np.unique(tets, return_inverse=True)
+    tets = tets.reshape(-1, 4).astype(np.int32)
+    i = used // (ny * nz)
+    j = (used // nz) % ny
+    k = used % nz
+    verts = np.stack([i, j, k], axis=1) * cell + np.asarray(origin, dtype=np.float64)
+    d = verts[tets[:, 1:]] - verts[tets[:, :1]]
+    neg = np.linalg.det(d) < 0
+    tets[neg] = tets[neg][:, [0, 2, 1, 3]]
+    return verts, tets
+
+
+def spiky_ball(rng, center, radius=0.1, n_spikes=64, l_lo=0.02, l_hi=0.05, base=0.012, cell=0.0038):
+    """A ball with conical spikes, tetrahedralised on a regular grid: the
+    solid is the sphere of `radius` united with n_spikes cones (directions
+    from a jittered Fibonacci sphere, lengths U(l_lo, l_hi), base radius
+    `base` at the sphere, apex at radius + length); the grid cells (size
+    `cell`) whose centres are inside are kept (largest connected group),
+    each split into 6 tets."""
+    dirs = _fibonacci_dirs(n_spikes, rng)
+    lens = rng.uniform(l_lo, l_hi, size=n_spikes)
+    ext = radius + l_hi
+    n = int(math.ceil(2 * ext / cell))
+    g = (np.arange(n) + 0.5) * cell - n * cell / 2
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    inside = (P * P).sum(1) <= radius * radius
+    for d, L in zip(dirs, lens):
+        t = P @ d
+        rho2 = (P * P).sum(1) - t * t
+        cand = (t >= radius - base) & (t <= radius + L)
+        rr = base * np.clip((radius + L - t) / L, 0.0, None)
+        inside |= cand & (rho2 <= rr * rr)
+    inside = inside.reshape(n, n, n)
+    org = np.asarray(center, dtype=np.float64) - n * cell / 2
+    v, t = _grid_kuhn_mesh(inside, cell, org)
+    return v + rng.uniform(-0.02 * cell, 0.02 * cell, size=v.shape), t  # no exactly parallel edges
+
+
+def spiky_balls(seed: int = 0, cell: float = 0.0039, precision: int = 1, n_steps: int = 60) -> Scene:
+    """Five spiky balls (radius 0.1 m, 64 spikes of 0.02-0.05 m) in a
+    0.7 x 0.7 m open box, four on the floor in a 2 x 2 grid and one on top,
+    compressed by a plate that starts 0.02 m above the top ball and moves
+    down at 0.5 m/s to 30 % of its initial height, then back up at 0.5 m/s;
+    E = 5e4 Pa, nu = 0.45, rho = 1000 kg/m^3, h = 1/60 s.  With the default
+    cell of 3.9 mm each ball has about 4.6e5 tets; vertices are jittered by
+    up to 2 % of a cell (rest shape too)."""
+    rng = np.random.default_rng(seed)
+    ext = 0.1 + 0.05
+    b = _Builder()
+    gap = 0.004
+    centres = [(sx * (ext + gap), sy * (ext + gap), ext + gap) for sx in (-1, 1) for sy in (-1, 1)]
+    centres.append((0.0, 0.0, ext + gap + 2 * ext + gap))
+    for c in centres:
+        v, t = spiky_ball(rng, c, cell=cell)
+        b.add_solid(v, t, 0)
+    half = 2 * (ext + gap) + 0.02
+    bv, bt = open_box(half, 0.9)
+    b.add_obstacle(bv, bt)
+    z0 = centres[-1][2] + ext + 0.02
+    pv, pt = ground_quad(half - 0.005, z=z0)
+    b.add_obstacle(pv, pt[:, [0, 2, 1]])
+    s = b.build(f"spiky_balls_seed{seed}", [[5e4, 0.45, 1000.0]], Params(dt=1.0 / 60.0, precision=precision),
+                n_steps, {"seed": seed, "cell": cell, "plate_speed": 0.5, "plate_z0": z0,
+                          "plate_z_min": 0.3 * z0})
+    s.meta["plate_vertices"] = np.arange(s.nv - 4, s.nv)
+    return s
+
+
+def plate_schedule_z(scene: Scene, step: int) -> float:
+    """plate height at the end of step `step` (0-based) for spiky_balls:
+    down at plate_speed to plate_z_min, then back up at the same speed"""
+    z0, zmin, v, h = scene.meta["plate_z0"], scene.meta["plate_z_min"], scene.meta["plate_speed"], scene.params.dt
+    t = (step + 1) * h
+    t_down = (z0 - zmin) / v
+    return z0 - v * t if t <= t_down else min(z0, zmin + v * (t - t_down))
+
+
+def plate_targets_schedule(scene: Scene, step: int) -> np.ndarray:
+    """Prescribed obstacle positions at the end of step `step` for
+    spiky_balls (the plate follows plate_schedule_z)"""
+    x = scene.x0.copy()
+    ids = scene.meta["plate_vertices"]
+    x[ids, 2] = plate_schedule_z(scene, step)
+    return x[scene.dirichlet == 1]
+
+
 CONFIGS = {
     "two_cubes": two_cubes,
     "eight_cubes": eight_cubes,
