@@ -245,6 +245,50 @@ def _progress(msg):
     sys.stderr.flush()
 
 
+def run_large(args, torch, B, scenes, peak, stream):
+    """The large contact-rich compression scene (five spiky balls, about
+    2.3M tets, moving plate), first `--large-steps` steps from rest, each
+    step timed with CUDA events; per-kernel timers on for the PCG roofline
+    (the matrix no longer fits in shared memory: HBM streaming)."""
+    s = scenes.spiky_balls(precision=1)
+    sim = B.Sim(s, stream=stream.cuda_stream)
+    B.bf_enable_timers(sim.h, True)
+    ms, stats = [], []
+    for i in range(args.large_steps):
+        B.bf_set_obstacle_targets(sim.h, scenes.plate_targets_schedule(s, i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st = sim.step(1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        stats.append(st[0])
+    timers = B.bf_get_timers(sim.h)
+    cfg = B.bf_get_pcg_config(sim.h)
+    info = sim.info()
+    sim.close()
+    n_pcg, ms_pcg = timers.get("pcg_persistent", (0, 0.0))
+    cg = sum(x["cg_iters"] for x in stats)
+    nc = statistics.mean(x["n_contacts"] for x in stats)
+    per_it = pcg_iteration_bytes(info["nnzb"], s.nv, nc, 4)
+    achieved = per_it * cg / (ms_pcg / 1e3) / 1e9 if ms_pcg > 0 else None
+    total = sum(ms)
+    srt = sorted(ms)
+    return {"workload": f"spiky balls: 5 balls (radius 0.1 m, 64 spikes 0.02-0.05 m), {s.nt} tets, {s.nv} vertices, "
+                        "grid Kuhn mesher (3.9 mm cells), open 0.66 m box, plate moving down at 0.5 m/s; "
+                        "E = 5e4 Pa, nu = 0.45, h = 1/60 s, mixed precision; first steps from rest",
+            "steps": args.large_steps, "steps_per_s": args.large_steps / (total / 1e3), "unit": "steps/s",
+            "ms_per_step": total / args.large_steps, "p50_step_ms": srt[len(srt) // 2],
+            "p99_step_ms": srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))],
+            "mean_outer_iters": statistics.mean(x["outer_iters"] for x in stats),
+            "cg_iters_total": cg, "mean_contacts": nc, "max_contacts": max(x["n_contacts"] for x in stats),
+            "pcg_roofline": {"bound": "hbm", "kernel": "pcg_persistent (global-vector variant)" if cfg["resident"] == 2
+                             else "pcg_persistent", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak if achieved else None, "alg_bytes_per_iteration": per_it,
+                             "us_per_iteration": 1e3 * ms_pcg / max(cg, 1), "share_of_steps": ms_pcg / total,
+                             "pcg_config": cfg}}
+
+
 def main():
     import faulthandler
     import signal
@@ -263,6 +307,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--large-steps", type=int, default=20,
+                    help="steps of the 2.3M-tet spiky-ball compression scene (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -430,6 +476,11 @@ def main():
         _progress(f"served: {served['steps_per_s']:.1f} steps/s")
         served["steps_per_s"] = allsum(ws, served["steps"]) / allmax(ws, served["seconds"])
 
+    large = None
+    if args.large_steps > 0:
+        large = run_large(args, torch, B, scenes, peak, stream)
+        _progress(f"large: {large['steps_per_s']:.3f} steps/s")
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         v, n, el = oracle_sample(args.cpu_seconds, seed)
@@ -459,6 +510,7 @@ def main():
                     plain, workload="the same scenes in FP64, one scene at a time on one stream", unit="steps/s"),
                 "batched_vs_plain_fp64": (batched["steps_per_s"] / plain["steps_per_s"]) if batched and plain
                 else None,
+                "large": large,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "

@@ -1,8 +1,10 @@
 """Stand-alone block-Jacobi PCG workload: the Newton system of the eight-cube
-scene (8 cubes x 16^3 cells) assembled at a contact state, solved with
-bf_pcg in the library's default (persistent) mode.
+scene (8 cubes x 16^3 cells) or of the spiky-ball compression scene (about
+2.3M tets) assembled at a contact state, solved with bf_pcg in the
+library's default (persistent) mode.
 
-    python -m paper_2512_12151_b300.pcg_case [--precision 1] [--steps 14] [--solves 2]
+    python -m paper_2512_12151_b300.pcg_case [--scene eight_cubes|spiky_balls]
+        [--precision 1] [--steps 14] [--solves 2] [--timers]
 
 The scene is first advanced `--steps` time steps with the per-phase PCG (so
 that no persistent-PCG launch happens before the timed solves; profilers can
@@ -23,6 +25,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--scene", default="eight_cubes", choices=["eight_cubes", "spiky_balls"])
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--steps", type=int, default=14)
     ap.add_argument("--solves", type=int, default=2)
@@ -34,10 +37,16 @@ def main(argv=None):
     from . import binding as B
     from . import scenes
 
-    s = scenes.eight_cubes(args.seed, precision=args.precision)
+    if args.scene == "eight_cubes":
+        s = scenes.eight_cubes(args.seed, precision=args.precision)
+    else:
+        s = scenes.spiky_balls(args.seed, precision=args.precision)
     sim = B.Sim(s)
     B.bf_set_pcg_mode(sim.h, 0)
-    sim.step(args.steps)
+    for i in range(args.steps):
+        if args.scene == "spiky_balls":
+            B.bf_set_obstacle_targets(sim.h, scenes.plate_targets_schedule(s, i))
+        sim.step(1)
     x, _ = sim.state()
     keys, _, _ = B.bf_get_active_set(sim.h)
     xd = torch.tensor(np.ascontiguousarray(x), device="cuda", dtype=torch.float64)
@@ -64,7 +73,7 @@ def main(argv=None):
     if args.timers:
         phases = {k[len("pcg_phase_"):]: round(1e3 * v[1] / v[0], 3)
                   for k, v in B.bf_get_timers(sim.h).items() if k.startswith("pcg_phase_") and v[0]}
-    print(json.dumps({"workload": "eight_cubes 16^3 Newton system after %d steps" % args.steps,
+    print(json.dumps({"workload": "%s Newton system after %d steps" % (s.name, args.steps),
                       "precision": "mixed" if args.precision else "fp64", "nv": s.nv, "nnzb": info["nnzb"],
                       "contacts": len(keys), "iterations": iters, "ms_per_solve": [round(v, 3) for v in ms],
                       "us_per_iteration": [round(1e3 * m / max(i, 1), 3) for m, i in zip(ms, iters)],
