@@ -272,6 +272,7 @@ def run_large(args, torch, B, scenes, peak, stream):
     nc = statistics.mean(x["n_contacts"] for x in stats)
     per_it = pcg_iteration_bytes(info["nnzb"], s.nv, nc, 4)
     achieved = per_it * cg / (ms_pcg / 1e3) / 1e9 if ms_pcg > 0 else None
+    tr = traffic_for("pcg_persistent_global") if cfg["resident"] == 2 else None  # DRAM bytes per iteration
     total = sum(ms)
     srt = sorted(ms)
     return {"workload": f"spiky balls: 5 balls (radius 0.1 m, 64 spikes 0.02-0.05 m), {s.nt} tets, {s.nv} vertices, "
@@ -285,6 +286,9 @@ def run_large(args, torch, B, scenes, peak, stream):
             "pcg_roofline": {"bound": "hbm", "kernel": "pcg_persistent (global-vector variant)" if cfg["resident"] == 2
                              else "pcg_persistent", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak if achieved else None, "alg_bytes_per_iteration": per_it,
+                             "traffic": round(tr * cg / n_pcg) if tr and n_pcg else None,
+                             "traffic_note": "DRAM bytes per launch: per-iteration bytes of the committed ncu capture "
+                                             "of this kernel source times the iterations per launch",
                              "us_per_iteration": 1e3 * ms_pcg / max(cg, 1), "share_of_steps": ms_pcg / total,
                              "pcg_config": cfg}}
 

@@ -261,14 +261,14 @@ __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, un
 // row in that order; ent(t, row, j, a) loads the 9 values of the row's j-th
 // block and returns the neighbour's window offset; getu(v_rel, out) loads u
 // there.  Every row is written, so s_q needs no clearing.
-template <class CT, class GetU, class Ent>
+template <int UNROLL, class CT, class GetU, class Ent>
 __device__ __forceinline__ void row_sums(int nr, const int *rinfo, GetU getu, Ent ent, CT *s_q, int ldq)
 {
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
         const int info = rinfo[t];
         const int row = info >> 8, len = info & 255;
         CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
-#pragma unroll 2
+#pragma unroll UNROLL
         for (int j = 0; j < len; ++j) {
             CT a[9], u[3];
             getu(ent(t, row, j, a), u);
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             __syncthreads();
             if (timer) tS += globaltimer() - t0;
             auto getp = [&](int vr, CT *o) { load3v(s_p4 + 4 * vr, o); };
-            row_sums<CT>(nr, s_rinfo, getp, ent, s_q, ld);
+            row_sums<2, CT>(nr, s_rinfo, getp, ent, s_q, ld);
             if (timer) tR += globaltimer() - t0;
             // this CTA's contact pairs: y += mu gamma g (g . p) into qc
             CT cdot = CT(0);
@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             const double alpha = ctl.alpha;
             const RT al = mixed ? (RT)ctl.al : (RT)alpha;
             Acc acc[2] = {};
+#pragma unroll 2
             for (int i = threadIdx.x; i < nr; i += blockDim.x) {
                 const int a = r0 + i;
                 VT qg[3];
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 for (int k = 0; k < 9; ++k) a[k] = (double)tv[k];
                 return v;
             };
-            row_sums<double>(nr, s_rinfo, getx, ent64, s_hx, ld);
+            row_sums<2, double>(nr, s_rinfo, getx, ent64, s_hx, ld);
             for (int k = threadIdx.x; k < nco; k += blockDim.x) {
                 const int i = c + k * (int)gridDim.x;
                 const int4 v = A.cv[i];
