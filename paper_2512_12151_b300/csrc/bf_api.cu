@@ -100,7 +100,7 @@ static const char *kTimerNames[T_N] = {"elastic_grad_hess", "spmv_bsr_contact", 
                                        "contact_assemble", "energy", "ccd_narrow_accd", "lbvh_build",
                                        "pcg_persistent", "pcg_phase_spmv", "pcg_phase_reduce1",
                                        "pcg_phase_update", "pcg_phase_reduce2", "pcg_phase_stage_cum",
-                                       "pcg_phase_rows_cum", "pcg_phase_contact_cum"};
+                                       "pcg_phase_rows_cum", "pcg_phase_contact_cum", "ccd_broad_query"};
 
 ScopedTimer::ScopedTimer(Scene &s, int tid) : S(&s), id(tid)
 {

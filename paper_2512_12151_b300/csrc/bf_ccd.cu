@@ -775,6 +775,7 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
     cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
     for (int attempt = 0; attempt < 3; ++attempt) {
         cudaMemsetAsync(S.dflag + F_NCAND_PT, 0, 2 * sizeof(int), S.stream);
+        ScopedTimer tq(S, T_CCD_QUERY);
         if (S.nsv && S.nst)
             {
                 k_query<PT><<<cdiv(S.nsv, kQueryThreads), kQueryThreads, 0, S.stream>>>(

@@ -43,7 +43,7 @@ enum { ERR_NONFINITE = 1, ERR_CAND_OVERFLOW = 2, ERR_HIT_OVERFLOW = 4, ERR_PQ = 
 
 enum TimerId { T_ELASTIC = 0, T_SPMV, T_PCG_UPDATE, T_PCG_DIR, T_CONTACT, T_ENERGY, T_CCD_NARROW,
                T_BVH, T_PCG_PERSISTENT, T_PCG_PH_SPMV, T_PCG_PH_RED1, T_PCG_PH_UPD, T_PCG_PH_RED2,
-               T_PCG_PH_STAGE, T_PCG_PH_ROWS, T_PCG_PH_CONTACT, T_N };
+               T_PCG_PH_STAGE, T_PCG_PH_ROWS, T_PCG_PH_CONTACT, T_CCD_QUERY, T_N };
 
 struct LBVH {
     int n = 0, cap = 0, npad = 0;  // leaves, capacity, leaves padded to a power of two
