@@ -440,3 +440,37 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
             assert np.linalg.norm(sols[k] - sols[3]) <= 1e-4 * np.linalg.norm(sols[3])
     finally:
         B.bf_scene_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def multi_cta_state():
+    """a 16k-tet scene (two stacked cubes, 3,460 vertices: the persistent
+    PCG splits it over several CTAs) advanced by the oracle into contact"""
+    s = scenes.batch_scene(11, 1.8e4, 2e4, precision=0)
+    o = O.Oracle(s)
+    o.step(5)
+    x, v = o.get_state()
+    keys, lam, gam = o.active_get()
+    assert len(keys) > 100
+    return s, x, v, keys, lam, gam
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision):
+    """One time step from an oracle contact state on a system the persistent
+    PCG spreads over several CTAs: positions within 1e-6 (FP64) or 1e-4
+    (mixed) x the bounding-box diagonal, same active set in FP64."""
+    s, x, v, keys, lam, gam = multi_cta_state
+    sim, o = make_pair(s, x, v, keys, lam, gam, precision)
+    o.step(1)
+    _, st = sim.step(1)
+    assert B.bf_get_pcg_config(sim.h)["ctas"] > 1
+    xo, vo = o.get_state()
+    xg, vg = sim.state()
+    tol = (1e-6 if precision == 0 else 1e-4) * s.bbox_diag()
+    assert np.abs(xg - xo).max() <= tol, np.abs(xg - xo).max()
+    if precision == 0:
+        ko, _, _ = o.active_get()
+        kg, _, _ = B.bf_get_active_set(sim.h)
+        assert keyset(ko) == keyset(kg)
+    sim.close()
