@@ -272,8 +272,10 @@ int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
 
 /* Configuration of the persistent PCG chosen at the scene's first solve
  * (host int32[8]): mode, CTAs, threads per CTA, shared memory bytes per
- * CTA, matrix resident in shared memory (0/1), max rows, max blocks and
- * max window vertices per CTA (zeros before the first solve). */
+ * CTA, variant (0: blocks streamed through the BSR map, vectors in shared
+ * memory; 1: blocks resident in shared memory; 2: blocks streamed from a
+ * jagged global copy, per-row vectors in global memory), max rows, max
+ * blocks and max window vertices per CTA (zeros before the first solve). */
 int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
 
 /* Number of this library's own kernel launches issued for the scene since

@@ -222,8 +222,9 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s: far bey
 // arrives (that slot was last read before the previous barrier and is next
 // written after this one).  Barrier: one arrival counter whose top bit
 // flips when every CTA has arrived (CTA 0 adds 0x80000000 - (gridDim.x - 1),
-// the others 1), with a release on the arrival and acquire loads while
-// spinning (bounded: ERR_BARRIER and false on timeout).
+// the others 1, so the sum of one barrier's arrivals is 0x80000000), with a
+// release on the arrival and acquire loads while spinning (bounded:
+// ERR_BARRIER and false on timeout).
 template <int K>
 __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, unsigned n, unsigned *bar, int *dflag,
                                            double (&tot)[K])
@@ -234,12 +235,15 @@ __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, un
     if (blockIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc[8 * next + k] = 0.0;
+    // the top bit of the counter is (n + 1) & 1 once barrier n is complete
+    // (it flips at the last arrival of every barrier), so the arrival needs
+    // no returned value and the polling starts at once
     const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    unsigned old;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(add) : "memory");
+    const unsigned want = ((n + 1u) & 1u) << 31;
     unsigned spins = 0;
     unsigned long long t_start = 0;
-    while (((old ^ ld_acquire_gpu(bar)) & 0x80000000u) == 0u) {
+    while ((ld_acquire_gpu(bar) & 0x80000000u) != want) {
         if ((++spins & 255u) == 0u) {  // give up after kBarrierTimeoutNs
             const unsigned long long t = globaltimer();
             if (t_start == 0) t_start = t;
