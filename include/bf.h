@@ -106,6 +106,7 @@ typedef struct {
  * no elastic energy), Dm^-1, the surface (tet faces used once, plus the
  * obstacle triangles), the block-sparse pattern, and sizes work buffers.
  * stream: a cudaStream_t (NULL = default stream) used by all later calls.
+ * Limits: n_verts < 2^21, n_tets < 2^29.
  * Errors: BF_E_ARG (bad sizes, ids out of range, degenerate tets), BF_E_OOM. */
 int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_allocator *alloc,
                     void *stream, bf_scene **out);

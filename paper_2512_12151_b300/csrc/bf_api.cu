@@ -368,6 +368,37 @@ static int step_once(Scene &S, bf_step_stats *out)
 // ---------------------------------------------------------------------------
 // scene creation
 // ---------------------------------------------------------------------------
+// LSD radix sort of non-negative 64-bit keys (16-bit digits; a digit on
+// which every key agrees is skipped), carrying a payload when one is given.
+// Scene creation sorts a few million keys, where this is several times
+// faster than a comparison sort.
+template <class K, class V>
+static void radix_sort(std::vector<K> &key, std::vector<V> *val)
+{
+    const size_t n = key.size();
+    std::vector<K> k2(n);
+    std::vector<V> v2(val ? n : 0);
+    std::vector<size_t> cnt(1 << 16);
+    for (int shift = 0; shift < 64; shift += 16) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (size_t i = 0; i < n; ++i) cnt[((unsigned long long)key[i] >> shift) & 0xffff]++;
+        if (n == 0 || cnt[((unsigned long long)key[0] >> shift) & 0xffff] == n) continue;
+        size_t sum = 0;
+        for (auto &c : cnt) {
+            const size_t t = c;
+            c = sum;
+            sum += t;
+        }
+        for (size_t i = 0; i < n; ++i) {
+            const size_t d = cnt[((unsigned long long)key[i] >> shift) & 0xffff]++;
+            k2[d] = key[i];
+            if (val) v2[d] = (*val)[i];
+        }
+        key.swap(k2);
+        if (val) val->swap(v2);
+    }
+}
+
 static long long tri_key_sorted(int a, int b, int c)
 {
     int t[3] = {a, b, c};
@@ -380,7 +411,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     const int nv = m->n_verts, nt = m->n_tets, nm = m->n_mats, nx = m->n_obst_tris;
     if (nv <= 0 || nt < 0 || nx < 0 || (nt > 0 && nm <= 0) || !m->rest_pos || !m->init_pos) return BF_E_ARG;
     if ((nt > 0 && (!m->tets || !m->tet_mat || !m->mats)) || (nx > 0 && !m->obst_tris)) return BF_E_ARG;
-    if (nv >= (1 << 30) || nt >= (1 << 30)) return BF_E_ARG;
+    if (nv >= (1 << 21) || nt >= (1 << 29)) return BF_E_ARG;  // triangle keys pack 3 vertex ids of 21 bits
     if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
         prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
         prm->s_ccd >= 1)
@@ -435,18 +466,20 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     // surface: tet faces used exactly once (outward order (1,2,3), (0,3,2),
     // (0,1,3), (0,2,1) of a positively oriented tet), then obstacle triangles
     static const int fl[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
-    std::vector<std::pair<long long, int>> faces(4 * (size_t)nt);
+    std::vector<long long> fkey(4 * (size_t)nt);
+    std::vector<int> fidx(4 * (size_t)nt);
     for (int e = 0; e < nt; ++e)
         for (int f = 0; f < 4; ++f) {
             const int *t = m->tets + 4 * e;
-            faces[4 * e + f] = {tri_key_sorted(t[fl[f][0]], t[fl[f][1]], t[fl[f][2]]), 4 * e + f};
+            fkey[4 * e + f] = tri_key_sorted(t[fl[f][0]], t[fl[f][1]], t[fl[f][2]]);
+            fidx[4 * e + f] = 4 * e + f;
         }
-    std::sort(faces.begin(), faces.end());
-    for (size_t i = 0; i < faces.size();) {
+    radix_sort(fkey, &fidx);  // stable: equal keys keep their face order
+    for (size_t i = 0; i < fkey.size();) {
         size_t j = i;
-        while (j < faces.size() && faces[j].first == faces[i].first) ++j;
+        while (j < fkey.size() && fkey[j] == fkey[i]) ++j;
         if (j - i == 1) {
-            const int e = faces[i].second / 4, f = faces[i].second % 4;
+            const int e = fidx[i] / 4, f = fidx[i] % 4;
             for (int k = 0; k < 3; ++k) S.h_st.push_back(m->tets[4 * e + fl[f][k]]);
         }
         i = j;
@@ -464,7 +497,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
             const int a = S.h_st[3 * i + k], b = S.h_st[3 * i + (k + 1) % 3];
             ek.push_back(((long long)std::min(a, b) << 32) | (long long)std::max(a, b));
         }
-    std::sort(ek.begin(), ek.end());
+    radix_sort(ek, (std::vector<int> *)nullptr);
     ek.erase(std::unique(ek.begin(), ek.end()), ek.end());
     for (long long k : ek) {
         S.h_se.push_back((int)(k >> 32));
@@ -479,13 +512,15 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         S.nsv = (int)S.h_sv.size();
     }
     {
-        std::vector<std::pair<long long, int>> tk(S.nst);
-        for (int i = 0; i < S.nst; ++i) tk[i] = {tri_key_sorted(S.h_st[3 * i], S.h_st[3 * i + 1], S.h_st[3 * i + 2]), i};
-        std::sort(tk.begin(), tk.end());
-        for (auto &p : tk) {
-            S.h_tri_key_sorted.push_back(p.first);
-            S.h_tri_key_idx.push_back(p.second);
+        std::vector<long long> tk(S.nst);
+        std::vector<int> ti(S.nst);
+        for (int i = 0; i < S.nst; ++i) {
+            tk[i] = tri_key_sorted(S.h_st[3 * i], S.h_st[3 * i + 1], S.h_st[3 * i + 2]);
+            ti[i] = i;
         }
+        radix_sort(tk, &ti);
+        S.h_tri_key_sorted = tk;
+        S.h_tri_key_idx = ti;
     }
     // upper block pattern: diagonal of every vertex + (a, b), a < b, sharing a tet
     std::vector<long long> pk;
@@ -499,7 +534,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
                 pk.push_back(((long long)a << 32) | b);
             }
     }
-    std::sort(pk.begin(), pk.end());
+    radix_sort(pk, (std::vector<int> *)nullptr);
     pk.erase(std::unique(pk.begin(), pk.end()), pk.end());
     S.nnzb = (int)pk.size();
     S.h_rowptr.assign(nv + 1, 0);
@@ -545,9 +580,10 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
             fnbr[fill[c]] = r;
             fblk[fill[c]++] = k | (int)0x80000000u;
         }
+        std::vector<std::pair<int, int>> tmp;
         for (int v = 0; v < nv; ++v) {
             const int b = S.h_frowptr[v], e = S.h_frowptr[v + 1];
-            std::vector<std::pair<int, int>> tmp;
+            tmp.clear();
             for (int i = b; i < e; ++i) tmp.push_back({fnbr[i], fblk[i]});
             std::sort(tmp.begin(), tmp.end());
             for (int i = b; i < e; ++i) {

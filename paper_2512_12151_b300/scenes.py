@@ -14,6 +14,7 @@ nu = 0.4, rho = 1000 kg/m^3, h = 0.01 s, contact radius delta = 1e-3 m.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -86,6 +87,12 @@ class Scene:
 
 def cube_mesh(cells: int, side: float):
     """Regular (cells+1)^3 grid on [0, side]^3 split into 6*cells^3 tets."""
+    v, t = _cube_mesh_cached(int(cells), float(side))
+    return v.copy(), t.copy()
+
+
+@functools.lru_cache(maxsize=64)
+def _cube_mesh_cached(cells: int, side: float):
     n = cells + 1
     g = np.arange(n, dtype=np.float64) * (side / cells)
     zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")
