@@ -226,7 +226,7 @@ def run_reference(args):
         return 0
     budget = float(os.environ.get("BF_REF_SECONDS", "90"))
     value, n, el = oracle_sample(budget)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws,
             "steps": n, "warmup": 0, "ms_per_step": 1000.0 * el / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("mixed precision (FP32 Hessian/SpMV/preconditioner, "

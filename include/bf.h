@@ -113,6 +113,19 @@ int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_
 int bf_scene_destroy(bf_scene *scene);
 int bf_set_stream(bf_scene *scene, void *stream);
 
+/* Checkpoint of the evolving state (no counterpart in the paper; lets a
+ * server evict a scene and re-admit it later): positions, velocities, the
+ * active set with multipliers and decay factors, mu and delta, and the
+ * obstacle targets when set, in a self-describing host buffer (8-byte
+ * aligned).  bf_save with buf NULL only sets *used to the bytes needed;
+ * with cap too small it returns BF_E_CAPACITY.  bf_load
+ * restores a checkpoint into a scene created from the same mesh (same
+ * vertex and prescribed-vertex counts, else BF_E_ARG, as for a buffer that
+ * is not a checkpoint or is cut short; pair keys that name no primitive of
+ * the mesh give the error bf_set_active_set gives). */
+int bf_save(bf_scene *scene, void *buf, size_t cap, size_t *used);
+int bf_load(bf_scene *scene, const void *buf, size_t size);
+
 /* Device bytes the scene holds (all its allocations); *bytes host. */
 int bf_scene_bytes(bf_scene *scene, int64_t *bytes);
 

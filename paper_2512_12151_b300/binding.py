@@ -108,6 +108,8 @@ def lib():
         "bf_get_pcg_config": [_P, _P],
         "bf_get_timers": [_P, C.c_int32, _P, _P, _P],
         "bf_scene_bytes": [_P, C.POINTER(C.c_int64)],
+        "bf_save": [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)],
+        "bf_load": [_P, _P, C.c_size_t],
         "bf_batch_create": [C.c_int32, C.c_int64, C.POINTER(_P)],
         "bf_batch_destroy": [_P],
         "bf_batch_admit": [_P, _P, C.c_int32, C.POINTER(C.c_int64)],
@@ -386,6 +388,20 @@ def bf_get_timers(h):
     names = (C.c_char_p * cap)()
     n = lib().bf_get_timers(h, cap, _np_ptr(launches), _np_ptr(ms), names)
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def bf_save(h):
+    """checkpoint of the scene's evolving state as bytes"""
+    n = C.c_size_t()
+    _check("bf_save", lib().bf_save(h, None, 0, C.byref(n)))
+    buf = (C.c_ubyte * n.value)()
+    _check("bf_save", lib().bf_save(h, buf, n.value, C.byref(n)))
+    return bytes(buf)
+
+
+def bf_load(h, data):
+    buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+    _check("bf_load", lib().bf_load(h, buf, len(data)))
 
 
 def bf_scene_bytes(h):

@@ -950,6 +950,77 @@ int bf_get_mu(bf_scene *scene, double *mu, double *delta)
     return BF_OK;
 }
 
+// checkpoint layout: header (8 int64: magic, version, n_verts, n_pairs,
+// whether obstacle targets are set, n_prescribed, 2 reserved), mu, delta,
+// x (3 n_verts), v (3 n_verts), the pairs' lambdas, their gammas, the
+// obstacle targets (3 n_prescribed) when set, then the pairs' 5-int keys
+// (every double stays 8-byte aligned)
+static const int64_t kCheckpointMagic = 0x4b43435f4642LL;  // "BF_CCK"
+
+static size_t checkpoint_bytes(int nv, int nc, int ntarget)
+{
+    return 8 * sizeof(int64_t) + 2 * sizeof(double) + 6 * (size_t)nv * sizeof(double) +
+           (size_t)nc * (5 * sizeof(int32_t) + 2 * sizeof(double)) + 3 * (size_t)ntarget * sizeof(double);
+}
+
+int bf_save(bf_scene *scene, void *buf, size_t cap, size_t *used)
+{
+    SCENE_OR_ARG(scene);
+    if (!used) return BF_E_ARG;
+    const int ntarget = S.has_targets ? S.ndir : 0;
+    const size_t need = checkpoint_bytes(S.nv, S.nc, ntarget);
+    *used = need;
+    if (!buf) return BF_OK;  // size query
+    if (cap < need) return BF_E_CAPACITY;
+    unsigned char *p = (unsigned char *)buf;
+    const int64_t hdr[8] = {kCheckpointMagic, 1, S.nv, S.nc, S.has_targets ? 1 : 0, S.ndir, 0, 0};
+    std::memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    double md[2] = {S.mu, S.delta};
+    std::memcpy(p, md, sizeof(md));
+    p += sizeof(md);
+    double *x = (double *)p, *v = x + 3 * (size_t)S.nv;
+    int st = bf_get_state(scene, x, v);
+    if (st) return st;
+    p += 6 * (size_t)S.nv * sizeof(double);
+    double *lam = (double *)p, *gam = lam + S.nc, *tgt = gam + S.nc;
+    int32_t *keys = (int32_t *)(tgt + 3 * (size_t)ntarget);
+    int32_t n = 0;
+    st = bf_get_active_set(scene, S.nc, &n, keys, lam, gam);
+    if (st || !ntarget) return st;
+    cudaMemcpyAsync(tgt, S.targets, 3 * (size_t)ntarget * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+int bf_load(bf_scene *scene, const void *buf, size_t size)
+{
+    SCENE_OR_ARG(scene);
+    if (!buf || size < 8 * sizeof(int64_t)) return BF_E_ARG;
+    const unsigned char *p = (const unsigned char *)buf;
+    int64_t hdr[8];
+    std::memcpy(hdr, p, sizeof(hdr));
+    if (hdr[0] != kCheckpointMagic || hdr[1] != 1 || hdr[2] != S.nv || hdr[3] < 0 || hdr[3] > (1 << 30) ||
+        (hdr[4] != 0 && hdr[4] != 1) || hdr[5] != S.ndir)
+        return BF_E_ARG;
+    const int nc = (int)hdr[3], ntarget = hdr[4] ? S.ndir : 0;
+    if (size < checkpoint_bytes(S.nv, nc, ntarget)) return BF_E_ARG;
+    p += sizeof(hdr);
+    double md[2];
+    std::memcpy(md, p, sizeof(md));
+    p += sizeof(md);
+    const double *x = (const double *)p, *v = x + 3 * (size_t)S.nv;
+    int st = bf_set_state(scene, x, v);
+    if (st) return st;
+    p += 6 * (size_t)S.nv * sizeof(double);
+    const double *lam = (const double *)p, *gam = lam + nc, *tgt = gam + nc;
+    const int32_t *keys = (const int32_t *)(tgt + 3 * (size_t)ntarget);
+    st = bf_set_active_set(scene, nc, keys, lam, gam);
+    if (st) return st;
+    st = bf_set_obstacle_targets(scene, ntarget ? tgt : nullptr);
+    if (st || !(md[0] > 0.0)) return st;  // mu is 0 until a scene's first step
+    return bf_set_mu(scene, md[0], md[1]);
+}
+
 int bf_set_mu(bf_scene *scene, double mu, double delta)
 {
     SCENE_OR_ARG(scene);
