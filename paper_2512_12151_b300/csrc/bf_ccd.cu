@@ -498,32 +498,45 @@ __device__ __forceinline__ bool box_overlap_f(const float *ql, const float *qh, 
 }
 
 constexpr int kQueryThreads = 128;
-constexpr int kQueryStack = 64;
+constexpr int kQueryStack = 32;   // a depth-first stack never holds more than the tree depth + 1 nodes
+constexpr int kQuerySplitLog = 3;  // each query is traversed as 8 independent subtree walks
 
-// Queries: surface vertices against the triangle tree (type PT), or each
-// edge leaf against the edge leaves after it in the tree's leaf order (type
-// EE; subtrees whose last leaf is not after the query leaf are skipped, so
-// every edge pair is met once).  Nodes are culled with their FP32
-// outward-rounded boxes (both children of a node from one 64-byte fetch); a
-// leaf is accepted only by the exact FP64 closed-box test, so the candidates
-// are exactly the pairs whose swept boxes overlap.  The traversal stack
-// lives in shared memory.
+struct QueryTree {
+    int nq;              // queries
+    const int *qids;     // PT: surface vertex per query; EE: unused (queries are the tree's own leaves)
+    int n, N;            // leaves, padded leaf count (power of two)
+    const float4 *node;  // FP32 boxes of nodes 2.. (node c at [2c], [2c + 1])
+    const int *prim;     // primitive per leaf position
+    const double *lo, *hi;  // exact FP64 leaf boxes, leaf order
+    int2 *cand;
+    int *count;
+};
+
+// One sub-walk: query q against the subtree rooted at node h0 (all nodes of
+// the tree's level ls are roots of the walks; ls = 0 is the root itself).
+// Nodes are culled with their FP32 outward-rounded boxes (both children of
+// a node from one 64-byte fetch); a leaf is accepted only by the exact FP64
+// closed-box test, so the candidates are exactly the pairs whose swept
+// boxes overlap.  Type PT queries a surface vertex against the triangle
+// tree; type EE queries an edge leaf against the edge leaves after it in
+// leaf order (subtrees whose last leaf is not after the query leaf are
+// skipped, so every edge pair is met once).  Candidate slots are reserved
+// with one atomic per group of converged lanes.
 template <int TYPE>
-__global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__restrict__ qids,
-                                                         const double *__restrict__ x0, const double *__restrict__ x1,
-                                                         int n, int N, const float4 *__restrict__ node,
-                                                         const int *__restrict__ prim, const double *__restrict__ lo,
-                                                         const double *__restrict__ hi, const int *__restrict__ st,
-                                                         const int *__restrict__ se, const uint8_t *__restrict__ dir,
-                                                         int2 *__restrict__ cand, int cap, int *count, int *dflag)
+__device__ __forceinline__ void query_walk(const QueryTree &T, int q, int h0, int ls, const double *__restrict__ x0,
+                                           const double *__restrict__ x1, const int *__restrict__ st,
+                                           const int *__restrict__ se, const uint8_t *__restrict__ dir, int cap,
+                                           int *dflag, int *stk)
 {
-    __shared__ int stack[kQueryStack * kQueryThreads];
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq || n == 0) return;
+    const int N = T.N, L = 31 - __clz(N);  // leaves are nodes [N, 2N)
+    if (TYPE == EE) {  // the walk's last leaf must come after q
+        const int span = 1 << (L - ls);
+        if ((h0 - (1 << ls) + 1) * span - 1 <= q) return;
+    }
     double ql[3], qh[3];
     int qa, qv0, qv1 = -1;
     if (TYPE == PT) {
-        qa = qids[q];
+        qa = T.qids[q];
         qv0 = qa;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -531,14 +544,14 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
             ql[c] = fmin(a, b);
             qh[c] = fmax(a, b);
         }
-    } else {  // q is a leaf position of the edge tree
-        qa = prim[q];
+    } else {
+        qa = T.prim[q];
         qv0 = se[2 * qa];
         qv1 = se[2 * qa + 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ql[c] = lo[3 * (size_t)q + c];
-            qh[c] = hi[3 * (size_t)q + c];
+            ql[c] = T.lo[3 * (size_t)q + c];
+            qh[c] = T.hi[3 * (size_t)q + c];
         }
     }
     float fl[3], fh[3];
@@ -548,13 +561,12 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
         fh[c] = __double2float_ru(qh[c]);
     }
     const bool qdir = TYPE == PT ? dir[qv0] != 0 : (dir[qv0] && dir[qv1]);
-    // leaf position k: exact test, pair filters, emit
     auto leaf = [&](int k) {
-        if (k >= n || (TYPE == EE && k <= q)) return;
-        const double *l2 = lo + 3 * (size_t)k, *h2 = hi + 3 * (size_t)k;
+        if (k >= T.n || (TYPE == EE && k <= q)) return;
+        const double *l2 = T.lo + 3 * (size_t)k, *h2 = T.hi + 3 * (size_t)k;
         if (ql[0] > h2[0] || l2[0] > qh[0] || ql[1] > h2[1] || l2[1] > qh[1] || ql[2] > h2[2] || l2[2] > qh[2])
             return;
-        const int b = prim[k];
+        const int b = T.prim[k];
         bool ok;
         if (TYPE == PT) {
             const int t0 = st[3 * b], t1 = st[3 * b + 1], t2 = st[3 * b + 2];
@@ -564,17 +576,24 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
             ok = e0 != qv0 && e0 != qv1 && e1 != qv0 && e1 != qv1 && !(qdir && dir[e0] && dir[e1]);
         }
         if (ok) {
-            const int idx = atomicAdd(count, 1);
-            if (idx < cap) cand[idx] = TYPE == PT ? make_int2(qa, b) : make_int2(min(qa, b), max(qa, b));
+            const unsigned m = __activemask();
+            const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+            int base = 0;
+            if (lane == lead) base = atomicAdd(T.count, __popc(m));
+            base = __shfl_sync(m, base, lead);
+            const int idx = base + __popc(m & ((1u << lane) - 1));
+            if (idx < cap) T.cand[idx] = TYPE == PT ? make_int2(qa, b) : make_int2(min(qa, b), max(qa, b));
         }
     };
     if (N == 1) {
         leaf(0);
         return;
     }
-    const int L = 31 - __clz(N);  // leaves are nodes [N, 2N)
-    int *stk = stack + threadIdx.x;
-    stk[0] = 1;
+    if (ls > 0) {  // the walk's own root box
+        const float4 *p = T.node + 2 * (size_t)h0;
+        if (!box_overlap_f(fl, fh, __ldg(p), __ldg(p + 1))) return;
+    }
+    stk[0] = h0;
     int sp = 1;
     for (int visits = 0; sp > 0; ++visits) {
         if (visits > N + 64) {  // the tree has N - 1 internal nodes
@@ -583,8 +602,8 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
         }
         const int h = stk[--sp * kQueryThreads];
         const int lc = 32 - __clz(h);  // level of the children (root = level 0)
-        const float4 *p = node + 4 * (size_t)h;  // children 2h, 2h + 1: 4 consecutive float4
-        const float4 l0 = __ldg(p), h0 = __ldg(p + 1), l1 = __ldg(p + 2), h1 = __ldg(p + 3);
+        const float4 *p = T.node + 4 * (size_t)h;  // children 2h, 2h + 1: 4 consecutive float4
+        const float4 l0 = __ldg(p), h0b = __ldg(p + 1), l1 = __ldg(p + 2), h1 = __ldg(p + 3);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int cnode = 2 * h + k;
@@ -592,7 +611,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
                 const int span = 1 << (L - lc);
                 if ((cnode - (1 << lc) + 1) * span - 1 <= q) continue;
             }
-            if (!box_overlap_f(fl, fh, k ? l1 : l0, k ? h1 : h0)) continue;
+            if (!box_overlap_f(fl, fh, k ? l1 : l0, k ? h1 : h0b)) continue;
             if (lc == L) {
                 leaf(cnode - N);
             } else {
@@ -603,6 +622,41 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(int nq, const int *__re
                 stk[sp++ * kQueryThreads] = cnode;
             }
         }
+    }
+}
+
+// level whose nodes root the sub-walks: kQuerySplitLog, but above the leaves
+__host__ __device__ __forceinline__ int query_split_level(int N)
+{
+    int L = 0;
+    while ((1 << L) < N) ++L;
+    return L <= 1 ? 0 : (L - 1 < kQuerySplitLog ? L - 1 : kQuerySplitLog);
+}
+
+// warps of a query type: each warp takes 32 consecutive queries and one
+// sub-walk root, so the lanes of a warp walk the same subtree
+__host__ __device__ __forceinline__ int query_warps(int nq, int N)
+{
+    return nq > 0 && N > 0 ? ((nq + 31) / 32) << query_split_level(N) : 0;
+}
+
+// Both query types in one launch (the PT warps first, then the EE warps):
+// each alone is too small to fill the device.
+__global__ void __launch_bounds__(kQueryThreads) k_query(QueryTree pt, QueryTree ee, int wpt, int wee,
+                                                         const double *__restrict__ x0, const double *__restrict__ x1,
+                                                         const int *__restrict__ st, const int *__restrict__ se,
+                                                         const uint8_t *__restrict__ dir, int cap, int *dflag)
+{
+    __shared__ int stack[kQueryStack * kQueryThreads];
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    int *stk = stack + threadIdx.x;
+    if (w < wpt) {
+        const int ls = query_split_level(pt.N), j = w & ((1 << ls) - 1), q = (w >> ls) * 32 + lane;
+        if (q < pt.nq) query_walk<PT>(pt, q, (1 << ls) + j, ls, x0, x1, st, se, dir, cap, dflag, stk);
+    } else if ((w -= wpt) < wee) {
+        const int ls = query_split_level(ee.N), j = w & ((1 << ls) - 1), q = (w >> ls) * 32 + lane;
+        if (q < ee.nq) query_walk<EE>(ee, q, (1 << ls) + j, ls, x0, x1, st, se, dir, cap, dflag, stk);
     }
 }
 
@@ -776,19 +830,17 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
     for (int attempt = 0; attempt < 3; ++attempt) {
         cudaMemsetAsync(S.dflag + F_NCAND_PT, 0, 2 * sizeof(int), S.stream);
         ScopedTimer tq(S, T_CCD_QUERY);
-        if (S.nsv && S.nst)
-            {
-                k_query<PT><<<cdiv(S.nsv, kQueryThreads), kQueryThreads, 0, S.stream>>>(
-                    S.nsv, S.sv, x0, x1, S.bvh_tri.n, S.bvh_tri.npad, S.bvh_tri.node, S.bvh_tri.prim, S.bvh_tri.lo,
-                    S.bvh_tri.hi, S.st,
-                    S.se, S.dir, S.cand_pt, S.cand_cap, S.dflag + F_NCAND_PT, S.dflag); ++S.n_launch;
-            }
-        if (S.nse > 1)
-            {
-                k_query<EE><<<cdiv(S.nse, kQueryThreads), kQueryThreads, 0, S.stream>>>(
-                    S.nse, nullptr, x0, x1, S.bvh_edge.n, S.bvh_edge.npad, S.bvh_edge.node, S.bvh_edge.prim, S.bvh_edge.lo,
-                    S.bvh_edge.hi, S.st, S.se, S.dir, S.cand_ee, S.cand_cap, S.dflag + F_NCAND_EE, S.dflag); ++S.n_launch;
-            }
+        const QueryTree pt{S.nst ? S.nsv : 0, S.sv, S.bvh_tri.n, S.bvh_tri.npad, S.bvh_tri.node,
+                           S.bvh_tri.prim, S.bvh_tri.lo, S.bvh_tri.hi, S.cand_pt, S.dflag + F_NCAND_PT};
+        const QueryTree ee{S.nse > 1 ? S.nse : 0, nullptr, S.bvh_edge.n, S.bvh_edge.npad, S.bvh_edge.node,
+                           S.bvh_edge.prim, S.bvh_edge.lo, S.bvh_edge.hi, S.cand_ee, S.dflag + F_NCAND_EE};
+        const int wpt = query_warps(pt.nq, pt.N), wee = query_warps(ee.nq, ee.N);
+        if (wpt + wee > 0) {
+            const int wpb = kQueryThreads / 32;
+            k_query<<<cdiv(wpt + wee, wpb), kQueryThreads, 0, S.stream>>>(pt, ee, wpt, wee, x0, x1, S.st, S.se,
+                                                                        S.dir, S.cand_cap, S.dflag);
+            ++S.n_launch;
+        }
         st = sync_flags(S);
         if (st) return st;
         npt = S.h_flag[F_NCAND_PT];

@@ -111,6 +111,26 @@ def run_sequential(scene_list, n_steps=None):
     return out, handles
 
 
+def evict(h):
+    """Checkpoint of a scene (bf_save) whose device memory is then freed;
+    the scene must not be running in a batch."""
+    blob = B.bf_save(h)
+    B.bf_scene_destroy(h)
+    return blob
+
+
+def restore(scene, blob, params=None):
+    """(handle, keep-alive) of a scene re-created from its mesh and resumed
+    from a checkpoint made by evict"""
+    h, keep = create(scene, params)
+    try:
+        B.bf_load(h, blob)
+    except Exception:
+        B.bf_scene_destroy(h)
+        raise
+    return h, keep
+
+
 def destroy(handles):
     for h, _ in handles:
         B.bf_scene_destroy(h)

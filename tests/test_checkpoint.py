@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2512_12151_b300 import binding as B
-from paper_2512_12151_b300 import scenes
+from paper_2512_12151_b300 import scenes, serving
 
 pytestmark = pytest.mark.gpu
 
@@ -80,3 +80,30 @@ def test_refused_buffers(torch_cuda):
     assert np.array_equal(a.state()[0], x0)
     a.close()
     other.close()
+
+
+def test_evict_and_readmit_in_a_batch(torch_cuda):
+    s = scenes.batch_scene(7)
+    h, keep = serving.create(s)
+    B.bf_step(h, 6)
+    x_straight, _ = B.bf_get_state(h, s.nv)
+    B.bf_scene_destroy(h)
+    h, keep = serving.create(s)
+    b = B.bf_batch_create(2, 1 << 34)
+    try:
+        t = B.bf_batch_admit(b, h, 3)
+        assert B.bf_batch_wait(b, t, 600000)
+        assert B.bf_batch_result(b, t, 3)["status"] == 0
+        B.bf_batch_release(b, t)
+        blob = serving.evict(h)
+        assert B.bf_batch_info(b)["resident_bytes"] == 0
+        h, keep = serving.restore(s, blob)
+        t = B.bf_batch_admit(b, h, 3)
+        assert B.bf_batch_wait(b, t, 600000)
+        assert B.bf_batch_result(b, t, 3)["status"] == 0
+        B.bf_batch_release(b, t)
+    finally:
+        B.bf_batch_destroy(b)
+    x_resumed, _ = B.bf_get_state(h, s.nv)
+    B.bf_scene_destroy(h)
+    assert np.abs(x_straight - x_resumed).max() <= 1e-5 * s.bbox_diag()
