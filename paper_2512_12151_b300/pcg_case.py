@@ -4,13 +4,14 @@ scene (8 cubes x 16^3 cells) or of the spiky-ball compression scene (about
 library's default (persistent) mode.
 
     python -m paper_2512_12151_b300.pcg_case [--scene eight_cubes|spiky_balls]
-        [--precision 1] [--steps 14] [--solves 2] [--timers]
+        [--precision 1] [--steps 14] [--solves 2] [--mode 1] [--timers]
 
 The scene is first advanced `--steps` time steps with the per-phase PCG (so
 that no persistent-PCG launch happens before the timed solves; profilers can
 then select the n-th persistent launch directly), then the system
 H p = -G of the first Newton iteration of the next subproblem (Alg. 2) is
-assembled at x = x_hat = x^t and solved `--solves` times from p = 0.  Prints
+assembled at x = x_hat = x^t and solved `--solves` times from p = 0 in PCG mode `--mode` (see
+bf_set_pcg_mode).  Prints
 one JSON line: iterations per solve, milliseconds per solve, microseconds per
 iteration, the solver configuration and the system size.
 """
@@ -30,6 +31,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=14)
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--mode", type=int, default=1, help="bf_set_pcg_mode of the timed solves")
     ap.add_argument("--timers", action="store_true", help="also report the per-phase time of CTA 0")
     args = ap.parse_args(argv)
 
@@ -57,7 +59,7 @@ def main(argv=None):
     G = torch.zeros_like(xd)
     B.bf_assemble(sim.h, xt, xd, xd, G)
     b = -G
-    B.bf_set_pcg_mode(sim.h, 1)
+    B.bf_set_pcg_mode(sim.h, args.mode)
     B.bf_enable_timers(sim.h, args.timers)
     iters, ms = [], []
     for _ in range(args.solves):

@@ -158,7 +158,7 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
     b = B.bf_batch_create(n_workers, budget_bytes)
     deadline = time.monotonic() + timeout_s
     live = {}  # ticket -> (handle, keep)
-    lat, waits, steps, bad = [], [], 0, 0
+    lat, waits, steps, bad, statuses = [], [], 0, 0, []
     lock = threading.Lock()
     t0 = B.bf_batch_now(b)
 
@@ -193,6 +193,8 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
                 lat.extend(_latencies(r))
                 steps += r["steps_done"]
                 bad += r["status"] != 0
+                if r["status"] != 0:
+                    statuses.append(int(r["status"]))
             B.bf_batch_release(b, t)
             B.bf_scene_destroy(h)
 
@@ -214,7 +216,8 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
         reap(block=True)
         out = _summary(lat, steps, last_done - t0 - requests[0][0] if requests else 0.0)
         w = np.asarray(waits)
-        out.update({"requests": len(requests), "failed": bad, "workers": n_workers, "creators": n_creators,
+        out.update({"requests": len(requests), "failed": bad, "failed_status": statuses, "workers": n_workers,
+                    "creators": n_creators,
                     "admission_wait_p50_ms": float(np.percentile(w, 50) * 1e3) if len(w) else None,
                     "admission_wait_p99_ms": float(np.percentile(w, 99) * 1e3) if len(w) else None,
                     "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None})

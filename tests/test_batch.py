@@ -73,5 +73,5 @@ def test_budget_tickets_and_results(torch_cuda):
 def test_serve_small_stream(torch_cuda):
     reqs = serving.poisson_requests(12, rate=200.0, seed=1, t_lo=1e3, t_hi=6e3)
     out = serving.serve(reqs, n_steps=3, n_workers=4)
-    assert out["failed"] == 0 and out["steps"] == 36
+    assert out["failed"] == 0 and out["steps"] == 36, out
     assert out["p99_step_ms"] >= out["p50_step_ms"] > 0
