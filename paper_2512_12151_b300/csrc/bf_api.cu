@@ -324,10 +324,13 @@ static int step_once(Scene &S, bf_step_stats *out)
         cudaMemcpyAsync(S.xh_prev, S.xh, nb, cudaMemcpyDeviceToDevice, S.stream);
         int rc = solve_subproblem(S, S.xtilde, S.xk, S.xh, ss);
         if (rc) return rc;
-        rc = run_update_active_set(S, S.xk, S.xh_prev);
-        if (rc) return rc;
+        // UpdateActiveSet along x^k -> xhat^k and MaxStepSize along
+        // x^k -> xhat^{k+1}: one broad phase serves both
+        int nh = 0;
         double alpha = 1.0;
-        rc = run_ccd(S, S.xk, S.xh, false, &alpha, nullptr);
+        rc = run_ccd_two(S, S.xk, S.xh_prev, S.xh, &nh, &alpha);
+        if (rc) return rc;
+        rc = apply_active_set_hits(S, nh);
         if (rc) return rc;
         launch_blend(S, S.xk, S.xh, alpha, n);
         if (k + 1 >= S.prm.k_min) beta = (1.0 - alpha) * beta;

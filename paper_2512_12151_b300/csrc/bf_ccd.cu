@@ -249,9 +249,11 @@ void launch_linearize_out(Scene &S, const double *xlin, double *dout, double *go
 // ---------------------------------------------------------------------------
 // LBVH
 // ---------------------------------------------------------------------------
+// box of a primitive over its vertices at x0 and x1 (and x2 unless null)
 template <int NV>
 __global__ void k_prim_boxes(int n, const int *__restrict__ ids, const double *__restrict__ x0,
-                             const double *__restrict__ x1, double *__restrict__ lo, double *__restrict__ hi)
+                             const double *__restrict__ x1, const double *__restrict__ x2, double *__restrict__ lo,
+                             double *__restrict__ hi)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -264,6 +266,11 @@ __global__ void k_prim_boxes(int n, const int *__restrict__ ids, const double *_
             const double a = x0[3 * v + c], b = x1[3 * v + c];
             l[c] = fmin(l[c], fmin(a, b));
             h[c] = fmax(h[c], fmax(a, b));
+            if (x2) {
+                const double e = x2[3 * v + c];
+                l[c] = fmin(l[c], e);
+                h[c] = fmax(h[c], e);
+            }
         }
     }
 #pragma unroll
@@ -449,12 +456,14 @@ static void bvh_fill(Scene &S, LBVH &T)
     }
 }
 
-// Builds the tree over the swept boxes along x0 -> x1: Morton order of the
+// Builds the tree over the swept boxes along x0 -> x1 (or the boxes of the
+// vertices at x0, x1 and x2 when x2 is given): Morton order of the
 // box centres (radix sort), then the node boxes.  Within one time step, when
 // the scene allows it, the leaf order of the step's first build is kept and
 // only the boxes are recomputed: any leaf order gives the same candidates.
 template <int NV>
-static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0, const double *x1)
+static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0, const double *x1,
+                     const double *x2)
 {
     if (T.n != n) T.topo_valid = 0;
     T.n = n;
@@ -465,7 +474,7 @@ static int bvh_build(Scene &S, LBVH &T, int n, const int *ids, const double *x0,
     while (T.npad < n) T.npad <<= 1;
     ScopedTimer tm(S, T_BVH);
     const int nb = cdiv(n, kThreads);
-    k_prim_boxes<NV><<<nb, kThreads, 0, S.stream>>>(n, ids, x0, x1, T.plo, T.phi); ++S.n_launch;
+    k_prim_boxes<NV><<<nb, kThreads, 0, S.stream>>>(n, ids, x0, x1, x2, T.plo, T.phi); ++S.n_launch;
     if (!(S.bvh_reuse && T.topo_valid)) {
         int init[6];
         for (int c = 0; c < 3; ++c) {
@@ -524,7 +533,8 @@ struct QueryTree {
 // with one atomic per group of converged lanes.
 template <int TYPE>
 __device__ __forceinline__ void query_walk(const QueryTree &T, int q, int h0, int ls, const double *__restrict__ x0,
-                                           const double *__restrict__ x1, const int *__restrict__ st,
+                                           const double *__restrict__ x1, const double *__restrict__ x2,
+                                           const int *__restrict__ st,
                                            const int *__restrict__ se, const uint8_t *__restrict__ dir, int cap,
                                            int *dflag, int *stk)
 {
@@ -543,6 +553,10 @@ __device__ __forceinline__ void query_walk(const QueryTree &T, int q, int h0, in
             const double a = x0[3 * qa + c], b = x1[3 * qa + c];
             ql[c] = fmin(a, b);
             qh[c] = fmax(a, b);
+            if (x2) {
+                ql[c] = fmin(ql[c], x2[3 * qa + c]);
+                qh[c] = fmax(qh[c], x2[3 * qa + c]);
+            }
         }
     } else {
         qa = T.prim[q];
@@ -644,6 +658,7 @@ __host__ __device__ __forceinline__ int query_warps(int nq, int N)
 // each alone is too small to fill the device.
 __global__ void __launch_bounds__(kQueryThreads) k_query(QueryTree pt, QueryTree ee, int wpt, int wee,
                                                          const double *__restrict__ x0, const double *__restrict__ x1,
+                                                         const double *__restrict__ x2,
                                                          const int *__restrict__ st, const int *__restrict__ se,
                                                          const uint8_t *__restrict__ dir, int cap, int *dflag)
 {
@@ -653,15 +668,18 @@ __global__ void __launch_bounds__(kQueryThreads) k_query(QueryTree pt, QueryTree
     int *stk = stack + threadIdx.x;
     if (w < wpt) {
         const int ls = query_split_level(pt.N), j = w & ((1 << ls) - 1), q = (w >> ls) * 32 + lane;
-        if (q < pt.nq) query_walk<PT>(pt, q, (1 << ls) + j, ls, x0, x1, st, se, dir, cap, dflag, stk);
+        if (q < pt.nq) query_walk<PT>(pt, q, (1 << ls) + j, ls, x0, x1, x2, st, se, dir, cap, dflag, stk);
     } else if ((w -= wpt) < wee) {
         const int ls = query_split_level(ee.N), j = w & ((1 << ls) - 1), q = (w >> ls) * 32 + lane;
-        if (q < ee.nq) query_walk<EE>(ee, q, (1 << ls) + j, ls, x0, x1, st, se, dir, cap, dflag, stk);
+        if (q < ee.nq) query_walk<EE>(ee, q, (1 << ls) + j, ls, x0, x1, x2, st, se, dir, cap, dflag, stk);
     }
 }
 
-// narrow phase over candidates; mode 0: min TOI, mode 1: collect hits
-template <int TYPE>
+// narrow phase over candidates; mode 0: min TOI, mode 1: collect hits.
+// FILTER: the list is a superset; a pair goes on only if its exact FP64
+// swept boxes overlap (the test the broad phase's leaf test makes: point
+// against triangle, edge against edge, closed boxes)
+template <int TYPE, bool FILTER>
 __global__ void k_narrow(int n, const int2 *__restrict__ cand, const int *__restrict__ st, const int *__restrict__ se,
                          const double *__restrict__ x0, const double *__restrict__ x1, double s, int max_iter, int mode,
                          double *toi_min, int *hit_type, int *hit_a, int *hit_b, double *hit_toi, int hit_cap,
@@ -674,6 +692,25 @@ __global__ void k_narrow(int n, const int2 *__restrict__ cand, const int *__rest
     double p0[12], p1[12], t;
     gather12(x0, v, p0);
     gather12(x1, v, p1);
+    if (FILTER) {
+        const int split = TYPE == PT ? 1 : 2;  // vertices [0, split) against [split, 4)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double l1 = INFINITY, h1 = -INFINITY, l2 = INFINITY, h2 = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double lo = fmin(p0[3 * k + a], p1[3 * k + a]), hi = fmax(p0[3 * k + a], p1[3 * k + a]);
+                if (k < split) {
+                    l1 = fmin(l1, lo);
+                    h1 = fmax(h1, hi);
+                } else {
+                    l2 = fmin(l2, lo);
+                    h2 = fmax(h2, hi);
+                }
+            }
+            if (l1 > h2 || l2 > h1) return;
+        }
+    }
     if (!accd(TYPE, p0, p1, s, 1.0, max_iter, &t)) return;
     if (mode == 0) {
         atomic_min_pos(toi_min, t);
@@ -816,14 +853,14 @@ int ccd_reserve(Scene &S, int npt, int nee, int nhit)
     return BF_OK;
 }
 
-// Broad + narrow phase along x0 -> x1.  collect_hits: store every hit
-// (type, a, b, toi) and return their count; else *alpha_out =
-// min(1, min TOI).
-int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, double *alpha_out, int *nhits_out)
+// Broad phase: candidates (pairs whose swept boxes along x0 -> x1 overlap;
+// with x2, the boxes over x0, x1 and x2) into cand_pt / cand_ee, their
+// counts to *npt, *nee.
+static int broad_phase(Scene &S, const double *x0, const double *x1, const double *x2, int *npt_out, int *nee_out)
 {
-    int st = bvh_build<3>(S, S.bvh_tri, S.nst, S.st, x0, x1);
+    int st = bvh_build<3>(S, S.bvh_tri, S.nst, S.st, x0, x1, x2);
     if (st) return st;
-    st = bvh_build<2>(S, S.bvh_edge, S.nse, S.se, x0, x1);
+    st = bvh_build<2>(S, S.bvh_edge, S.nse, S.se, x0, x1, x2);
     if (st) return st;
     int npt = 0, nee = 0;
     cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
@@ -837,8 +874,8 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         const int wpt = query_warps(pt.nq, pt.N), wee = query_warps(ee.nq, ee.N);
         if (wpt + wee > 0) {
             const int wpb = kQueryThreads / 32;
-            k_query<<<cdiv(wpt + wee, wpb), kQueryThreads, 0, S.stream>>>(pt, ee, wpt, wee, x0, x1, S.st, S.se,
-                                                                        S.dir, S.cand_cap, S.dflag);
+            k_query<<<cdiv(wpt + wee, wpb), kQueryThreads, 0, S.stream>>>(pt, ee, wpt, wee, x0, x1, x2, S.st,
+                                                                        S.se, S.dir, S.cand_cap, S.dflag);
             ++S.n_launch;
         }
         st = sync_flags(S);
@@ -851,6 +888,18 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         if (st) return st;
     }
     if (npt > S.cand_cap || nee > S.cand_cap) return BF_E_CAPACITY;
+    *npt_out = npt;
+    *nee_out = nee;
+    return BF_OK;
+}
+
+// Narrow phase over the listed pairs: min TOI to *alpha_out, or every hit
+// (type, a, b, toi) stored and counted to *nhits_out.  With `filter` the
+// lists cover a wider motion: a pair goes on only if its exact swept boxes
+// along x0 -> x1 overlap, so exactly the candidates of this motion remain.
+static int narrow_phase(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,
+                        bool collect_hits, double *alpha_out, int *nhits_out)
+{
     const double s = S.prm.s_ccd;
     for (int attempt = 0; attempt < 3; ++attempt) {
         if (collect_hits) {
@@ -861,22 +910,22 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         }
         {
             ScopedTimer tm(S, T_CCD_NARROW);
-            if (npt)
-                {
-                    k_narrow<PT><<<cdiv(npt, 128), 128, 0, S.stream>>>(npt, S.cand_pt, S.st, S.se, x0, x1, s, kAccdMaxIter,
-                                                                  collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type,
-                                                                  S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
-                                                                  S.dflag + F_NHIT); ++S.n_launch;
-                }
-            if (nee)
-                {
-                    k_narrow<EE><<<cdiv(nee, 128), 128, 0, S.stream>>>(nee, S.cand_ee, S.st, S.se, x0, x1, s, kAccdMaxIter,
-                                                                  collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type,
-                                                                  S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
-                                                                  S.dflag + F_NHIT); ++S.n_launch;
-                }
+            auto launch = [&](auto kern, int n, const int2 *cand) {
+                if (!n) return;
+                kern<<<cdiv(n, 128), 128, 0, S.stream>>>(n, cand, S.st, S.se, x0, x1, s, kAccdMaxIter,
+                                                        collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type, S.hit_a,
+                                                        S.hit_b, S.hit_toi, S.hit_cap, S.dflag + F_NHIT);
+                ++S.n_launch;
+            };
+            if (filter) {
+                launch(k_narrow<PT, true>, npt, S.cand_pt);
+                launch(k_narrow<EE, true>, nee, S.cand_ee);
+            } else {
+                launch(k_narrow<PT, false>, npt, S.cand_pt);
+                launch(k_narrow<EE, false>, nee, S.cand_ee);
+            }
         }
-        st = sync_flags(S);
+        int st = sync_flags(S);
         if (st) return st;
         if (!collect_hits) {
             if (alpha_out) *alpha_out = std::min(1.0, S.h_scal[S_TOI]);
@@ -891,6 +940,29 @@ int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, dou
         if (st) return st;
     }
     return BF_E_CAPACITY;
+}
+
+// Broad + narrow phase along x0 -> x1.  collect_hits: store every hit
+// (type, a, b, toi) and return their count; else *alpha_out = min(1, TOI).
+int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, double *alpha_out, int *nhits_out)
+{
+    int npt = 0, nee = 0;
+    const int st = broad_phase(S, x0, x1, nullptr, &npt, &nee);
+    if (st) return st;
+    return narrow_phase(S, x0, x1, npt, nee, false, collect_hits, alpha_out, nhits_out);
+}
+
+// The two CCD passes of an outer iteration start at the same x0: the
+// candidates over the boxes of x0, xa and xb contain those of both motions,
+// and the exact box test of each narrow pass keeps exactly its own.
+int run_ccd_two(Scene &S, const double *x0, const double *xa, const double *xb, int *nhits_a, double *alpha_b)
+{
+    int npt = 0, nee = 0;
+    int st = broad_phase(S, x0, xa, xb, &npt, &nee);
+    if (st) return st;
+    st = narrow_phase(S, x0, xa, npt, nee, true, true, nullptr, nhits_a);
+    if (st) return st;
+    return narrow_phase(S, x0, xb, npt, nee, true, false, alpha_b, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -999,8 +1071,14 @@ static void compact_array(Scene &S, int nc, const int *flag, const int *pos, T *
 int run_update_active_set(Scene &S, const double *x, const double *xhat)
 {
     int nh = 0;
-    int st = run_ccd(S, x, xhat, true, nullptr, &nh);
+    const int st = run_ccd(S, x, xhat, true, nullptr, &nh);
     if (st) return st;
+    return apply_active_set_hits(S, nh);
+}
+
+int apply_active_set_hits(Scene &S, int nh)
+{
+    int st = BF_OK;
     if (nh > 0) {
         // sorted keys of C for the membership test
         size_t bytes = 0;

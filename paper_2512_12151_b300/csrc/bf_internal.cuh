@@ -209,6 +209,11 @@ void launch_linearize(Scene &S, const double *xlin);
 int run_ccd(Scene &S, const double *x0, const double *x1, bool collect_hits, double *alpha_out,
             int *nhits_out);
 int run_update_active_set(Scene &S, const double *x, const double *xhat);
+// both CCD passes of an outer iteration from one broad phase: hits along
+// x0 -> xa (collected, count to *nhits_a) and the TOI along x0 -> xb
+int run_ccd_two(Scene &S, const double *x0, const double *xa, const double *xb, int *nhits_a, double *alpha_b);
+// Alg. 3 on the hits collected by the last CCD pass
+int apply_active_set_hits(Scene &S, int nh);
 int accd_pairs(int type, int n, const double *x0, const double *x1, double s, double *toi,
                cudaStream_t st);
 int ccd_reserve(Scene &S, int npt, int nee, int nhit);
