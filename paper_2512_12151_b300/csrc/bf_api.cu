@@ -255,20 +255,34 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
         }
         assemble(S, xtilde, xlin, xhat);
         k_scale<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, -1.0); ++S.n_launch;
-        int it = 0;
-        int st = run_pcg(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it);
+        int it = 0, pending = 0;
+        int st = run_pcg_async(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it, &pending);
+        if (st && st != BF_E_CG_MAXIT) return st;
+        // L at xhat and at the full step queued behind the solve: one
+        // synchronisation for the three
+        launch_axpy_to(S, S.xtmp, xhat, 1.0, S.pdir, n);
+        launch_energy(S, xtilde, xlin, xhat, S.dscal + S_E0);
+        launch_energy(S, xtilde, xlin, S.xtmp, S.dscal + S_E1);
+        const int sst = sync_flags(S);
+        if (sst) {
+            pcg_release(S);
+            return sst;
+        }
+        if (pending) st = pcg_finish(S, &it);
         ss.cg += it;
         if (st == BF_E_CG_MAXIT) ss.cg_maxit++;
         else if (st) return st;
-        const double L0 = run_energy(S, xtilde, xlin, xhat);
+        const double L0 = S.h_scal[S_E0];
         if (!std::isfinite(L0)) return BF_E_NONFINITE;
         if (S.L_scale < 0.0) S.L_scale = std::fabs(L0);
         const double ls_tol = 1e-12 * std::max(std::fabs(L0), S.L_scale);
-        double r = 1.0;
+        double r = 1.0, L1 = S.h_scal[S_E1];
         bool ok = false;
         for (int j = 0; j <= S.prm.max_ls; ++j) {
-            launch_axpy_to(S, S.xtmp, xhat, r, S.pdir, n);
-            const double L1 = run_energy(S, xtilde, xlin, S.xtmp);
+            if (j > 0) {
+                launch_axpy_to(S, S.xtmp, xhat, r, S.pdir, n);
+                L1 = run_energy(S, xtilde, xlin, S.xtmp);
+            }
             if (std::isfinite(L1) && L1 <= L0 + ls_tol) {
                 ok = true;
                 break;
@@ -718,6 +732,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
 static void destroy(Scene &S)
 {
     if (S.stream) cudaStreamSynchronize(S.stream);
+    pcg_release(S);
     std::vector<void *> o = S.owned;
     for (void *p : o) dev_free(S, p);
     if (S.h_scal) cudaFreeHost(S.h_scal);

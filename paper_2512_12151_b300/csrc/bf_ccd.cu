@@ -897,34 +897,38 @@ static int broad_phase(Scene &S, const double *x0, const double *x1, const doubl
 // (type, a, b, toi) stored and counted to *nhits_out.  With `filter` the
 // lists cover a wider motion: a pair goes on only if its exact swept boxes
 // along x0 -> x1 overlap, so exactly the candidates of this motion remain.
+static void launch_narrow(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,
+                          bool collect_hits)
+{
+    const double s = S.prm.s_ccd;
+    if (collect_hits) {
+        cudaMemsetAsync(S.dflag + F_NHIT, 0, sizeof(int), S.stream);
+    } else {
+        const double one = 1.0;
+        cudaMemcpyAsync(S.dscal + S_TOI, &one, sizeof(double), cudaMemcpyHostToDevice, S.stream);
+    }
+    ScopedTimer tm(S, T_CCD_NARROW);
+    auto launch = [&](auto kern, int n, const int2 *cand) {
+        if (!n) return;
+        kern<<<cdiv(n, 128), 128, 0, S.stream>>>(n, cand, S.st, S.se, x0, x1, s, kAccdMaxIter, collect_hits ? 1 : 0,
+                                                S.dscal + S_TOI, S.hit_type, S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
+                                                S.dflag + F_NHIT);
+        ++S.n_launch;
+    };
+    if (filter) {
+        launch(k_narrow<PT, true>, npt, S.cand_pt);
+        launch(k_narrow<EE, true>, nee, S.cand_ee);
+    } else {
+        launch(k_narrow<PT, false>, npt, S.cand_pt);
+        launch(k_narrow<EE, false>, nee, S.cand_ee);
+    }
+}
+
 static int narrow_phase(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,
                         bool collect_hits, double *alpha_out, int *nhits_out)
 {
-    const double s = S.prm.s_ccd;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        if (collect_hits) {
-            cudaMemsetAsync(S.dflag + F_NHIT, 0, sizeof(int), S.stream);
-        } else {
-            const double one = 1.0;
-            cudaMemcpyAsync(S.dscal + S_TOI, &one, sizeof(double), cudaMemcpyHostToDevice, S.stream);
-        }
-        {
-            ScopedTimer tm(S, T_CCD_NARROW);
-            auto launch = [&](auto kern, int n, const int2 *cand) {
-                if (!n) return;
-                kern<<<cdiv(n, 128), 128, 0, S.stream>>>(n, cand, S.st, S.se, x0, x1, s, kAccdMaxIter,
-                                                        collect_hits ? 1 : 0, S.dscal + S_TOI, S.hit_type, S.hit_a,
-                                                        S.hit_b, S.hit_toi, S.hit_cap, S.dflag + F_NHIT);
-                ++S.n_launch;
-            };
-            if (filter) {
-                launch(k_narrow<PT, true>, npt, S.cand_pt);
-                launch(k_narrow<EE, true>, nee, S.cand_ee);
-            } else {
-                launch(k_narrow<PT, false>, npt, S.cand_pt);
-                launch(k_narrow<EE, false>, nee, S.cand_ee);
-            }
-        }
+        launch_narrow(S, x0, x1, npt, nee, filter, collect_hits);
         int st = sync_flags(S);
         if (st) return st;
         if (!collect_hits) {
@@ -960,9 +964,21 @@ int run_ccd_two(Scene &S, const double *x0, const double *xa, const double *xb, 
     int npt = 0, nee = 0;
     int st = broad_phase(S, x0, xa, xb, &npt, &nee);
     if (st) return st;
-    st = narrow_phase(S, x0, xa, npt, nee, true, true, nullptr, nhits_a);
-    if (st) return st;
-    return narrow_phase(S, x0, xb, npt, nee, true, false, alpha_b, nullptr);
+    for (int attempt = 0; attempt < 3; ++attempt) {  // both narrow passes, one synchronisation
+        launch_narrow(S, x0, xa, npt, nee, true, true);
+        launch_narrow(S, x0, xb, npt, nee, true, false);
+        st = sync_flags(S);
+        if (st) return st;
+        const int nh = S.h_flag[F_NHIT];
+        if (nh <= S.hit_cap) {
+            *nhits_a = nh;
+            *alpha_b = std::min(1.0, S.h_scal[S_TOI]);
+            return BF_OK;
+        }
+        st = ccd_reserve(S, 0, 0, nh);
+        if (st) return st;
+    }
+    return BF_E_CAPACITY;
 }
 
 // ---------------------------------------------------------------------------

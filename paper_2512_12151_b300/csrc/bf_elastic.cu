@@ -486,16 +486,20 @@ __global__ void __launch_bounds__(kThreads) k_energy(
     if (grid_sum<1>(v, partials, counter, tot)) *out = tot[0];
 }
 
-double run_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
+void launch_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat, double *out)
 {
     const long long nthr = (long long)S.nv + S.nt + S.nc;
     const int nb = cdiv(nthr, kThreads);
-    {
-        ScopedTimer tm(S, T_ENERGY);
-        k_energy<<<nb, kThreads, 0, S.stream>>>(S.nv, S.nt, S.nc, S.mass, S.dir, xtilde, xhat, S.tets, S.B, S.vol,
-                                                S.emu, S.elam, S.prm.dt * S.prm.dt, S.cv, S.cd, S.cg, S.clam, S.cgam,
-                                                S.cs, xlin, S.mu, S.delta, S.partials, S.counter, S.dscal + S_E0); ++S.n_launch;
-    }
+    ScopedTimer tm(S, T_ENERGY);
+    k_energy<<<nb, kThreads, 0, S.stream>>>(S.nv, S.nt, S.nc, S.mass, S.dir, xtilde, xhat, S.tets, S.B, S.vol, S.emu,
+                                            S.elam, S.prm.dt * S.prm.dt, S.cv, S.cd, S.cg, S.clam, S.cgam, S.cs, xlin,
+                                            S.mu, S.delta, S.partials, S.counter, out);
+    ++S.n_launch;
+}
+
+double run_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
+{
+    launch_energy(S, xtilde, xlin, xhat, S.dscal + S_E0);
     if (sync_flags(S)) return NAN;
     return S.h_scal[S_E0];
 }

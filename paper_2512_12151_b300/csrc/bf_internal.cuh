@@ -110,6 +110,7 @@ struct Scene {
     int pcg_allow_resident = 1;  // persistent PCG may keep the matrix in shared memory
     int pcg_force_global = 0;    // persistent PCG: use the global-vectors variant only
     int pcg_max_rows = 0, pcg_max_ent = 0, pcg_max_win = 0, pcg_block = 256;
+    int pcg_slots_held = 0, pcg_slots_dev = 0;  // SM slots held by a launched persistent solve
     unsigned short *pcg_eslot = nullptr;  // persistent PCG: shared-memory slot of every full-row entry
     int *pcg_rinfo = nullptr, *pcg_lvl = nullptr, *pcg_lvlptr = nullptr;  // rows by length, level offsets
     int pcg_max_len = 0;
@@ -186,6 +187,12 @@ void launch_zero(Scene &S, double *p, size_t n);
 void launch_spmv(Scene &S, const double *x, double *y, bool with_dot, const int *done);
 void launch_pinv(Scene &S);
 int run_pcg(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
+// Launches a solve whose completion the caller reads after its next
+// sync_flags with pcg_finish (*pending = 1: the persistent kernel); when
+// the solve had to complete here (*pending = 0) its status is returned.
+int run_pcg_async(Scene &S, const double *b, double *x, double tol, int maxit, int *iters, int *pending);
+int pcg_finish(Scene &S, int *iters);
+void pcg_release(Scene &S);  // gives back the SM slots of a launched solve (error paths, destruction)
 int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
 void launch_axpy_to(Scene &S, double *out, const double *a, double r, const double *p, int n);
 void launch_blend(Scene &S, double *xk, const double *xh, double alpha, int n);
@@ -195,6 +202,8 @@ void launch_velocity(Scene &S);
 void launch_vertex_init(Scene &S, const double *xtilde, const double *xhat);
 void launch_elastic(Scene &S, const double *xhat);
 double run_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat);
+// L(xhat) into *out (device), no synchronisation
+void launch_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat, double *out);
 double run_mu_max_diag(Scene &S);
 void launch_xtilde(Scene &S, double *xtilde);
 

@@ -1009,31 +1009,38 @@ static CoopSlots &coop_slots(int dev)
     return slots[dev & 63];
 }
 
-class CoopGuard {
-  public:
-    CoopGuard(int dev, int units, int capacity) : c_(coop_slots(dev)), units_(std::min(units, capacity))
-    {
-        std::unique_lock<std::mutex> lk(c_.mu);
-        c_.cv.wait(lk, [&] { return c_.used + units_ <= capacity; });
-        c_.used += units_;
-    }
-    ~CoopGuard()
-    {
-        {
-            std::lock_guard<std::mutex> lk(c_.mu);
-            c_.used -= units_;
-        }
-        c_.cv.notify_all();
-    }
+// takes `units` SM slots of device `dev` (waiting until they are free);
+// returns the units taken
+static int coop_acquire(int dev, int units, int capacity)
+{
+    CoopSlots &c = coop_slots(dev);
+    units = std::min(units, capacity);
+    std::unique_lock<std::mutex> lk(c.mu);
+    c.cv.wait(lk, [&] { return c.used + units <= capacity; });
+    c.used += units;
+    return units;
+}
 
-  private:
-    CoopSlots &c_;
-    int units_;
-};
+static void coop_release(int dev, int units)
+{
+    CoopSlots &c = coop_slots(dev);
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        c.used -= units;
+    }
+    c.cv.notify_all();
+}
+
+// the slots of a launched solve go back once it has completed
+static void release_pcg_slots(Scene &S)
+{
+    if (S.pcg_slots_held) coop_release(S.pcg_slots_dev, S.pcg_slots_held);
+    S.pcg_slots_held = 0;
+}
 
 template <class MT, class VT>
 static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *p1, VT *qc, VT *z, const double *b,
-                           double *x, double tol, int maxit, int *iters)
+                           double *x, double tol, int maxit, int *iters, bool defer)
 {
     if (S.pcg_grid == 0) {
         const int st = setup_persistent<MT, VT>(S);
@@ -1096,7 +1103,9 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int cps = std::max(1, kPcgThreads / S.pcg_block);
-    CoopGuard slots(dev, grid * (kSlotsPerSm / std::min(cps, kSlotsPerSm)), nsm * kSlotsPerSm);  // held until done
+    release_pcg_slots(S);
+    S.pcg_slots_dev = dev;  // held until the solve has completed
+    S.pcg_slots_held = coop_acquire(dev, grid * (kSlotsPerSm / std::min(cps, kSlotsPerSm)), nsm * kSlotsPerSm);
     {
         ScopedTimer tm(S, T_PCG_PERSISTENT);
         const void *kern = S.pcg_resident == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
@@ -1105,9 +1114,23 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(S.pcg_block), args, (size_t)S.pcg_smem, S.stream);
         ++S.n_launch;
     }
-    if (e != cudaSuccess) return BF_E_CUDA;
-    int st = sync_flags(S);
-    if (st) return st;
+    if (e != cudaSuccess) {
+        release_pcg_slots(S);
+        return BF_E_CUDA;
+    }
+    if (defer) return BF_OK;
+    const int st = sync_flags(S);
+    if (st) {
+        release_pcg_slots(S);
+        return st;
+    }
+    return pcg_finish(S, iters);
+}
+
+// status of the last persistent solve, after a sync_flags
+int pcg_finish(Scene &S, int *iters)
+{
+    release_pcg_slots(S);
     if (iters) *iters = S.h_flag[F_ITERS];
     if (S.timers_on) {  // per-phase device time seen by CTA 0 (globaltimer)
         const int ids[7] = {T_PCG_PH_SPMV, T_PCG_PH_RED1, T_PCG_PH_UPD, T_PCG_PH_RED2, T_PCG_PH_STAGE,
@@ -1125,20 +1148,36 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
 
 // Falls back to the per-phase launches when no persistent configuration
 // fits (a vertex window beyond 16-bit offsets, or too little shared memory).
-int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters)
+static int persistent_entry(Scene &S, const double *b, double *x, double tol, int maxit, int *iters, bool defer,
+                            int *pending)
 {
     int st;
     if (S.prm.precision == BF_PREC_MIXED)
         st = persistent_impl<float, float>(S, S.valf, S.pinvf, S.cg_pf, S.cg_pf2, S.cg_qcf, S.cg_zf, b, x, tol, maxit,
-                                           iters);
+                                           iters, defer);
     else
         st = persistent_impl<double, double>(S, S.val, S.pinv, S.cg_p, S.cg_p2, S.cg_qc, S.cg_z, b, x, tol, maxit,
-                                             iters);
+                                             iters, defer);
     if (st == BF_E_CAPACITY && S.pcg_grid == 0) {
         S.pcg_mode = 0;
         return run_pcg(S, b, x, tol, maxit, iters);
     }
+    if (pending) *pending = defer && st == BF_OK;
     return st;
+}
+
+void pcg_release(Scene &S) { release_pcg_slots(S); }
+
+int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters)
+{
+    return persistent_entry(S, b, x, tol, maxit, iters, false, nullptr);
+}
+
+int run_pcg_async(Scene &S, const double *b, double *x, double tol, int maxit, int *iters, int *pending)
+{
+    *pending = 0;
+    if (S.pcg_mode != 1) return run_pcg(S, b, x, tol, maxit, iters);
+    return persistent_entry(S, b, x, tol, maxit, iters, true, pending);
 }
 
 }  // namespace bf
