@@ -79,9 +79,12 @@ typedef struct {
 
 /* Solver parameters.  Paper defaults (section 6, Alg. 1-3): eps = 1e-3,
  * k_min = 2, gamma_decay (Gamma) = 0.9, c_mu (C of section 5.2) = 0.1.
- * s_ccd is the ACCD conservative rescaling (target gap s_ccd * d(x0)). */
+ * s_ccd is the ACCD conservative rescaling (target gap s_ccd * d(x0)).
+ * mu_f and eps_v [m/s] are the friction coefficient and the velocity
+ * threshold of the smoothed semi-implicit friction of appendix A (mu_f = 0:
+ * no friction; the paper uses k_min = 6 with friction). */
 typedef struct {
-    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd;
+    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision;
 } bf_params;
 

@@ -28,7 +28,8 @@ def build(force: bool = False) -> str:
 class OrParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("delta", C.c_double), ("gravity", C.c_double * 3),
                 ("eps", C.c_double), ("cg_tol", C.c_double), ("gamma_decay", C.c_double),
-                ("c_mu", C.c_double), ("s_ccd", C.c_double), ("k_min", C.c_int32),
+                ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
+                ("eps_v", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
                 ("max_cg", C.c_int32), ("precision", C.c_int32)]
 
@@ -58,6 +59,9 @@ def lib():
         L.or_pt_dist2.restype = C.c_double
         L.or_ee_dist2.restype = C.c_double
         L.or_pair_dist_grad.restype = C.c_double
+        L.or_friction_f0.restype = C.c_double
+        L.or_friction_f0.argtypes = [C.c_double, C.c_double, _D, _D]
+        L.or_friction_eval.restype = C.c_double
         L.or_create.restype = C.c_void_p
         L.or_create.argtypes = [C.c_int32, _D, _D, _D, C.c_int32, _I, _I, C.c_int32, _D, C.c_int32, _I,
                                 C.POINTER(C.c_uint8), C.POINTER(OrParams)]
@@ -167,11 +171,19 @@ def accd(ptype, x0, x1, s=0.1, tmax=1.0, max_iter=100000):
     return t.value if hit else np.inf
 
 
+def friction_f0(y, eh):
+    """(f0, f0', f0'') of the smoothed norm at y (appendix A)"""
+    f1, f2 = C.c_double(), C.c_double()
+    f0 = lib().or_friction_f0(float(y), float(eh), C.byref(f1), C.byref(f2))
+    return f0, f1.value, f2.value
+
+
 def params_struct(p) -> OrParams:
     s = OrParams()
     s.dt, s.delta = p.dt, p.delta
     s.gravity[:] = list(p.gravity)
     s.eps, s.cg_tol, s.gamma_decay, s.c_mu, s.s_ccd = p.eps, p.cg_tol, p.gamma_decay, p.c_mu, p.s_ccd
+    s.mu_f, s.eps_v = p.mu_f, p.eps_v
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.precision = p.precision
@@ -330,6 +342,26 @@ class Oracle:
         d = C.c_double()
         lib().or_min_distance(C.c_void_p(self.h), _p(_f64(x)), C.byref(d))
         return d.value
+
+    # ---- friction (appendix A) ----
+    def friction_setup(self):
+        return lib().or_friction_setup(C.c_void_p(self.h))
+
+    def friction_get(self):
+        """(vertex ids (nf, 4), weights (nf, 4), normals (nf, 3), coefficients (nf,))"""
+        nf = lib().or_friction_count(C.c_void_p(self.h))
+        v4, w4 = np.zeros((nf, 4), np.int32), np.zeros((nf, 4))
+        n3, k = np.zeros((nf, 3)), np.zeros(nf)
+        if nf:
+            lib().or_friction_get(C.c_void_p(self.h), _p(v4), _p(w4), _p(n3), _p(k))
+        return v4, w4, n3, k
+
+    def friction_eval(self, xhat):
+        """(energy, gradient (nv, 3), per-pair 3x3 tangent Hessians (nf, 3, 3))"""
+        nf = lib().or_friction_count(C.c_void_p(self.h))
+        g, A = np.zeros((self.nv, 3)), np.zeros((max(nf, 1), 3, 3))
+        E = lib().or_friction_eval(C.c_void_p(self.h), _p(_f64(xhat, 3 * self.nv)), _p(g), _p(A))
+        return E, g, A[:nf]
 
     def step(self, n=1, alpha_cap=0):
         st = (OrStats * max(n, 1))()

@@ -48,6 +48,12 @@ struct or_scene {
     or_params p;
     double mu, delta;
     double L_scale; /* |L| at the time step's first Newton iterate (< 0: unset) */
+    /* friction pairs of the time step (appendix A): vertices, closest-point
+     * weights and unit normal at x^t, coefficient mu_f F; fA: the 3x3
+     * tangent Hessian of each pair at the last assembly */
+    int nf, fcap;
+    int *fv;
+    double *fw, *fn, *fk, *fA;
 };
 
 /* ------------------------------------------------------------------ */
@@ -655,7 +661,7 @@ void or_destroy(or_scene *S)
     void *ptrs[] = {S->X, S->x, S->v, S->targets, S->grad, S->tets, S->tmat, S->mats, S->dir, S->B,
                     S->vol, S->emu, S->elam, S->mass, S->sv, S->st, S->se, S->tri_key_sorted,
                     S->tri_key_idx, S->rp, S->ci, S->tmap, S->val, S->ctype, S->ca, S->cb,
-                    S->clam, S->cgam, S->cd, S->cs, S->cg};
+                    S->clam, S->cgam, S->cd, S->cs, S->cg, S->fv, S->fw, S->fn, S->fk, S->fA};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(S);
 }
@@ -893,6 +899,144 @@ static double constraint_c(const or_scene *S, int i, const double *xlin, const d
     return S->cd[i] + s - S->delta;
 }
 
+/* ------------------------------------------------------------------ */
+/* Semi-implicit friction (appendix A, the model of IPC, Li et al.     */
+/* 2020): U_f = sum_i mu_f F_i f0(|u_i|; h eps_v) over the pairs active */
+/* at x^t, F_i from the AL state of the previous step and the tangent   */
+/* operator fixed at x^t.  Readings: F_i is the magnitude               */
+/* h^-2 mu max(0, lambda_i/mu - c_i(x^t)) (the printed expression is    */
+/* its negative), with mu, delta and lambda as the previous step left   */
+/* them; in the incremental potential h^2 U_f the h^-2 cancels.  u_i is */
+/* the relative displacement of the closest points (weights w_k at x^t) */
+/* projected on the plane normal to n = (P - Q) / d at x^t, so |u_i|    */
+/* needs no basis.  f0(y) = y for y >= eh = h eps_v, else               */
+/* -y^3/(3 eh^2) + y^2/eh + eh/3 (C^2 at eh).  Its Hessian in u,        */
+/* f0''(y) t t^T + f0'(y)/y (I - t t^T) with t = u/|u|, is PSD as it    */
+/* stands (f0'' >= 0, f0' >= 0 here), so no projection is needed.       */
+/* ------------------------------------------------------------------ */
+double or_friction_f0(double y, double eh, double *f1, double *f2)
+{
+    if (y >= eh) {
+        if (f1) *f1 = 1.0;
+        if (f2) *f2 = 0.0;
+        return y;
+    }
+    double s = y / eh;
+    if (f1) *f1 = s * (2.0 - s);
+    if (f2) *f2 = 2.0 * (1.0 - s) / eh;
+    return eh * (s * s * (1.0 - s / 3.0) + 1.0 / 3.0);
+}
+
+/* f0'(y) / y, finite at y = 0 */
+static double friction_f1_over_y(double y, double eh)
+{
+    if (y >= eh) return 1.0 / y;
+    return (2.0 - y / eh) / eh;
+}
+
+/* signed weights w (P - Q = sum_k w_k x_k) and unit normal (P - Q)/d */
+static double pair_closest(int type, const double *x, double w[4], double n[3])
+{
+    double d2;
+    if (type == OR_PT) {
+        double b[3];
+        d2 = pt_closest(x, x + 3, x + 6, x + 9, b);
+        w[0] = 1.0; w[1] = -b[0]; w[2] = -b[1]; w[3] = -b[2];
+    } else {
+        double wa[2], wb[2];
+        d2 = ee_closest(x, x + 3, x + 6, x + 9, wa, wb);
+        w[0] = wa[0]; w[1] = wa[1]; w[2] = -wb[0]; w[3] = -wb[1];
+    }
+    double d = sqrt(d2), diff[3] = {0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 3; ++c) diff[c] += w[k] * x[3 * k + c];
+    for (int c = 0; c < 3; ++c) n[c] = d > 0.0 ? diff[c] / d : 0.0;
+    return d;
+}
+
+int32_t or_friction_setup(or_scene *S)
+{
+    S->nf = 0;
+    if (!(S->p.mu_f > 0.0) || !(S->mu > 0.0)) return 0;
+    if (S->fcap < S->nc) {
+        free(S->fv); free(S->fw); free(S->fn); free(S->fk); free(S->fA);
+        S->fcap = S->nc;
+        S->fv = (int *)xcalloc(4 * S->fcap, sizeof(int));
+        S->fw = (double *)xcalloc(4 * S->fcap, sizeof(double));
+        S->fn = (double *)xcalloc(3 * S->fcap, sizeof(double));
+        S->fk = (double *)xcalloc(S->fcap, sizeof(double));
+        S->fA = (double *)xcalloc(9 * S->fcap, sizeof(double));
+    }
+    for (int i = 0; i < S->nc; ++i) {
+        int v[4];
+        double x12[12], w[4], n[3];
+        pair_verts(S, S->ctype[i], S->ca[i], S->cb[i], v);
+        gather12(S->x, v, x12);
+        double d = pair_closest(S->ctype[i], x12, w, n);
+        double F = S->clam[i] / S->mu - (d - S->delta); /* lambda/mu - c(x^t), times mu below */
+        if (!(d > 0.0) || !(F > 0.0)) continue;
+        int j = S->nf++;
+        memcpy(S->fv + 4 * j, v, sizeof(v));
+        memcpy(S->fw + 4 * j, w, sizeof(w));
+        memcpy(S->fn + 3 * j, n, sizeof(n));
+        S->fk[j] = S->p.mu_f * S->mu * F;
+    }
+    return S->nf;
+}
+
+int32_t or_friction_count(const or_scene *S) { return S->nf; }
+
+void or_friction_get(const or_scene *S, int32_t *v4, double *w4, double *n3, double *k)
+{
+    if (v4) memcpy(v4, S->fv, 4 * (size_t)S->nf * sizeof(int));
+    if (w4) memcpy(w4, S->fw, 4 * (size_t)S->nf * sizeof(double));
+    if (n3) memcpy(n3, S->fn, 3 * (size_t)S->nf * sizeof(double));
+    if (k) memcpy(k, S->fk, (size_t)S->nf * sizeof(double));
+}
+
+/* tangential relative displacement of friction pair j at xhat (from x^t) */
+static double friction_slip(const or_scene *S, int j, const double *xhat, double ut[3])
+{
+    const int *v = S->fv + 4 * j;
+    const double *w = S->fw + 4 * j, *n = S->fn + 3 * j;
+    double D[3] = {0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 3; ++c) D[c] += w[k] * (xhat[3 * v[k] + c] - S->x[3 * v[k] + c]);
+    double dn = dot3(D, n);
+    for (int c = 0; c < 3; ++c) ut[c] = D[c] - dn * n[c];
+    return sqrt(dot3(ut, ut));
+}
+
+double or_friction_eval(or_scene *S, const double *xhat, double *grad, double *A9)
+{
+    double eh = S->p.dt * S->p.eps_v, E = 0.0;
+    if (grad) memset(grad, 0, 3 * (size_t)S->nv * sizeof(double));
+    for (int j = 0; j < S->nf; ++j) {
+        double ut[3], f1, f2;
+        double y = friction_slip(S, j, xhat, ut);
+        E += S->fk[j] * or_friction_f0(y, eh, &f1, &f2);
+        double fy = friction_f1_over_y(y, eh), k = S->fk[j];
+        const int *v = S->fv + 4 * j;
+        const double *w = S->fw + 4 * j, *n = S->fn + 3 * j;
+        if (grad)
+            for (int a = 0; a < 4; ++a)
+                for (int c = 0; c < 3; ++c) grad[3 * v[a] + c] += k * fy * w[a] * ut[c];
+        if (A9) {
+            /* k [f0'' t t^T + f0'/y (P - t t^T)], P = I - n n^T, t = ut / y */
+            double t[3] = {0, 0, 0};
+            if (y > 0.0)
+                for (int c = 0; c < 3; ++c) t[c] = ut[c] / y;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double P = (a == b ? 1.0 : 0.0) - n[a] * n[b];
+                    double tt = t[a] * t[b];
+                    A9[9 * j + 3 * a + b] = y > 0.0 ? k * (f2 * tt + fy * (P - tt)) : k * fy * P;
+                }
+        }
+    }
+    return E;
+}
+
 /* Alg. 2, Newton system: G and H of E (PSD-projected) plus the AL contact
  * terms with s_i = max(0, c_i - lambda_i/mu); the slack values are kept
  * for the line search.  Dirichlet DoFs are eliminated (section 5.3):
@@ -913,6 +1057,12 @@ double or_assemble(or_scene *S, const double *xtilde, const double *xlin, const 
         for (int k = 0; k < 4; ++k)
             for (int cc = 0; cc < 3; ++cc) S->grad[3 * v[k] + cc] += coef * S->cg[12 * i + 3 * k + cc];
     }
+    if (S->nf) { /* friction (appendix A): its gradient, and its Hessian blocks kept in fA */
+        double *gf = (double *)xcalloc(3 * S->nv, sizeof(double));
+        E += or_friction_eval(S, xhat, gf, S->fA);
+        for (int i = 0; i < 3 * S->nv; ++i) S->grad[i] += gf[i];
+        free(gf);
+    }
     for (int v = 0; v < S->nv; ++v)
         if (S->dir[v])
             for (int c = 0; c < 3; ++c) S->grad[3 * v + c] = 0.0;
@@ -924,7 +1074,8 @@ double or_assemble(or_scene *S, const double *xtilde, const double *xlin, const 
 void or_slacks(const or_scene *S, double *s) { memcpy(s, S->cs, S->nc * sizeof(double)); }
 
 /* Per-vertex diagonal 3x3 blocks of the full H (elastic + mass + the
- * contact terms mu gamma_i g_ia g_ia^T), before Dirichlet elimination. */
+ * contact terms mu gamma_i g_ia g_ia^T + the friction terms w_a^2 A_j),
+ * before Dirichlet elimination. */
 static double *diag_blocks(const or_scene *S)
 {
     double *D = (double *)xcalloc((size_t)9 * S->nv, sizeof(double));
@@ -938,6 +1089,11 @@ static double *diag_blocks(const or_scene *S)
                 for (int b = 0; b < 3; ++b) D[9 * pv[k] + 3 * a + b] += S->mu * S->cgam[i] * g[a] * g[b];
         }
     }
+    for (int j = 0; j < S->nf; ++j)
+        for (int k = 0; k < 4; ++k) {
+            double w2 = S->fw[4 * j + k] * S->fw[4 * j + k];
+            for (int e = 0; e < 9; ++e) D[9 * S->fv[4 * j + k] + e] += w2 * S->fA[9 * j + e];
+        }
     return D;
 }
 
@@ -965,6 +1121,17 @@ void or_hess_apply(const or_scene *S, const double *in, double *out)
         t *= S->mu * S->cgam[i];
         for (int k = 0; k < 4; ++k)
             for (int c = 0; c < 3; ++c) out[3 * v[k] + c] += t * g[3 * k + c];
+    }
+    /* friction (appendix A): block (a, b) of pair j is w_a w_b A_j */
+    for (int j = 0; j < S->nf; ++j) {
+        const int *v = S->fv + 4 * j;
+        const double *w = S->fw + 4 * j, *A = S->fA + 9 * j;
+        double D3[3] = {0, 0, 0}, y3[3];
+        for (int k = 0; k < 4; ++k)
+            for (int c = 0; c < 3; ++c) D3[c] += w[k] * xm[3 * v[k] + c];
+        for (int a = 0; a < 3; ++a) y3[a] = (A[3 * a] * D3[0] + A[3 * a + 1] * D3[1]) + A[3 * a + 2] * D3[2];
+        for (int k = 0; k < 4; ++k)
+            for (int c = 0; c < 3; ++c) out[3 * v[k] + c] += w[k] * y3[c];
     }
     double *D = diag_blocks(S);
     for (int v = 0; v < S->nv; ++v)
@@ -1073,6 +1240,7 @@ double or_energy_L(or_scene *S, const double *xtilde, const double *xlin, const 
         double cs = constraint_c(S, i, xlin, xhat) - sfix[i];
         L += S->cgam[i] * (0.5 * S->mu * cs * cs - S->clam[i] * cs);
     }
+    if (S->nf) L += or_friction_eval(S, xhat, NULL, NULL);
     return L;
 }
 
@@ -1398,6 +1566,7 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
             for (int v = 0; v < S->nv; ++v)
                 if (S->dir[v])
                     for (int c = 0; c < 3; ++c) xh[3 * v + c] = S->targets[3 * v + c];
+        or_friction_setup(S); /* from the AL state the previous step left (appendix A) */
         S->delta = S->p.delta;
         S->L_scale = -1.0; /* set by the step's first Newton iterate */
         or_mu_init(S, xh, xtilde);

@@ -18,7 +18,10 @@
  * closed form; PCG against a dense solve; the AL subproblem against an
  * independent constrained solve (KKT point); the active-set filter and decay
  * on hand-built cases; the time step by free fall, momentum, the beta product,
- * the moving-boundary bound and penetration-free states.  Whole trajectories
+ * the moving-boundary bound and penetration-free states; friction by the
+ * smoothing function's boundary values, finite differences of its energy and
+ * gradient, and the sliding and sticking block on an incline (closed-form
+ * acceleration g (sin theta - mu_f cos theta)).  Whole trajectories
  * of contact scenes have no value fixed outside this code: parity unpinned
  * beyond the invariants above.
  */
@@ -31,7 +34,7 @@ extern "C" {
 #endif
 
 typedef struct {
-    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd;
+    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision;
 } or_params;
 
@@ -103,6 +106,20 @@ double or_max_step_size(or_scene *S, const double *x0, const double *x1);
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
                 int32_t alpha_cap);
 int32_t or_min_distance(or_scene *S, const double *x, double *dmin);
+
+/* ---- semi-implicit friction (appendix A) ---- */
+/* f0(y; eh) with eh = h eps_v, and its first two derivatives */
+double or_friction_f0(double y, double eh, double *f1, double *f2);
+/* friction pairs from the current state and active set (done at every
+ * time step's start by or_step); returns their count */
+int32_t or_friction_setup(or_scene *S);
+int32_t or_friction_count(const or_scene *S);
+/* per pair: 4 vertex ids, 4 closest-point weights, unit normal, coefficient
+ * k = mu_f mu max(0, lambda/mu - c(x^t)) */
+void or_friction_get(const or_scene *S, int32_t *v4, double *w4, double *n3, double *k);
+/* friction energy at xhat; gradient (3 nv, may be NULL) and per-pair 3x3
+ * tangent Hessians (9 per pair, may be NULL) */
+double or_friction_eval(or_scene *S, const double *xhat, double *grad, double *A9);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,8 @@ class BfError(RuntimeError):
 class bf_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("delta", C.c_double), ("gravity", C.c_double * 3),
                 ("eps", C.c_double), ("cg_tol", C.c_double), ("gamma_decay", C.c_double),
-                ("c_mu", C.c_double), ("s_ccd", C.c_double), ("k_min", C.c_int32),
+                ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
+                ("eps_v", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
                 ("max_cg", C.c_int32), ("precision", C.c_int32)]
 
@@ -160,6 +161,7 @@ def make_params(p) -> bf_params:
     s.dt, s.delta = p.dt, p.delta
     s.gravity[:] = list(p.gravity)
     s.eps, s.cg_tol, s.gamma_decay, s.c_mu, s.s_ccd = p.eps, p.cg_tol, p.gamma_decay, p.c_mu, p.s_ccd
+    s.mu_f, s.eps_v = p.mu_f, p.eps_v
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.precision = p.precision

@@ -431,7 +431,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     if (nv >= (1 << 21) || nt >= (1 << 29)) return BF_E_ARG;  // triangle keys pack 3 vertex ids of 21 bits
     if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
         prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
-        prm->s_ccd >= 1)
+        prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)))
         return BF_E_ARG;
     S.nv = nv;
     S.nt = nt;

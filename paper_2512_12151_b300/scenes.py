@@ -38,7 +38,9 @@ class Params:
     dt: time step h; delta: contact offset (section 4.2); eps, k_min:
     termination rule (Eq. termination, section 6 uses 1e-3 and 2);
     cg_tol: relative PCG tolerance; gamma_decay: Gamma of section 4.2;
-    c_mu: C of section 5.2; s_ccd: ACCD conservative rescaling.
+    c_mu: C of section 5.2; s_ccd: ACCD conservative rescaling; mu_f,
+    eps_v: friction coefficient and velocity threshold of the smoothed
+    friction of appendix A (mu_f = 0: no friction).
     """
     dt: float = 0.01
     delta: float = 1e-3
@@ -49,6 +51,8 @@ class Params:
     gamma_decay: float = 0.9
     c_mu: float = 0.1
     s_ccd: float = 0.1
+    mu_f: float = 0.0
+    eps_v: float = 1e-3
     max_outer: int = 1000
     max_newton: int = 50
     max_ls: int = 30
@@ -183,6 +187,29 @@ def two_cubes(seed: int = 0, cells: int = 4, side: float = 0.1, precision: int =
     b.add_obstacle(gv, gt)
     return b.build(f"two_cubes_{cells}^3_seed{seed}", [[1e5, 0.4, 1000.0]],
                    Params(precision=precision), 20, {"seed": seed, "cells": cells})
+
+
+def slope_cube(mu_f: float, theta: float = math.atan(0.5), cells: int = 2, side: float = 0.1, E: float = 1e6,
+               precision: int = 0, n_steps: int = 40, eps_v: float = 1e-3) -> Scene:
+    """A cube (side 0.1 m, cells^3 cells) resting on an incline of angle theta
+    (the paper's sliding-friction test: tan theta = 0.5, friction coefficients
+    around 0.5).  The incline is the static quad z = 0 (4 m x 4 m) and gravity
+    is tilted instead, g = 9.8 (-sin theta, 0, -cos theta): the cube slides
+    along -x when mu_f < tan theta, at g (sin theta - mu_f cos theta).  Its
+    bottom starts 1.2 delta above the plane, at rest; k_min = 6 (the paper's
+    setting with friction); E = 1e6 Pa, nu = 0.3, rho = 1000.  The quad is
+    offset so that its diagonal stays clear of the cube's path: pairs with
+    the second triangle would enter the active set only once the step's CCD
+    catches a vertex (Alg. 3), after a transient sinking."""
+    b = _Builder()
+    p = Params(precision=precision, mu_f=mu_f, eps_v=eps_v, k_min=6,
+               gravity=(-9.8 * math.sin(theta), 0.0, -9.8 * math.cos(theta)))
+    v, t = cube_mesh(cells, side)
+    b.add_solid(v + np.array([-side / 2, -side / 2, 1.2 * p.delta]), t, 0)
+    gv, gt = ground_quad(2.0, center=(0.0, 1.5))  # the quad's diagonal stays clear of the cube's path
+    b.add_obstacle(gv, gt)
+    return b.build(f"slope_cube_{cells}^3_mu{mu_f:g}", [[E, 0.3, 1000.0]], p, n_steps,
+                   {"mu_f": mu_f, "theta": theta, "cells": cells})
 
 
 def eight_cubes(seed: int = 0, cells: int = 16, side: float = 0.1, precision: int = 1) -> Scene:
