@@ -199,6 +199,19 @@ int bf_linearize(bf_scene *scene, const double *xlin, double *dist, double *grad
 int bf_assemble(bf_scene *scene, const double *xtilde, const double *xlin, const double *xhat,
                 double *grad, double *energy);
 
+/* Semi-implicit friction (appendix A).  bf_friction_setup builds the
+ * friction pairs from the current state and active set, with the current
+ * mu and delta, as every time step does at its start: the active pairs
+ * with k = mu_f mu max(0, lambda/mu - c(x)) > 0, their closest-point
+ * weights and unit normal at x; later assemblies, energies, Hessian
+ * products and solves include their terms until the next step replaces
+ * them.  *n_pairs (host, may be NULL) receives their count.  bf_friction_get
+ * copies up to cap pairs (host, any may be NULL; order unspecified): 4
+ * vertex ids, 4 weights, the normal and k per pair; *n their count.
+ * mu_f = 0 gives no pairs. */
+int bf_friction_setup(bf_scene *scene, int32_t *n_pairs);
+int bf_friction_get(bf_scene *scene, int32_t cap, int32_t *n, int32_t *v4, double *w4, double *n3, double *k);
+
 /* y = H x with the H of the last bf_assemble (device n_verts*3 each);
  * prescribed rows/columns are eliminated (identity on the diagonal). */
 int bf_hess_apply(bf_scene *scene, const double *x, double *y);

@@ -110,6 +110,8 @@ def lib():
         "bf_get_timers": [_P, C.c_int32, _P, _P, _P],
         "bf_scene_bytes": [_P, C.POINTER(C.c_int64)],
         "bf_save": [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)],
+        "bf_friction_setup": [_P, C.POINTER(C.c_int32)],
+        "bf_friction_get": [_P, C.c_int32, C.POINTER(C.c_int32), _P, _P, _P, _P],
         "bf_load": [_P, _P, C.c_size_t],
         "bf_batch_create": [C.c_int32, C.c_int64, C.POINTER(_P)],
         "bf_batch_destroy": [_P],
@@ -390,6 +392,24 @@ def bf_get_timers(h):
     names = (C.c_char_p * cap)()
     n = lib().bf_get_timers(h, cap, _np_ptr(launches), _np_ptr(ms), names)
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def bf_friction_setup(h):
+    n = C.c_int32()
+    _check("bf_friction_setup", lib().bf_friction_setup(h, C.byref(n)))
+    return n.value
+
+
+def bf_friction_get(h):
+    """(vertex ids (nf, 4), weights (nf, 4), normals (nf, 3), coefficients (nf,))"""
+    n = C.c_int32()
+    _check("bf_friction_get", lib().bf_friction_get(h, 0, C.byref(n), None, None, None, None))
+    v4, w4 = np.zeros((n.value, 4), np.int32), np.zeros((n.value, 4))
+    n3, k = np.zeros((n.value, 3)), np.zeros(n.value)
+    if n.value:
+        _check("bf_friction_get", lib().bf_friction_get(h, n.value, C.byref(n), _np_ptr(v4), _np_ptr(w4),
+                                                        _np_ptr(n3), _np_ptr(k)))
+    return v4, w4, n3, k
 
 
 def bf_save(h):

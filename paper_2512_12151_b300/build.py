@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["bf_api.cu", "bf_linalg.cu", "bf_pcg.cu", "bf_elastic.cu", "bf_contact.cu", "bf_ccd.cu", "bf_batch.cu"]
+SOURCES = ["bf_api.cu", "bf_linalg.cu", "bf_pcg.cu", "bf_elastic.cu", "bf_contact.cu", "bf_ccd.cu", "bf_batch.cu",
+           "bf_friction.cu"]
 EXTRA = {"bf_ccd.cu": ["-fmad=false"]}
 
 

@@ -215,13 +215,16 @@ int active_reserve(Scene &S, int n)
 // ---------------------------------------------------------------------------
 // Newton step pieces
 // ---------------------------------------------------------------------------
-static void assemble(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
+static int assemble(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
 {
     cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
     launch_vertex_init(S, xtilde, xhat);
     launch_elastic(S, xhat);
     launch_contact_assemble(S, xlin, xhat);
+    const int st = launch_friction_assemble(S, xhat);
+    if (st) return st;
     launch_pinv(S);
+    return BF_OK;
 }
 
 static double mu_init(Scene &S, const double *xtilde, const double *xhat)
@@ -253,10 +256,11 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
             ss.newton_cap++;
             break;
         }
-        assemble(S, xtilde, xlin, xhat);
+        int st = assemble(S, xtilde, xlin, xhat);
+        if (st) return st;
         k_scale<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, -1.0); ++S.n_launch;
         int it = 0, pending = 0;
-        int st = run_pcg_async(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it, &pending);
+        st = run_pcg_async(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it, &pending);
         if (st && st != BF_E_CG_MAXIT) return st;
         // L at xhat and at the full step queued behind the solve: one
         // synchronisation for the three
@@ -317,6 +321,10 @@ static int step_once(Scene &S, bf_step_stats *out)
         {
             k_apply_targets<<<cdiv(S.ndir, kThreads), kThreads, 0, S.stream>>>(S.ndir, S.dir_ids, S.targets, S.xh); ++S.n_launch;
         }
+    {
+        const int fst = friction_setup(S);  // from the AL state the previous step left (appendix A)
+        if (fst) return fst;
+    }
     S.delta = S.prm.delta;
     S.L_scale = -1.0;  // set by the step's first Newton iterate
     S.bvh_tri.topo_valid = S.bvh_edge.topo_valid = 0;  // one tree topology per time step
@@ -1110,14 +1118,36 @@ int bf_assemble(bf_scene *scene, const double *xtilde, const double *xlin, const
     SCENE_OR_ARG(scene);
     if (!xtilde || !xlin || !xhat) return BF_E_ARG;
     if (!(S.mu > 0.0)) return BF_E_ARG;
-    assemble(S, xtilde, xlin, xhat);
+    int st = assemble(S, xtilde, xlin, xhat);
+    if (st) return st;
     if (grad) cudaMemcpyAsync(grad, S.grad, 3 * (size_t)S.nv * 8, cudaMemcpyDeviceToDevice, S.stream);
     if (energy) {
         *energy = run_energy(S, xtilde, xlin, xhat);
     }
-    int st = sync_flags(S);
+    st = sync_flags(S);
     if (st) return st;
     return (S.h_flag[F_ERR] & ERR_NONFINITE) ? BF_E_NONFINITE : BF_OK;
+}
+
+int bf_friction_setup(bf_scene *scene, int32_t *n_pairs)
+{
+    SCENE_OR_ARG(scene);
+    const int st = friction_setup(S);
+    if (n_pairs) *n_pairs = S.nf;
+    return st;
+}
+
+int bf_friction_get(bf_scene *scene, int32_t cap, int32_t *n, int32_t *v4, double *w4, double *n3, double *k)
+{
+    SCENE_OR_ARG(scene);
+    if (n) *n = S.nf;
+    const int m = std::min(cap, S.nf);
+    if (m <= 0) return BF_OK;
+    if (v4) cudaMemcpyAsync(v4, S.fv, (size_t)m * sizeof(int4), cudaMemcpyDeviceToHost, S.stream);
+    if (w4) cudaMemcpyAsync(w4, S.fw, 4 * (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
+    if (n3) cudaMemcpyAsync(n3, S.fn, 3 * (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
+    if (k) cudaMemcpyAsync(k, S.fk, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
+    return check_cuda(cudaStreamSynchronize(S.stream));
 }
 
 int bf_hess_apply(bf_scene *scene, const double *x, double *y)

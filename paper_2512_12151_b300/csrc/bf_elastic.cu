@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "bf_device.cuh"
+#include "bf_friction.cuh"
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -430,8 +431,10 @@ __global__ void __launch_bounds__(kThreads) k_energy(
     const double *__restrict__ Bm, const double *__restrict__ vol, const double *__restrict__ emu,
     const double *__restrict__ elam, double h2, const int4 *__restrict__ cv, const double *__restrict__ cd,
     const double *__restrict__ cg, const double *__restrict__ clam, const double *__restrict__ cgam,
-    const double *__restrict__ cs, const double *__restrict__ xlin, double mu, double delta, double *partials,
-    unsigned *counter, double *out)
+    const double *__restrict__ cs, const double *__restrict__ xlin, double mu, double delta, int nf,
+    const int4 *__restrict__ fv, const double *__restrict__ fw, const double *__restrict__ fn,
+    const double *__restrict__ fk, const double *__restrict__ fx0, double eh, double *partials, unsigned *counter,
+    double *out)
 {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0;
@@ -481,6 +484,8 @@ __global__ void __launch_bounds__(kThreads) k_energy(
         const double c = cd[i] + lin - delta;
         const double r = c - cs[i];
         e = cgam[i] * (0.5 * mu * r * r - clam[i] * r);
+    } else if (tid < (long long)nv + nt + nc + nf) {  // friction (appendix A)
+        e = friction_energy_term((int)(tid - nv - nt - nc), fv, fw, fn, fk, fx0, xh, eh);
     }
     double v[1] = {e}, tot[1];
     if (grid_sum<1>(v, partials, counter, tot)) *out = tot[0];
@@ -488,12 +493,13 @@ __global__ void __launch_bounds__(kThreads) k_energy(
 
 void launch_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat, double *out)
 {
-    const long long nthr = (long long)S.nv + S.nt + S.nc;
+    const long long nthr = (long long)S.nv + S.nt + S.nc + S.nf;
     const int nb = cdiv(nthr, kThreads);
     ScopedTimer tm(S, T_ENERGY);
     k_energy<<<nb, kThreads, 0, S.stream>>>(S.nv, S.nt, S.nc, S.mass, S.dir, xtilde, xhat, S.tets, S.B, S.vol, S.emu,
                                             S.elam, S.prm.dt * S.prm.dt, S.cv, S.cd, S.cg, S.clam, S.cgam, S.cs, xlin,
-                                            S.mu, S.delta, S.partials, S.counter, out);
+                                            S.mu, S.delta, S.nf, S.fv, S.fw, S.fn, S.fk, S.fx0,
+                                            S.prm.dt * S.prm.eps_v, S.partials, S.counter, out);
     ++S.n_launch;
 }
 

@@ -35,7 +35,7 @@ enum {
 };
 // device flag slots (dflag)
 enum {
-    F_DONE = 0, F_ITERS, F_ERR, F_MAXIT, F_NCAND_PT, F_NCAND_EE, F_NHIT, F_NKEEP, F_NSCRATCH,
+    F_DONE = 0, F_ITERS, F_ERR, F_MAXIT, F_NCAND_PT, F_NCAND_EE, F_NHIT, F_NKEEP, F_NSCRATCH, F_NFRIC,
     F_NFLAG = 32
 };
 // error bits in dflag[F_ERR]
@@ -147,6 +147,12 @@ struct Scene {
     bool bvh_reuse = false;  // within a time step: refit the trees instead of rebuilding them
     int cand_cap = 0;
     int2 *cand_pt = nullptr, *cand_ee = nullptr;
+    // friction pairs of the time step (appendix A): vertices, closest-point
+    // weights and unit normal at x^t (fx0), coefficient mu_f mu F, free mask
+    int nf = 0, fcap = 0;
+    int4 *fv = nullptr;
+    double *fw = nullptr, *fn = nullptr, *fk = nullptr, *fx0 = nullptr;
+    unsigned char *fmask = nullptr;
     int hit_cap = 0;
     int *hit_type = nullptr, *hit_a = nullptr, *hit_b = nullptr;
     double *hit_toi = nullptr;
@@ -187,6 +193,11 @@ void launch_zero(Scene &S, double *p, size_t n);
 void launch_spmv(Scene &S, const double *x, double *y, bool with_dot, const int *done);
 void launch_pinv(Scene &S);
 int run_pcg(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
+// rank-one terms of the Hessian applied by the PCG and the SpMV: the
+// augmented-Lagrangian pairs, then two per friction pair
+inline int n_terms(const Scene &S) { return S.nc + 2 * S.nf; }
+int friction_setup(Scene &S);                              // at a time step's start
+int launch_friction_assemble(Scene &S, const double *xhat);  // per Newton iteration
 // Launches a solve whose completion the caller reads after its next
 // sync_flags with pcg_finish (*pending = 1: the persistent kernel); when
 // the solve had to complete here (*pending = 0) its status is returned.

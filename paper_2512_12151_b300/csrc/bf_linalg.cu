@@ -120,10 +120,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(
 template <class MT, class VI, class VO>
 static void spmv_impl(Scene &S, const MT *val, const VI *x, VO *y, int with_dot, const int *done)
 {
-    const long long nthr = (long long)S.nnzb + S.nc;
+    const long long nthr = (long long)S.nnzb + n_terms(S);
     const int nb = cdiv(nthr, kThreads);
     ScopedTimer tm(S, T_SPMV);
-    k_spmv<MT, VI, VO><<<nb, kThreads, 0, S.stream>>>(S.nnzb, S.rowid, S.col, val, S.nc, S.cv, S.cg,
+    k_spmv<MT, VI, VO><<<nb, kThreads, 0, S.stream>>>(S.nnzb, S.rowid, S.col, val, n_terms(S), S.cv, S.cg,
                                                       S.cw, S.cmask, x, y, with_dot, S.partials,
                                                       S.counter, S.dscal, S.dflag, done); ++S.n_launch;
 }
