@@ -314,6 +314,41 @@ def run_large_bounded(args):
         return {"error": f"not finished within {args.large_timeout:g} s", "steps_completed": done}
 
 
+def run_friction(args, seed, ws, B, scenes, stream, flush):
+    """The eight-cube scene with the semi-implicit friction of appendix A
+    (mu_f = 0.5, eps_v = 1e-3 m/s, K_min = 6 as the paper uses with
+    friction), mixed precision: W warm-up steps, then each step timed with
+    CUDA events after the L2 flush, like the main line."""
+    import torch
+    s = scenes.eight_cubes(seed, precision=args.precision)
+    s.params.mu_f, s.params.eps_v, s.params.k_min = 0.5, 1e-3, 6
+    sim = B.Sim(s, stream=stream.cuda_stream)
+    W, K = max(args.warmup, 15), args.friction_steps  # from step 15 on the cubes are in contact
+    for _ in range(W):
+        sim.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    for i in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        _, st = sim.step(1)
+        ev[i][1].record(stream)
+        stats.append(st[0])
+    torch.cuda.synchronize()
+    sim.close()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    total = allmax(ws, sum(ms))
+    return {"workload": "the eight-cube scene (196,608 tets) with friction: mu_f = 0.5, eps_v = 1e-3 m/s, K_min = 6, "
+                        f"steps {W}..{W + K - 1} from rest, mixed precision",
+            "steps": K, "steps_per_s": allsum(ws, K) / (total / 1000.0), "unit": "steps/s",
+            "p50_step_ms": round(ms[len(ms) // 2], 3), "p99_step_ms": round(ms[-1], 3),
+            "mean_outer_iters": statistics.mean(x["outer_iters"] for x in stats),
+            "mean_cg_iters_per_step": statistics.mean(x["cg_iters"] for x in stats),
+            "mean_contacts": statistics.mean(x["n_contacts"] for x in stats)}
+
+
 def main():
     import faulthandler
     import signal
@@ -335,6 +370,8 @@ def main():
     ap.add_argument("--large-steps", type=int, default=20,
                     help="steps of the 2.3M-tet spiky-ball compression scene (0: skip)")
     ap.add_argument("--large-timeout", type=float, default=240.0)
+    ap.add_argument("--friction-steps", type=int, default=20,
+                    help="timed steps of the eight-cube scene with friction (0: skip)")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -516,6 +553,11 @@ def main():
         large = run_large_bounded(args)
         _progress(f"large: {large.get('steps_per_s')} steps/s")
 
+    friction = None
+    if args.friction_steps > 0:
+        friction = run_friction(args, seed, ws, B, scenes, stream, flush)
+        _progress(f"friction: {friction['steps_per_s']:.1f} steps/s")
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         v, n, el = oracle_sample(args.cpu_seconds, seed)
@@ -546,6 +588,7 @@ def main():
                 "batched_vs_plain_fp64": (batched["steps_per_s"] / plain["steps_per_s"]) if batched and plain
                 else None,
                 "large": large,
+                "friction": friction,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "bf.h"
+#include "bf_device.cuh"
 #include "bf_internal.cuh"
 
 struct bf_scene {
@@ -151,6 +152,23 @@ __global__ void k_scale(int n, double *__restrict__ out, const double *__restric
     if (i < n) out[i] = s * in[i];
 }
 
+// *out = |v| (grid sum)
+__global__ void k_norm(int n, const double *__restrict__ v, double *partials, unsigned *counter, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s[1] = {i < n ? v[i] * v[i] : 0.0}, tot[1];
+    if (grid_sum<1>(s, partials, counter, tot)) *out = sqrt(tot[0]);
+}
+
+// out = -in / |in| (zero for a zero vector)
+__global__ void k_neg_unit(int n, double *__restrict__ out, const double *__restrict__ in,
+                           const double *__restrict__ nrm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double g = *nrm;
+    if (i < n) out[i] = g > 0.0 ? -in[i] / g : 0.0;
+}
+
 __global__ void k_apply_targets(int nd, const int *__restrict__ ids, const double *__restrict__ tg,
                                 double *__restrict__ x)
 {
@@ -258,13 +276,19 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
         }
         int st = assemble(S, xtilde, xlin, xhat);
         if (st) return st;
-        k_scale<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, -1.0); ++S.n_launch;
+        // H p = -G solved for the unit right-hand side, p scaled back by |G|
+        // on the device: the FP32 products of the mixed-precision solve would
+        // underflow for a gradient at its rounding floor (a subproblem that
+        // starts at its optimum)
+        k_norm<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.grad, S.partials, S.counter, S.dscal + S_GNORM);
+        k_neg_unit<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, S.dscal + S_GNORM);
+        S.n_launch += 2;
         int it = 0, pending = 0;
         st = run_pcg_async(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it, &pending);
         if (st && st != BF_E_CG_MAXIT) return st;
         // L at xhat and at the full step queued behind the solve: one
         // synchronisation for the three
-        launch_axpy_to(S, S.xtmp, xhat, 1.0, S.pdir, n);
+        launch_axpy_scaled(S, S.xtmp, xhat, 1.0, S.pdir, S.dscal + S_GNORM, n);
         launch_energy(S, xtilde, xlin, xhat, S.dscal + S_E0);
         launch_energy(S, xtilde, xlin, S.xtmp, S.dscal + S_E1);
         const int sst = sync_flags(S);
@@ -284,7 +308,7 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
         bool ok = false;
         for (int j = 0; j <= S.prm.max_ls; ++j) {
             if (j > 0) {
-                launch_axpy_to(S, S.xtmp, xhat, r, S.pdir, n);
+                launch_axpy_scaled(S, S.xtmp, xhat, r, S.pdir, S.dscal + S_GNORM, n);
                 L1 = run_energy(S, xtilde, xlin, S.xtmp);
             }
             if (std::isfinite(L1) && L1 <= L0 + ls_tol) {

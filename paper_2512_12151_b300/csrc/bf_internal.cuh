@@ -30,7 +30,7 @@ enum { PT = 0, EE = 1 };
 enum {
     S_RZ = 0, S_BB, S_ALPHA, S_BETA, S_RR, S_PQ, S_E0, S_E1, S_MU, S_TOI, S_DOT, S_MAXDIAG,
     S_T_SPMV, S_T_RED1, S_T_UPD, S_T_RED2, S_RES = 16,  // S_RES..S_RES+23: reduction accumulators
-    S_T_STAGE = 40, S_T_ROWS, S_T_CONTACT,
+    S_T_STAGE = 40, S_T_ROWS, S_T_CONTACT, S_GNORM,
     S_NSCAL = 48
 };
 // device flag slots (dflag)
@@ -206,6 +206,9 @@ int pcg_finish(Scene &S, int *iters);
 void pcg_release(Scene &S);  // gives back the SM slots of a launched solve (error paths, destruction)
 int run_pcg_persistent(Scene &S, const double *b, double *x, double tol, int maxit, int *iters);
 void launch_axpy_to(Scene &S, double *out, const double *a, double r, const double *p, int n);
+// out = a + r * (*scale) * p, scale on the device
+void launch_axpy_scaled(Scene &S, double *out, const double *a, double r, const double *p, const double *scale,
+                        int n);
 void launch_blend(Scene &S, double *xk, const double *xh, double alpha, int n);
 void launch_velocity(Scene &S);
 

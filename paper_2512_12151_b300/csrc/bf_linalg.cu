@@ -418,6 +418,18 @@ void launch_axpy_to(Scene &S, double *out, const double *a, double r, const doub
     k_axpy_to<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, out, a, r, p); ++S.n_launch;
 }
 
+__global__ void k_axpy_scaled(int n, double *__restrict__ out, const double *__restrict__ a, double r,
+                              const double *__restrict__ p, const double *__restrict__ scale)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + r * (*scale * p[i]);
+}
+void launch_axpy_scaled(Scene &S, double *out, const double *a, double r, const double *p, const double *scale,
+                        int n)
+{
+    k_axpy_scaled<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, out, a, r, p, scale); ++S.n_launch;
+}
+
 // Eq. CCD-clamp: x^[k+1] = (1 - alpha) x^[k] + alpha xhat^[k+1]
 __global__ void k_blend(int n, double *__restrict__ xk, const double *__restrict__ xh, double alpha)
 {

@@ -496,59 +496,39 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     unsigned long long tA = 0, tA2 = 0, tB = 0, tB2 = 0, t0 = 0, tS = 0, tR = 0, tC = 0;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     __syncthreads();
-    // ---- init: |b|^2; then the solve for b / |b| (the FP32 products of a
-    // right-hand side near the rounding floor of a converged Newton
-    // iteration would underflow), r = b / |b|, x = 0, z = P r, p_old = 0;
-    // x is scaled back by |b| at the end -------------------------------------
+    // ---- init: r = b, x = 0, z = P r, p_old = 0 ------------------------------
     {
-        double acc[1] = {0.0};
+        Acc acc[2] = {};
         for (int i = threadIdx.x; i < nr; i += blockDim.x) {
             const int a = r0 + i;
+            RT rv[3];
+            double bb = 0.0;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const double bk = A.b[3 * a + k];
+                rv[k] = (RT)bk;
+                s_r[k * ld + i] = rv[k];
                 s_x[k * ld + i] = 0.0;
                 if (mixed) s_xl[k * ld + i] = RT(0);
                 qc[3 * a + k] = VT(0);
                 if (mixed) A.qd[3 * a + k] = 0.0;
                 if (A.nc > 0) pb[0][3 * a + k] = VT(0);
-                acc[0] += bk * bk;  // |b|^2 in FP64
-            }
-        }
-        if constexpr (mixed) {
-            AccF af[1];
-            af[0].add(acc[0]);
-            reduce(af, [&](const double *t) { ctl.bb = t[0]; });
-        } else {
-            reduce(acc, [&](const double *t) { ctl.bb = t[0]; });
-        }
-    }
-    // every CTA reads the same reduced bits, so all scale alike
-    const double bsc = ctl.bb > 0.0 && isfinite(ctl.bb) ? 1.0 / sqrt(ctl.bb) : 1.0;
-    {
-        Acc acc[1] = {};
-        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-            const int a = r0 + i;
-            RT rv[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                rv[k] = (RT)(A.b[3 * a + k] * bsc);
-                s_r[k * ld + i] = rv[k];
+                bb += bk * bk;  // |b|^2 in FP64
             }
             acc_add(acc[0], precond(i, rv));
+            acc_add(acc[1], bb);
         }
         reduce(acc, [&](const double *t) {
-            const double bb = ctl.bb;
             ctl.rz = t[0];
-            ctl.bb = bb * bsc * bsc;  // the scaled |b|^2 (1 up to rounding)
-            ctl.rr = ctl.bb;
-            ctl.rr_ref = ctl.bb;
+            ctl.bb = t[1];
+            ctl.rr = t[1];
+            ctl.rr_ref = t[1];
             ctl.beta = 0.0;
             ctl.bt = 0.f;
             ctl.it = 0;
             ctl.folds = 0;
-            if (bb > 0.0 && isfinite(bb) && isfinite(t[0])) ctl.state = PCG_RUN;
-            else ctl.state = bb == 0.0 ? PCG_DONE : PCG_BAD;
+            if (t[1] > 0.0 && isfinite(t[1]) && isfinite(t[0])) ctl.state = PCG_RUN;
+            else ctl.state = t[1] == 0.0 ? PCG_DONE : PCG_BAD;
         });
     }
     int parity = 0;
@@ -661,9 +641,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 if (!isfinite(pq)) {
                     ctl.state = PCG_BAD;
                 } else if (!(pq > 0.0)) {
-                    // no curvature left along p (its rounding at the noise floor of
-                    // a nearly zero right-hand side): stop with the current x, as
-                    // the per-phase solver does, and let the line search judge it
+                    // no curvature left along p: stop with the current x, as the
+                    // per-phase solver does, and let the line search judge it
                     ctl.state = PCG_DONE;
                 } else {
                     ctl.alpha = ctl.rz / pq;
@@ -788,7 +767,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 double rr = 0.0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const double rh = A.b[3 * a + k] * bsc - s_hx[k * ld + i] - __ldcg(A.qd + 3 * a + k);
+                    const double rh = A.b[3 * a + k] - s_hx[k * ld + i] - __ldcg(A.qd + 3 * a + k);
                     A.qd[3 * a + k] = 0.0;
                     rr += rh * rh;
                     rv[k] = (RT)rh;
@@ -815,15 +794,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     for (int i = threadIdx.x; i < nr; i += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            A.x[3 * (r0 + i) + k] = (s_x[k * ld + i] + (mixed ? (double)s_xl[k * ld + i] : 0.0)) / bsc;
+            A.x[3 * (r0 + i) + k] = s_x[k * ld + i] + (mixed ? (double)s_xl[k * ld + i] : 0.0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.dflag[F_ITERS] = ctl.it;
         A.dflag[F_MAXIT] = ctl.state == PCG_MAXIT;
         A.dflag[F_DONE] = 1;
         if (ctl.state == PCG_BAD) A.dflag[F_ERR] |= ERR_NONFINITE;
-        A.dscal[S_RR] = ctl.rr / (bsc * bsc);  // in the units of b
-        A.dscal[S_BB] = ctl.bb / (bsc * bsc);
-        A.dscal[S_RZ] = ctl.rz / (bsc * bsc);
+        A.dscal[S_RR] = ctl.rr;
+        A.dscal[S_BB] = ctl.bb;
+        A.dscal[S_RZ] = ctl.rz;
         A.dscal[S_T_SPMV] = 1e-6 * (double)tA;
         A.dscal[S_T_RED1] = 1e-6 * (double)tA2;
         A.dscal[S_T_UPD] = 1e-6 * (double)tB;
