@@ -31,7 +31,7 @@ class OrParams(C.Structure):
                 ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
                 ("eps_v", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
-                ("max_cg", C.c_int32), ("precision", C.c_int32)]
+                ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32)]
 
 
 class OrStats(C.Structure):
@@ -76,6 +76,12 @@ def lib():
         L.or_snh_pk1.argtypes = [_D, C.c_double, C.c_double, _D]
         L.or_snh_hess9.argtypes = [_D, C.c_double, C.c_double, _D]
         L.or_elem_grad_hess.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, C.c_int, _D, _D, _D]
+        L.or_elem_grad_hess_model.argtypes = [C.c_int, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, _D, _D,
+                                              _D]
+        L.or_cor_psi.restype = C.c_double
+        L.or_cor_psi.argtypes = [_D, C.c_double, C.c_double]
+        L.or_cor_pk1.argtypes = [_D, C.c_double, C.c_double, _D]
+        L.or_cor_hess9.argtypes = [_D, C.c_double, C.c_double, _D]
         L.or_pair_dist_grad.argtypes = [C.c_int, _D, _D]
     return _lib
 
@@ -121,6 +127,22 @@ def snh_hess9(F, mu, lam):
     return H.reshape(9, 9)
 
 
+def cor_psi(F, mu, lam):
+    return lib().or_cor_psi(_p(_f64(F, 9)), mu, lam)
+
+
+def cor_pk1(F, mu, lam):
+    P = np.zeros(9)
+    lib().or_cor_pk1(_p(_f64(F, 9)), mu, lam, _p(P))
+    return P.reshape(3, 3)
+
+
+def cor_hess9(F, mu, lam):
+    H = np.zeros(81)
+    lib().or_cor_hess9(_p(_f64(F, 9)), mu, lam, _p(H))
+    return H.reshape(9, 9)
+
+
 def sym_eig(A):
     A = _f64(A)
     n = A.shape[0]
@@ -143,11 +165,11 @@ def elem_F(x12, B):
     return F.reshape(3, 3)
 
 
-def elem_grad_hess(x12, B, vol, mu, lam, project=True):
+def elem_grad_hess(x12, B, vol, mu, lam, project=True, model=0):
     psi = C.c_double()
     g, H = np.zeros(12), np.zeros(144)
-    lib().or_elem_grad_hess(_p(_f64(x12, 12)), _p(_f64(B, 9)), vol, mu, lam, int(project),
-                            C.byref(psi), _p(g), _p(H))
+    lib().or_elem_grad_hess_model(int(model), _p(_f64(x12, 12)), _p(_f64(B, 9)), vol, mu, lam, int(project),
+                                  C.byref(psi), _p(g), _p(H))
     return psi.value, g, H.reshape(12, 12)
 
 
@@ -187,6 +209,7 @@ def params_struct(p) -> OrParams:
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.precision = p.precision
+    s.model = p.model
     return s
 
 

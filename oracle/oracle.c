@@ -224,6 +224,140 @@ void or_psd_project(int n, const double *A, double *Ap)
     free(Q);
 }
 
+/* ------------------------------------------------------------------ */
+/* Corotated linear elasticity (COR, one of the models of Tab. 2;       */
+/* McAdams et al. 2011): Psi = mu |F - R|^2 + lam/2 (tr(S) - 3)^2 with  */
+/* F = R S the polar decomposition (R a rotation also for inverted F:   */
+/* the rotation-variant SVD F = U diag(s) V^T, U and V rotations, s_2   */
+/* negative when det F < 0), lam the Lame constant (no shift: the small  */
+/* strain limit is linear elasticity as it stands).                     */
+/* ------------------------------------------------------------------ */
+static void rot_svd(const double F[9], double U[9], double s[3], double V[9])
+{
+    /* V, s^2 from F^T F (descending); U = F V / s, completed to a rotation */
+    double FtF[9], w[3], Q[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double t = 0.0;
+            for (int r = 0; r < 3; ++r) t += F[3 * r + a] * F[3 * r + b];
+            FtF[3 * a + b] = t;
+        }
+    or_sym_eig(3, FtF, w, Q); /* unordered; Q columns */
+    int ord[3] = {0, 1, 2};   /* descending eigenvalues */
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (w[ord[j]] > w[ord[i]]) { int t = ord[i]; ord[i] = ord[j]; ord[j] = t; }
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) V[3 * r + k] = Q[3 * r + ord[k]];
+    if (det3(V) < 0.0)
+        for (int r = 0; r < 3; ++r) V[3 * r + 2] = -V[3 * r + 2];
+    double u[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) {
+            double t = 0.0;
+            for (int c = 0; c < 3; ++c) t += F[3 * r + c] * V[3 * c + k];
+            u[k][r] = t; /* F v_k */
+        }
+    double n0 = sqrt(dot3(u[0], u[0]));
+    for (int r = 0; r < 3; ++r) u[0][r] = n0 > 0.0 ? u[0][r] / n0 : (r == 0 ? 1.0 : 0.0);
+    double p = dot3(u[0], u[1]);
+    for (int r = 0; r < 3; ++r) u[1][r] -= p * u[0][r];
+    double n1 = sqrt(dot3(u[1], u[1]));
+    if (n1 > 1e-300) {
+        for (int r = 0; r < 3; ++r) u[1][r] /= n1;
+    } else { /* any unit vector orthogonal to u0 */
+        double e[3] = {0, 0, 0};
+        e[fabs(u[0][0]) < 0.9 ? 0 : 1] = 1.0;
+        double t = dot3(e, u[0]);
+        for (int r = 0; r < 3; ++r) u[1][r] = e[r] - t * u[0][r];
+        double nn = sqrt(dot3(u[1], u[1]));
+        for (int r = 0; r < 3; ++r) u[1][r] /= nn;
+    }
+    double u2[3];
+    cross3(u[0], u[1], u2);
+    for (int r = 0; r < 3; ++r) {
+        U[3 * r + 0] = u[0][r];
+        U[3 * r + 1] = u[1][r];
+        U[3 * r + 2] = u2[r];
+    }
+    /* s_k = u_k^T F v_k (s_2 carries the sign of det F) */
+    for (int k = 0; k < 3; ++k) {
+        double t = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) t += U[3 * r + k] * F[3 * r + c] * V[3 * c + k];
+        s[k] = t;
+    }
+}
+
+double or_cor_psi(const double F[9], double mu, double lam)
+{
+    double U[9], s[3], V[9];
+    rot_svd(F, U, s, V);
+    double e = 0.0, tr = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        e += (s[k] - 1.0) * (s[k] - 1.0);
+        tr += s[k];
+    }
+    return mu * e + 0.5 * lam * (tr - 3.0) * (tr - 3.0); /* |F - R|^2 = |diag(s) - I|^2 */
+}
+
+/* R = U V^T and tr(S) = sum s */
+static double cor_rotation(const double F[9], double R[9], double U[9], double s[3], double V[9])
+{
+    rot_svd(F, U, s, V);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += U[3 * r + k] * V[3 * c + k];
+            R[3 * r + c] = t;
+        }
+    return s[0] + s[1] + s[2];
+}
+
+void or_cor_pk1(const double F[9], double mu, double lam, double P[9])
+{
+    double R[9], U[9], s[3], V[9];
+    double tr = cor_rotation(F, R, U, s, V);
+    for (int k = 0; k < 9; ++k) P[k] = 2.0 * mu * (F[k] - R[k]) + lam * (tr - 3.0) * R[k];
+}
+
+/* d2Psi/dF2 = 2 mu (I - dR/dF) + lam vec(R) vec(R)^T + lam (tr S - 3) dR/dF,
+ * with the derivative of the polar rotation: for dF, W = U^T dR V is skew
+ * with W_ij = ((U^T dF V)_ij - (U^T dF V)_ji) / (s_i + s_j). */
+void or_cor_hess9(const double F[9], double mu, double lam, double H[81])
+{
+    double R[9], U[9], s[3], V[9];
+    double tr = cor_rotation(F, R, U, s, V);
+    memset(H, 0, 81 * sizeof(double));
+    for (int col = 0; col < 9; ++col) { /* dF = E_ab, vec index a + 3 b */
+        int a = col % 3, b = col / 3;
+        double Fh[3][3], W[3][3] = {{0}}, dR[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Fh[i][j] = U[3 * a + i] * V[3 * b + j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j) {
+                double w = (Fh[i][j] - Fh[j][i]) / (s[i] + s[j]);
+                W[i][j] = w;
+                W[j][i] = -w;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double t = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) t += U[3 * r + i] * W[i][j] * V[3 * c + j];
+                dR[3 * r + c] = t;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                int row = r + 3 * c;
+                double v = -2.0 * mu * dR[3 * r + c] + lam * (tr - 3.0) * dR[3 * r + c];
+                if (row == col) v += 2.0 * mu;
+                v += lam * R[3 * r + c] * R[3 * a + b];
+                H[9 * row + col] = v;
+            }
+    }
+}
+
 /* F = Ds Dm^-1 with Ds = [x1 - x0, x2 - x0, x3 - x0] (section 3). */
 void or_elem_F(const double x[12], const double B[9], double F[9])
 {
@@ -255,12 +389,19 @@ static void elem_A(const double B[9], double A[4][3])
 void or_elem_grad_hess(const double x[12], const double B[9], double vol, double mu, double lam,
                        int project, double *psi, double g[12], double H[144])
 {
+    or_elem_grad_hess_model(0, x, B, vol, mu, lam, project, psi, g, H);
+}
+
+void or_elem_grad_hess_model(int model, const double x[12], const double B[9], double vol, double mu, double lam,
+                             int project, double *psi, double g[12], double H[144])
+{
     double F[9], P[9], H9[81], H9p[81], A[4][3];
     or_elem_F(x, B, F);
     elem_A(B, A);
-    if (psi) *psi = vol * or_snh_psi(F, mu, lam);
+    if (psi) *psi = vol * (model == 1 ? or_cor_psi(F, mu, lam) : or_snh_psi(F, mu, lam));
     if (g) {
-        or_snh_pk1(F, mu, lam, P);
+        if (model == 1) or_cor_pk1(F, mu, lam, P);
+        else or_snh_pk1(F, mu, lam, P);
         for (int i = 0; i < 4; ++i)
             for (int r = 0; r < 3; ++r) {
                 double s = 0.0;
@@ -269,7 +410,8 @@ void or_elem_grad_hess(const double x[12], const double B[9], double vol, double
             }
     }
     if (H) {
-        or_snh_hess9(F, mu, lam, H9);
+        if (model == 1) or_cor_hess9(F, mu, lam, H9);
+        else or_snh_hess9(F, mu, lam, H9);
         if (project) or_psd_project(9, H9, H9p);
         else memcpy(H9p, H9, sizeof(H9p));
         for (int i = 0; i < 4; ++i)
@@ -634,6 +776,7 @@ or_scene *or_create(int32_t nv, const double *rest, const double *x0, const doub
         S->vol[e] = det3(Dm) / 6.0;
         const double *m = S->mats + 3 * S->tmat[e];
         or_lame(m[0], m[1], &S->emu[e], &S->elam[e]);
+        if (prm->model == 1) S->elam[e] -= S->emu[e]; /* COR: the Lame constant itself */
         for (int k = 0; k < 4; ++k) S->mass[t[k]] += m[2] * S->vol[e] / 4.0;
     }
     for (int v = 0; v < nv; ++v)
@@ -844,7 +987,7 @@ static double assemble_elastic(or_scene *S, const double *xtilde, const double *
         double x12[12], g[12], H[144], psi;
         const int *t = S->tets + 4 * e;
         gather12(xhat, t, x12);
-        or_elem_grad_hess(x12, S->B + 9 * e, S->vol[e], S->emu[e], S->elam[e], 1, &psi, g, H);
+        or_elem_grad_hess_model(S->p.model, x12, S->B + 9 * e, S->vol[e], S->emu[e], S->elam[e], 1, &psi, g, H);
         energy += h2 * psi;
         for (int i = 0; i < 4; ++i) {
             for (int c = 0; c < 3; ++c) S->grad[3 * t[i] + c] += h2 * g[3 * i + c];
@@ -1234,7 +1377,7 @@ double or_energy_L(or_scene *S, const double *xtilde, const double *xlin, const 
         double x12[12], F[9];
         gather12(xhat, S->tets + 4 * e, x12);
         or_elem_F(x12, S->B + 9 * e, F);
-        L += h2 * S->vol[e] * or_snh_psi(F, S->emu[e], S->elam[e]);
+        L += h2 * S->vol[e] * (S->p.model == 1 ? or_cor_psi(F, S->emu[e], S->elam[e]) : or_snh_psi(F, S->emu[e], S->elam[e]));
     }
     for (int i = 0; i < S->nc; ++i) {
         double cs = constraint_c(S, i, xlin, xhat) - sfix[i];

@@ -35,7 +35,7 @@ extern "C" {
 
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
-    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision;
+    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model; /* model: 0 SNH, 1 COR */
 } or_params;
 
 typedef struct {
@@ -55,6 +55,14 @@ void or_elem_F(const double x[12], const double B[9], double F[9]);
 void or_elem_grad_hess(const double x[12], const double B[9], double vol, double mu, double lam,
                        int project, double *psi, double g[12], double H[144]);
 void or_lame(double E, double nu, double *mu, double *lam);
+/* corotated linear elasticity (COR, Tab. 2) */
+double or_cor_psi(const double F[9], double mu, double lam);
+void or_cor_pk1(const double F[9], double mu, double lam, double P[9]);
+void or_cor_hess9(const double F[9], double mu, double lam, double H[81]);
+/* element energy, gradient and (projected) Hessian of material model
+ * model (0 SNH, 1 COR); or_elem_grad_hess is model 0 */
+void or_elem_grad_hess_model(int model, const double x[12], const double B[9], double vol, double mu, double lam,
+                             int project, double *psi, double g[12], double H[144]);
 
 /* ---- distances and CCD (section 4.2, section 5.1) ---- */
 double or_pt_dist2(const double p[3], const double a[3], const double b[3], const double c[3]);
