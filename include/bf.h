@@ -82,10 +82,13 @@ typedef struct {
  * s_ccd is the ACCD conservative rescaling (target gap s_ccd * d(x0)).
  * mu_f and eps_v [m/s] are the friction coefficient and the velocity
  * threshold of the smoothed semi-implicit friction of appendix A (mu_f = 0:
- * no friction; the paper uses k_min = 6 with friction). */
+ * no friction; the paper uses k_min = 6 with friction).  model selects the
+ * material of every tet: BF_MODEL_SNH (stable Neo-Hookean, section 3) or
+ * BF_MODEL_COR (corotated linear, one of the models of Tab. 2). */
+enum { BF_MODEL_SNH = 0, BF_MODEL_COR = 1 };
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
-    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision;
+    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model;
 } bf_params;
 
 /* Per-time-step statistics (the columns of Tab. 1 / Tab. 2). */

@@ -463,7 +463,8 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     if (nv >= (1 << 21) || nt >= (1 << 29)) return BF_E_ARG;  // triangle keys pack 3 vertex ids of 21 bits
     if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
         prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
-        prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)))
+        prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)) ||
+        (prm->model != BF_MODEL_SNH && prm->model != BF_MODEL_COR))
         return BF_E_ARG;
     S.nv = nv;
     S.nt = nt;
@@ -505,7 +506,8 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         const double E = m->mats[3 * mi], nu = m->mats[3 * mi + 1], rho = m->mats[3 * mi + 2];
         if (!(E > 0) || !(nu > -1 && nu < 0.5) || !(rho > 0)) return BF_E_ARG;
         emu[e] = E / (2.0 * (1.0 + nu));
-        elam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) + emu[e];
+        elam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));  // COR: the Lame constant
+        if (prm->model == BF_MODEL_SNH) elam[e] += emu[e];      // SNH: shifted (linear small-strain limit)
         for (int k = 0; k < 4; ++k) mass[t[k]] += rho * vol[e] / 4.0;
     }
     for (int v = 0; v < nv; ++v) {

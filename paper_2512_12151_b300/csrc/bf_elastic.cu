@@ -155,8 +155,14 @@ __device__ __forceinline__ void atomic_add_val(double *p, double v) { atomicAdd(
 __device__ __forceinline__ void atomic_add_val(float *p, double v) { atomicAdd(p, (float)v); }
 
 // Per-tet gradient and PSD Hessian; HT is the Hessian arithmetic type and
-// MT the storage type of the block values.
-template <class HT, class MT>
+// MT the storage type of the block values.  MODEL BF_MODEL_COR: the
+// corotated energy Psi = mu |F - R|^2 + lam/2 (tr S - 3)^2 (F = R S, R from
+// the rotation-variant SVD), P = 2 mu (F - R) + lam (tr S - 3) R in FP64
+// (its own FP64 SVD); in the SVD frame its Hessian has the scaling block
+// 2 mu I + lam 1 1^T (PSD for lam >= 0), flip eigenvalues 2 mu and twist
+// eigenvalues (Psi_p + Psi_q) / (s_p + s_q) with Psi_p = 2 mu (s_p - 1) +
+// lam (tr S - 3), the same assembly as SNH's.
+template <class HT, class MT, int MODEL>
 __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict__ tets, const double *__restrict__ Bm,
                                                  const double *__restrict__ vol, const double *__restrict__ emu,
                                                  const double *__restrict__ elam, const uint8_t *__restrict__ dir,
@@ -191,6 +197,62 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         A[3][c] = B[6 + c];
         A[0][c] = -(B[c] + B[3 + c] + B[6 + c]);
     }
+    HT Ft[3][3], U[3][3], s[3], V[3][3];
+    const HT muT = (HT)mu, lamT = (HT)lam;
+    HT c1[3][3], c2[3][3], S3[3][3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            c1[p][q] = HT(0);
+            c2[p][q] = HT(0);
+        }
+    if constexpr (MODEL == BF_MODEL_COR) {
+        double Ud[3][3], sd[3], Vd[3][3], R[3][3];
+        svd3<double>(F, Ud, sd, Vd);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) R[r][c] = Ud[r][0] * Vd[c][0] + Ud[r][1] * Vd[c][1] + Ud[r][2] * Vd[c][2];
+        const double trm3 = sd[0] + sd[1] + sd[2] - 3.0;
+        const double sc = h2 * V0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (dir[vid[i]]) continue;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                double g = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g += (2.0 * mu * (F[r][c] - R[r][c]) + lam * trm3 * R[r][c]) * A[i][c];
+                atomicAdd(grad + 3 * vid[i] + r, sc * g);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            s[r] = (HT)sd[r];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                U[r][c] = (HT)Ud[r][c];
+                V[r][c] = (HT)Vd[r][c];
+            }
+        }
+        const HT t3 = (HT)trm3;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            const int p = kk == 0 ? 1 : 0, q = kk == 2 ? 1 : 2;
+            const HT den = s[p] + s[q];
+            const HT num = HT(2) * muT * (s[p] + s[q] - HT(2)) + HT(2) * lamT * t3;
+            HT wt = den > HT(1e-30) || den < HT(-1e-30) ? num / den : HT(0);
+            HT wf = HT(2) * muT;
+            wt = wt > HT(0) ? wt : HT(0);
+            c1[p][q] = c1[q][p] = HT(0.5) * (wt + wf);
+            c2[p][q] = c2[q][p] = HT(0.5) * (wf - wt);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) S3[p][q] = lamT + (p == q ? HT(2) * muT : HT(0));
+    } else {
     // ---- gradient (FP64) ----
     {
         double C[3][3];  // cofactor: columns f1 x f2, f2 x f0, f0 x f1
@@ -218,24 +280,14 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         }
     }
     // ---- PSD Hessian in HT ----
-    HT Ft[3][3], U[3][3], s[3], V[3][3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) Ft[r][c] = (HT)F[r][c];
     svd3<HT>(Ft, U, s, V);
-    const HT muT = (HT)mu, lamT = (HT)lam;
     const HT J = s[0] * s[1] * s[2];
     const HT kap = lamT * (J - HT(1)) - muT;
     // twist / flip pairs: (0,1) third 2, (0,2) third 1, (1,2) third 0
-    HT c1[3][3], c2[3][3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            c1[p][q] = HT(0);
-            c2[p][q] = HT(0);
-        }
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
         const int p = kk == 0 ? 1 : 0, q = kk == 2 ? 1 : 2;
@@ -246,7 +298,6 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         c2[p][q] = c2[q][p] = HT(0.5) * (wf - wt);
     }
     // scaling block A3 = mu I + kap [[0 s2 s1][s2 0 s0][s1 s0 0]] + lam g g^T, PSD-projected
-    HT S3[3][3];
     {
         const HT g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
         HT A3[3][3];
@@ -266,6 +317,7 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
                 S3[p][q] = acc;
             }
     }
+    }  // model
     // a_i' = V^T A_i'
     HT a[4][3];
 #pragma unroll
@@ -321,16 +373,17 @@ void launch_elastic(Scene &S, const double *xhat)
     const double h2 = S.prm.dt * S.prm.dt;
     ScopedTimer tm(S, T_ELASTIC);
     const int nb = cdiv(S.nt, 128);
-    if (S.prm.precision == BF_PREC_MIXED)
-        {
-            k_elastic<float, float><<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2,
-                                                          S.grad, S.valf, S.nnzb, S.tblk); ++S.n_launch;
-        }
-    else
-        {
-            k_elastic<double, double><<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat,
-                                                            h2, S.grad, S.val, S.nnzb, S.tblk); ++S.n_launch;
-        }
+    const bool cor = S.prm.model == BF_MODEL_COR;
+    if (S.prm.precision == BF_PREC_MIXED) {
+        auto kern = cor ? k_elastic<float, float, BF_MODEL_COR> : k_elastic<float, float, BF_MODEL_SNH>;
+        kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.valf,
+                                       S.nnzb, S.tblk);
+    } else {
+        auto kern = cor ? k_elastic<double, double, BF_MODEL_COR> : k_elastic<double, double, BF_MODEL_SNH>;
+        kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.val,
+                                       S.nnzb, S.tblk);
+    }
+    ++S.n_launch;
 }
 
 // inertia gradient M (xhat - x~) and mass on the diagonal blocks; prescribed
@@ -426,7 +479,7 @@ void launch_xtilde(Scene &S, double *xtilde)
 // Reduced deterministically.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_energy(
-    int nv, int nt, int nc, const double *__restrict__ mass, const uint8_t *__restrict__ dir,
+    int nv, int nt, int nc, int model, const double *__restrict__ mass, const uint8_t *__restrict__ dir,
     const double *__restrict__ xt, const double *__restrict__ xh, const int4 *__restrict__ tets,
     const double *__restrict__ Bm, const double *__restrict__ vol, const double *__restrict__ emu,
     const double *__restrict__ elam, double h2, const int4 *__restrict__ cv, const double *__restrict__ cd,
@@ -470,7 +523,24 @@ __global__ void __launch_bounds__(kThreads) k_energy(
         const double J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
                          F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
         const double m = emu[t], l = elam[t];
-        e = h2 * vol[t] * (0.5 * m * (I2 - 3.0) - m * (J - 1.0) + 0.5 * l * (J - 1.0) * (J - 1.0));
+        if (model == BF_MODEL_COR) {  // singular values from F^T F, the smallest signed by det F
+            double C2[3][3], w[3], Q[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) C2[a][b] = F[0][a] * F[0][b] + F[1][a] * F[1][b] + F[2][a] * F[2][b];
+            sym3_eig<double>(C2, w, Q);
+            double sv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sv[a] = sqrt(w[a] > 0.0 ? w[a] : 0.0);
+            const int lo = sv[0] <= sv[1] ? (sv[0] <= sv[2] ? 0 : 2) : (sv[1] <= sv[2] ? 1 : 2);
+            if (J < 0.0) sv[lo] = -sv[lo];
+            const double tr = sv[0] + sv[1] + sv[2];
+            e = h2 * vol[t] * (m * ((sv[0] - 1.0) * (sv[0] - 1.0) + (sv[1] - 1.0) * (sv[1] - 1.0) +
+                                    (sv[2] - 1.0) * (sv[2] - 1.0)) + 0.5 * l * (tr - 3.0) * (tr - 3.0));
+        } else {
+            e = h2 * vol[t] * (0.5 * m * (I2 - 3.0) - m * (J - 1.0) + 0.5 * l * (J - 1.0) * (J - 1.0));
+        }
     } else if (tid < (long long)nv + nt + nc) {
         const int i = (int)(tid - nv - nt);
         const int4 v4 = cv[i];
@@ -496,7 +566,8 @@ void launch_energy(Scene &S, const double *xtilde, const double *xlin, const dou
     const long long nthr = (long long)S.nv + S.nt + S.nc + S.nf;
     const int nb = cdiv(nthr, kThreads);
     ScopedTimer tm(S, T_ENERGY);
-    k_energy<<<nb, kThreads, 0, S.stream>>>(S.nv, S.nt, S.nc, S.mass, S.dir, xtilde, xhat, S.tets, S.B, S.vol, S.emu,
+    k_energy<<<nb, kThreads, 0, S.stream>>>(S.nv, S.nt, S.nc, S.prm.model, S.mass, S.dir, xtilde, xhat, S.tets, S.B,
+                                            S.vol, S.emu,
                                             S.elam, S.prm.dt * S.prm.dt, S.cv, S.cd, S.cg, S.clam, S.cgam, S.cs, xlin,
                                             S.mu, S.delta, S.nf, S.fv, S.fw, S.fn, S.fk, S.fx0,
                                             S.prm.dt * S.prm.eps_v, S.partials, S.counter, out);
