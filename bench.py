@@ -314,16 +314,15 @@ def run_large_bounded(args):
         return {"error": f"not finished within {args.large_timeout:g} s", "steps_completed": done}
 
 
-def run_friction(args, seed, ws, B, scenes, stream, flush):
-    """The eight-cube scene with the semi-implicit friction of appendix A
-    (mu_f = 0.5, eps_v = 1e-3 m/s, K_min = 6 as the paper uses with
-    friction), mixed precision: W warm-up steps, then each step timed with
-    CUDA events after the L2 flush, like the main line."""
+def run_variant(args, seed, ws, B, scenes, stream, flush, workload, K, W, **params):
+    """The eight-cube scene with modified parameters (friction, material),
+    mixed precision: W warm-up steps, then each step timed with CUDA events
+    after the L2 flush, like the main line."""
     import torch
     s = scenes.eight_cubes(seed, precision=args.precision)
-    s.params.mu_f, s.params.eps_v, s.params.k_min = 0.5, 1e-3, 6
+    for k, v in params.items():
+        setattr(s.params, k, v)
     sim = B.Sim(s, stream=stream.cuda_stream)
-    W, K = max(args.warmup, 15), args.friction_steps  # from step 15 on the cubes are in contact
     for _ in range(W):
         sim.step(1)
     torch.cuda.synchronize()
@@ -340,8 +339,7 @@ def run_friction(args, seed, ws, B, scenes, stream, flush):
     sim.close()
     ms = sorted(a.elapsed_time(b) for a, b in ev)
     total = allmax(ws, sum(ms))
-    return {"workload": "the eight-cube scene (196,608 tets) with friction: mu_f = 0.5, eps_v = 1e-3 m/s, K_min = 6, "
-                        f"steps {W}..{W + K - 1} from rest, mixed precision",
+    return {"workload": f"{workload}, steps {W}..{W + K - 1} from rest, mixed precision",
             "steps": K, "steps_per_s": allsum(ws, K) / (total / 1000.0), "unit": "steps/s",
             "p50_step_ms": round(ms[len(ms) // 2], 3), "p99_step_ms": round(ms[-1], 3),
             "mean_outer_iters": statistics.mean(x["outer_iters"] for x in stats),
@@ -372,6 +370,8 @@ def main():
     ap.add_argument("--large-timeout", type=float, default=240.0)
     ap.add_argument("--friction-steps", type=int, default=20,
                     help="timed steps of the eight-cube scene with friction (0: skip)")
+    ap.add_argument("--cor-steps", type=int, default=20,
+                    help="timed steps of the eight-cube scene with the corotated material (0: skip)")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -553,10 +553,18 @@ def main():
         large = run_large_bounded(args)
         _progress(f"large: {large.get('steps_per_s')} steps/s")
 
-    friction = None
-    if args.friction_steps > 0:
-        friction = run_friction(args, seed, ws, B, scenes, stream, flush)
+    friction = cor = None
+    if args.friction_steps > 0:  # from step 15 on the cubes are in contact
+        friction = run_variant(args, seed, ws, B, scenes, stream, flush,
+                               "the eight-cube scene (196,608 tets) with the friction of appendix A: mu_f = 0.5, "
+                               "eps_v = 1e-3 m/s, K_min = 6", args.friction_steps, max(args.warmup, 15),
+                               mu_f=0.5, eps_v=1e-3, k_min=6)
         _progress(f"friction: {friction['steps_per_s']:.1f} steps/s")
+    if args.cor_steps > 0:
+        cor = run_variant(args, seed, ws, B, scenes, stream, flush,
+                          "the eight-cube scene (196,608 tets) with the corotated material (COR)", args.cor_steps,
+                          max(args.warmup, 15), model=1)
+        _progress(f"cor: {cor['steps_per_s']:.1f} steps/s")
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
@@ -589,6 +597,7 @@ def main():
                 else None,
                 "large": large,
                 "friction": friction,
+                "cor": cor,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "
