@@ -66,7 +66,7 @@ def lib():
         L.or_create.argtypes = [C.c_int32, _D, _D, _D, C.c_int32, _I, _I, C.c_int32, _D, C.c_int32, _I,
                                 C.POINTER(C.c_uint8), C.POINTER(OrParams)]
         L.or_destroy.argtypes = [C.c_void_p]
-        for name in ("or_get_mu", "or_mu_init", "or_assemble", "or_energy_L", "or_max_step_size"):
+        for name in ("or_get_mu", "or_mu_init", "or_assemble", "or_energy_L", "or_max_step_size", "or_inversion_step"):
             getattr(L, name).restype = C.c_double
         L.or_set_mu_delta.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.or_pcg.argtypes = [C.c_void_p, _D, _D, C.c_double, C.c_int32]
@@ -82,6 +82,13 @@ def lib():
         L.or_cor_psi.argtypes = [_D, C.c_double, C.c_double]
         L.or_cor_pk1.argtypes = [_D, C.c_double, C.c_double, _D]
         L.or_cor_hess9.argtypes = [_D, C.c_double, C.c_double, _D]
+        L.or_nh_psi.restype = C.c_double
+        L.or_nh_psi.argtypes = [_D, C.c_double, C.c_double]
+        L.or_nh_pk1.argtypes = [_D, C.c_double, C.c_double, _D]
+        L.or_nh_hess9.argtypes = [_D, C.c_double, C.c_double, _D]
+        L.or_cubic_first_root.restype = C.c_double
+        L.or_cubic_first_root.argtypes = [_D]
+        L.or_det_cubic.argtypes = [_D, _D, C.c_double, _D]
         L.or_pair_dist_grad.argtypes = [C.c_int, _D, _D]
     return _lib
 
@@ -141,6 +148,34 @@ def cor_hess9(F, mu, lam):
     H = np.zeros(81)
     lib().or_cor_hess9(_p(_f64(F, 9)), mu, lam, _p(H))
     return H.reshape(9, 9)
+
+
+def nh_psi(F, mu, lam):
+    return lib().or_nh_psi(_p(_f64(F, 9)), mu, lam)
+
+
+def nh_pk1(F, mu, lam):
+    P = np.zeros(9)
+    lib().or_nh_pk1(_p(_f64(F, 9)), mu, lam, _p(P))
+    return P.reshape(3, 3)
+
+
+def nh_hess9(F, mu, lam):
+    H = np.zeros(81)
+    lib().or_nh_hess9(_p(_f64(F, 9)), mu, lam, _p(H))
+    return H.reshape(9, 9)
+
+
+def cubic_first_root(c):
+    """smallest root in (0, 1] of c0 + c1 t + c2 t^2 + c3 t^3 (c0 > 0), else 1"""
+    return lib().or_cubic_first_root(_p(_f64(c, 4)))
+
+
+def det_cubic(A, B, s):
+    """coefficients (c0..c3) of det(A + t B) - s det(A)"""
+    c = np.zeros(4)
+    lib().or_det_cubic(_p(_f64(A, 9)), _p(_f64(B, 9)), s, _p(c))
+    return c
 
 
 def sym_eig(A):
@@ -360,6 +395,10 @@ class Oracle:
 
     def max_step_size(self, x0, x1):
         return lib().or_max_step_size(C.c_void_p(self.h), _p(_f64(x0)), _p(_f64(x1)))
+
+    def inversion_step(self, x0, x1):
+        """the inversion bound of MaxStepSize over x0 -> x1 (any model)"""
+        return lib().or_inversion_step(C.c_void_p(self.h), _p(_f64(x0)), _p(_f64(x1)))
 
     def min_distance(self, x):
         d = C.c_double()

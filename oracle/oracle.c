@@ -358,6 +358,117 @@ void or_cor_hess9(const double F[9], double mu, double lam, double H[81])
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Neo-Hookean (NH, one of the models of Tab. 2):                         */
+/* Psi = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2, lam the Lame        */
+/* constant.  It is undefined for J <= 0 (the paper's example of a        */
+/* non-invertible material, section 4.1); the energy is +inf there, so a  */
+/* line search backtracks out of inverted states.                         */
+/* ------------------------------------------------------------------ */
+double or_nh_psi(const double F[9], double mu, double lam)
+{
+    double J = det3(F);
+    if (!(J > 0.0)) return INFINITY;
+    double I2 = 0.0;
+    for (int k = 0; k < 9; ++k) I2 += F[k] * F[k];
+    double L = log(J);
+    return 0.5 * mu * (I2 - 3.0) - mu * L + 0.5 * lam * L * L;
+}
+
+/* P = mu (F - F^-T) + lam ln J F^-T */
+void or_nh_pk1(const double F[9], double mu, double lam, double P[9])
+{
+    double Fi[9];
+    inv3(F, Fi);
+    double L = log(det3(F));
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double fit = Fi[3 * c + r]; /* (F^-T)_rc */
+            P[3 * r + c] = mu * (F[3 * r + c] - fit) + lam * L * fit;
+        }
+}
+
+/* d2Psi / dF_ij dF_kl = mu d_ik d_jl + (mu - lam ln J) (F^-1)_jk (F^-1)_li
+ *                       + lam (F^-T)_ij (F^-T)_kl,
+ * from d(F^-1) = -F^-1 dF F^-1 and d(ln J) = F^-T : dF. */
+void or_nh_hess9(const double F[9], double mu, double lam, double H[81])
+{
+    double Fi[9];
+    inv3(F, Fi);
+    double L = log(det3(F));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double v = (mu - lam * L) * Fi[3 * j + k] * Fi[3 * l + i] + lam * Fi[3 * j + i] * Fi[3 * l + k];
+                    if (i == k && j == l) v += mu;
+                    H[9 * (i + 3 * j) + (k + 3 * l)] = v;
+                }
+}
+
+/* Smallest root in (0, 1] of p(t) = c0 + c1 t + c2 t^2 + c3 t^3 with
+ * p(0) = c0 > 0; returns 1 when p stays positive on [0, 1].  The real
+ * roots of p' split [0, 1] into pieces on which p is monotone; the first
+ * piece whose right end has p <= 0 holds the root, which bisection brackets
+ * to adjacent doubles.  The returned t is the bracket's left end (p > 0). */
+double or_cubic_first_root(const double c[4])
+{
+    if (!(c[0] > 0.0)) return 0.0;
+    double br[4];
+    int nb = 0;
+    br[nb++] = 0.0;
+    /* critical points: 3 c3 t^2 + 2 c2 t + c1 = 0 */
+    double qa = 3.0 * c[3], qb = 2.0 * c[2], qc = c[1], crit[2];
+    int nc = 0;
+    if (qa != 0.0) {
+        double disc = qb * qb - 4.0 * qa * qc;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            crit[nc++] = (-qb - sq) / (2.0 * qa);
+            crit[nc++] = (-qb + sq) / (2.0 * qa);
+        }
+    } else if (qb != 0.0) {
+        crit[nc++] = -qc / qb;
+    }
+    if (nc == 2 && crit[0] > crit[1]) { double t = crit[0]; crit[0] = crit[1]; crit[1] = t; }
+    for (int k = 0; k < nc; ++k)
+        if (crit[k] > 0.0 && crit[k] < 1.0) br[nb++] = crit[k];
+    br[nb++] = 1.0;
+    for (int k = 0; k + 1 < nb; ++k) {
+        double lo = br[k], hi = br[k + 1];
+        double phi = c[0] + hi * (c[1] + hi * (c[2] + hi * c[3]));
+        if (phi > 0.0) continue;
+        for (;;) {
+            double mid = 0.5 * (lo + hi);
+            if (!(mid > lo && mid < hi)) break;
+            double pm = c[0] + mid * (c[1] + mid * (c[2] + mid * c[3]));
+            if (pm > 0.0) lo = mid;
+            else hi = mid;
+        }
+        return lo;
+    }
+    return 1.0;
+}
+
+/* Coefficients of det(A + t B) - s det(A) (3x3, row-major), from the
+ * multilinearity of det in the columns: t^k collects the determinants with
+ * k columns taken from B and 3 - k from A. */
+void or_det_cubic(const double A[9], const double B[9], double s, double c[4])
+{
+    c[0] = c[1] = c[2] = c[3] = 0.0;
+    for (int mask = 0; mask < 8; ++mask) {
+        double M[9];
+        int k = 0;
+        for (int col = 0; col < 3; ++col) {
+            const double *src = (mask >> col) & 1 ? B : A;
+            k += (mask >> col) & 1;
+            for (int r = 0; r < 3; ++r) M[3 * r + col] = src[3 * r + col];
+        }
+        c[k] += det3(M);
+    }
+    c[0] -= s * det3(A);
+}
+
 /* F = Ds Dm^-1 with Ds = [x1 - x0, x2 - x0, x3 - x0] (section 3). */
 void or_elem_F(const double x[12], const double B[9], double F[9])
 {
@@ -392,15 +503,23 @@ void or_elem_grad_hess(const double x[12], const double B[9], double vol, double
     or_elem_grad_hess_model(0, x, B, vol, mu, lam, project, psi, g, H);
 }
 
+double or_model_psi(int model, const double F[9], double mu, double lam)
+{
+    if (model == 1) return or_cor_psi(F, mu, lam);
+    if (model == 2) return or_nh_psi(F, mu, lam);
+    return or_snh_psi(F, mu, lam);
+}
+
 void or_elem_grad_hess_model(int model, const double x[12], const double B[9], double vol, double mu, double lam,
                              int project, double *psi, double g[12], double H[144])
 {
     double F[9], P[9], H9[81], H9p[81], A[4][3];
     or_elem_F(x, B, F);
     elem_A(B, A);
-    if (psi) *psi = vol * (model == 1 ? or_cor_psi(F, mu, lam) : or_snh_psi(F, mu, lam));
+    if (psi) *psi = vol * or_model_psi(model, F, mu, lam);
     if (g) {
         if (model == 1) or_cor_pk1(F, mu, lam, P);
+        else if (model == 2) or_nh_pk1(F, mu, lam, P);
         else or_snh_pk1(F, mu, lam, P);
         for (int i = 0; i < 4; ++i)
             for (int r = 0; r < 3; ++r) {
@@ -411,6 +530,7 @@ void or_elem_grad_hess_model(int model, const double x[12], const double B[9], d
     }
     if (H) {
         if (model == 1) or_cor_hess9(F, mu, lam, H9);
+        else if (model == 2) or_nh_hess9(F, mu, lam, H9);
         else or_snh_hess9(F, mu, lam, H9);
         if (project) or_psd_project(9, H9, H9p);
         else memcpy(H9p, H9, sizeof(H9p));
@@ -776,7 +896,7 @@ or_scene *or_create(int32_t nv, const double *rest, const double *x0, const doub
         S->vol[e] = det3(Dm) / 6.0;
         const double *m = S->mats + 3 * S->tmat[e];
         or_lame(m[0], m[1], &S->emu[e], &S->elam[e]);
-        if (prm->model == 1) S->elam[e] -= S->emu[e]; /* COR: the Lame constant itself */
+        if (prm->model == 1 || prm->model == 2) S->elam[e] -= S->emu[e]; /* COR, NH: the Lame constant itself */
         for (int k = 0; k < 4; ++k) S->mass[t[k]] += m[2] * S->vol[e] / 4.0;
     }
     for (int v = 0; v < nv; ++v)
@@ -1377,7 +1497,7 @@ double or_energy_L(or_scene *S, const double *xtilde, const double *xlin, const 
         double x12[12], F[9];
         gather12(xhat, S->tets + 4 * e, x12);
         or_elem_F(x12, S->B + 9 * e, F);
-        L += h2 * S->vol[e] * (S->p.model == 1 ? or_cor_psi(F, S->emu[e], S->elam[e]) : or_snh_psi(F, S->emu[e], S->elam[e]));
+        L += h2 * S->vol[e] * or_model_psi(S->p.model, F, S->emu[e], S->elam[e]);
     }
     for (int i = 0; i < S->nc; ++i) {
         double cs = constraint_c(S, i, xlin, xhat) - sfix[i];
@@ -1640,7 +1760,34 @@ int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat)
     return m;
 }
 
-/* MaxStepSize (section 4.1): alpha = min(1, min_i TOI_i) over x0 -> x1. */
+/* Inversion-aware step bound (section 4.1: for a non-invertible material
+ * such as NH, MaxStepSize also keeps the trajectory inversion-free).
+ * Reading: along x0 + t (x1 - x0) each element's J(t) = det F(t), a cubic
+ * in t, may fall to the fraction s_ccd of J(0) and no further, the same
+ * fraction ACCD keeps of a gap; the bound is the smallest t in (0, 1] with
+ * J(t) = s J(0) over the elements with a free vertex, else 1.  An element
+ * with J(0) <= 0 allows no step (0). */
+double or_inversion_step(or_scene *S, const double *x0, const double *x1)
+{
+    double a = 1.0;
+    for (int e = 0; e < S->nt; ++e) {
+        const int *t = S->tets + 4 * e;
+        if (S->dir[t[0]] && S->dir[t[1]] && S->dir[t[2]] && S->dir[t[3]]) continue;
+        double xa[12], xb[12], dx[12], F0[9], dF[9], c[4];
+        gather12(x0, t, xa);
+        gather12(x1, t, xb);
+        for (int k = 0; k < 12; ++k) dx[k] = xb[k] - xa[k];
+        or_elem_F(xa, S->B + 9 * e, F0);
+        or_elem_F(dx, S->B + 9 * e, dF); /* F is linear in x: F(t) = F0 + t dF */
+        or_det_cubic(F0, dF, S->p.s_ccd, c);
+        double te = or_cubic_first_root(c);
+        if (te < a) a = te;
+    }
+    return a;
+}
+
+/* MaxStepSize (section 4.1): alpha = min(1, min_i TOI_i) over x0 -> x1,
+ * and for NH also at most the inversion bound. */
 double or_max_step_size(or_scene *S, const double *x0, const double *x1)
 {
     hitvec hv = {0, 0, 0};
@@ -1649,6 +1796,10 @@ double or_max_step_size(or_scene *S, const double *x0, const double *x1)
     for (int i = 0; i < hv.n; ++i)
         if (hv.h[i].toi < a) a = hv.h[i].toi;
     free(hv.h);
+    if (S->p.model == 2) {
+        double ai = or_inversion_step(S, x0, x1);
+        if (ai < a) a = ai;
+    }
     return a;
 }
 

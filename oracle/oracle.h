@@ -35,7 +35,7 @@ extern "C" {
 
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
-    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model; /* model: 0 SNH, 1 COR */
+    int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model; /* model: 0 SNH, 1 COR, 2 NH */
 } or_params;
 
 typedef struct {
@@ -59,8 +59,14 @@ void or_lame(double E, double nu, double *mu, double *lam);
 double or_cor_psi(const double F[9], double mu, double lam);
 void or_cor_pk1(const double F[9], double mu, double lam, double P[9]);
 void or_cor_hess9(const double F[9], double mu, double lam, double H[81]);
+double or_nh_psi(const double F[9], double mu, double lam);
+void or_nh_pk1(const double F[9], double mu, double lam, double P[9]);
+void or_nh_hess9(const double F[9], double mu, double lam, double H[81]);
+double or_model_psi(int model, const double F[9], double mu, double lam);
+double or_cubic_first_root(const double c[4]);
+void or_det_cubic(const double A[9], const double B[9], double s, double c[4]);
 /* element energy, gradient and (projected) Hessian of material model
- * model (0 SNH, 1 COR); or_elem_grad_hess is model 0 */
+ * model (0 SNH, 1 COR, 2 NH); or_elem_grad_hess is model 0 */
 void or_elem_grad_hess_model(int model, const double x[12], const double B[9], double vol, double mu, double lam,
                              int project, double *psi, double g[12], double H[144]);
 
@@ -111,6 +117,7 @@ int32_t or_ccd_hits(or_scene *S, const double *x0, const double *x1, int32_t bru
                     int32_t cap, int32_t *keys, double *toi);
 int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat);
 double or_max_step_size(or_scene *S, const double *x0, const double *x1);
+double or_inversion_step(or_scene *S, const double *x0, const double *x1);
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
                 int32_t alpha_cap);
 int32_t or_min_distance(or_scene *S, const double *x, double *dmin);
