@@ -372,6 +372,8 @@ def main():
                     help="timed steps of the eight-cube scene with friction (0: skip)")
     ap.add_argument("--cor-steps", type=int, default=20,
                     help="timed steps of the eight-cube scene with the corotated material (0: skip)")
+    ap.add_argument("--nh-steps", type=int, default=20,
+                    help="timed steps of the eight-cube scene with the Neo-Hookean material (0: skip)")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -553,7 +555,7 @@ def main():
         large = run_large_bounded(args)
         _progress(f"large: {large.get('steps_per_s')} steps/s")
 
-    friction = cor = None
+    friction = cor = nh = None
     if args.friction_steps > 0:  # from step 15 on the cubes are in contact
         friction = run_variant(args, seed, ws, B, scenes, stream, flush,
                                "the eight-cube scene (196,608 tets) with the friction of appendix A: mu_f = 0.5, "
@@ -565,6 +567,11 @@ def main():
                           "the eight-cube scene (196,608 tets) with the corotated material (COR)", args.cor_steps,
                           max(args.warmup, 15), model=1)
         _progress(f"cor: {cor['steps_per_s']:.1f} steps/s")
+    if args.nh_steps > 0:
+        nh = run_variant(args, seed, ws, B, scenes, stream, flush,
+                         "the eight-cube scene (196,608 tets) with the Neo-Hookean material (NH) and the inversion "
+                         "bound of MaxStepSize", args.nh_steps, max(args.warmup, 15), model=2)
+        _progress(f"nh: {nh['steps_per_s']:.1f} steps/s")
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
@@ -598,6 +605,7 @@ def main():
                 "large": large,
                 "friction": friction,
                 "cor": cor,
+                "nh": nh,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "

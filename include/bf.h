@@ -83,9 +83,14 @@ typedef struct {
  * mu_f and eps_v [m/s] are the friction coefficient and the velocity
  * threshold of the smoothed semi-implicit friction of appendix A (mu_f = 0:
  * no friction; the paper uses k_min = 6 with friction).  model selects the
- * material of every tet: BF_MODEL_SNH (stable Neo-Hookean, section 3) or
- * BF_MODEL_COR (corotated linear, one of the models of Tab. 2). */
-enum { BF_MODEL_SNH = 0, BF_MODEL_COR = 1 };
+ * material of every tet: BF_MODEL_SNH (stable Neo-Hookean, section 3),
+ * BF_MODEL_COR (corotated linear) or BF_MODEL_NH (Neo-Hookean,
+ * Psi = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2, +inf for J <= 0),
+ * the other models of Tab. 2.  NH is not defined for inverted elements, so
+ * its MaxStepSize also bounds the step by element inversion (section 4.1;
+ * bf_inversion_step), and a state with an inverted element makes its
+ * energy infinite. */
+enum { BF_MODEL_SNH = 0, BF_MODEL_COR = 1, BF_MODEL_NH = 2 };
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model;
@@ -251,8 +256,18 @@ int bf_ccd_hits(bf_scene *scene, const double *x0, const double *x1, int32_t cap
 /* Alg. 3 UpdateActiveSet(x, xhat, C); *n_active (host, may be NULL). */
 int bf_update_active_set(bf_scene *scene, const double *x, const double *xhat, int32_t *n_active);
 
-/* MaxStepSize: alpha = min(1, min_i TOI_i) along x0 -> x1 (*alpha host). */
+/* MaxStepSize: alpha = min(1, min_i TOI_i) along x0 -> x1 (*alpha host);
+ * with BF_MODEL_NH also at most bf_inversion_step's bound. */
 int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double *alpha);
+
+/* Inversion bound of MaxStepSize (section 4.1, for non-invertible
+ * materials): along x0 + t (x1 - x0) (device, n_verts*3 each) every element
+ * with a free vertex keeps J(t) = det F(t) above s_ccd * J(0); *alpha (host)
+ * = the smallest t in (0, 1] with J(t) = s_ccd J(0) over those elements,
+ * else 1; an element with J(0) <= 0 gives 0.  Evaluated for any model;
+ * the time step applies it with BF_MODEL_NH only.  Synchronises the
+ * scene's stream. */
+int bf_inversion_step(bf_scene *scene, const double *x0, const double *x1, double *alpha);
 
 /* Narrow phase only: additive CCD on n explicit pairs of one type (0 = PT,
  * 1 = EE); x0, x1 (device, n*12: the 4 vertices of each pair), toi

@@ -101,6 +101,7 @@ def lib():
         "bf_ccd_hits": [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32), _P, _P],
         "bf_update_active_set": [_P, _P, _P, C.POINTER(C.c_int32)],
         "bf_max_step_size": [_P, _P, _P, C.POINTER(C.c_double)],
+        "bf_inversion_step": [_P, _P, _P, C.POINTER(C.c_double)],
         "bf_accd": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_max_step_size_pairs_noalloc": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_enable_timers": [_P, C.c_int32],
@@ -357,6 +358,13 @@ def bf_max_step_size(h, x0, x1):
 def bf_accd(ptype, x0, x1, s, toi, stream=None):
     n = toi.numel()
     _check("bf_accd", lib().bf_accd(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(toi), stream))
+
+
+def bf_inversion_step(h, x0, x1):
+    """inversion bound of MaxStepSize along x0 -> x1 (device tensors)"""
+    a = C.c_double()
+    _check("bf_inversion_step", lib().bf_inversion_step(h, _dptr(x0), _dptr(x1), C.byref(a)))
+    return a.value
 
 
 def bf_max_step_size_pairs_noalloc(ptype, n, x0, x1, s, alpha, stream=None):

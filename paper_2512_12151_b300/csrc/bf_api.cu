@@ -464,7 +464,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
         prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
         prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)) ||
-        (prm->model != BF_MODEL_SNH && prm->model != BF_MODEL_COR))
+        (prm->model != BF_MODEL_SNH && prm->model != BF_MODEL_COR && prm->model != BF_MODEL_NH))
         return BF_E_ARG;
     S.nv = nv;
     S.nt = nt;
@@ -506,7 +506,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         const double E = m->mats[3 * mi], nu = m->mats[3 * mi + 1], rho = m->mats[3 * mi + 2];
         if (!(E > 0) || !(nu > -1 && nu < 0.5) || !(rho > 0)) return BF_E_ARG;
         emu[e] = E / (2.0 * (1.0 + nu));
-        elam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));  // COR: the Lame constant
+        elam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));  // COR, NH: the Lame constant
         if (prm->model == BF_MODEL_SNH) elam[e] += emu[e];      // SNH: shifted (linear small-strain limit)
         for (int k = 0; k < 4; ++k) mass[t[k]] += rho * vol[e] / 4.0;
     }
@@ -1279,6 +1279,20 @@ int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double
     SCENE_OR_ARG(scene);
     if (!x0 || !x1 || !alpha) return BF_E_ARG;
     return run_ccd(S, x0, x1, false, alpha, nullptr);
+}
+
+int bf_inversion_step(bf_scene *scene, const double *x0, const double *x1, double *alpha)
+{
+    SCENE_OR_ARG(scene);
+    if (!x0 || !x1 || !alpha) return BF_E_ARG;
+    const double one = 1.0;
+    int st = check_cuda(cudaMemcpyAsync(S.dscal + S_TOI, &one, sizeof(double), cudaMemcpyHostToDevice, S.stream));
+    if (st) return st;
+    launch_inversion_bound(S, x0, x1, S.dscal + S_TOI);
+    st = sync_flags(S);
+    if (st) return st;
+    *alpha = std::min(1.0, S.h_scal[S_TOI]);
+    return BF_OK;
 }
 
 int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double s, double *toi, void *stream)

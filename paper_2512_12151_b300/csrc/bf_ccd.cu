@@ -893,7 +893,8 @@ static int broad_phase(Scene &S, const double *x0, const double *x1, const doubl
     return BF_OK;
 }
 
-// Narrow phase over the listed pairs: min TOI to *alpha_out, or every hit
+// Narrow phase over the listed pairs: min TOI (with NH also the inversion
+// bound) to *alpha_out, or every hit
 // (type, a, b, toi) stored and counted to *nhits_out.  With `filter` the
 // lists cover a wider motion: a pair goes on only if its exact swept boxes
 // along x0 -> x1 overlap, so exactly the candidates of this motion remain.
@@ -922,6 +923,9 @@ static void launch_narrow(Scene &S, const double *x0, const double *x1, int npt,
         launch(k_narrow<PT, false>, npt, S.cand_pt);
         launch(k_narrow<EE, false>, nee, S.cand_ee);
     }
+    // NH is not defined for inverted elements: MaxStepSize also keeps every
+    // element's volume (section 4.1)
+    if (!collect_hits && S.prm.model == BF_MODEL_NH) launch_inversion_bound(S, x0, x1, S.dscal + S_TOI);
 }
 
 static int narrow_phase(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,

@@ -14,6 +14,14 @@
 // (p, q) with third axis k the twist / flip eigenvalues are
 // mu +/- (lam (J - 1) - mu) sigma_k, c1 = (w_t+ + w_f+)/2, c2 = (w_f+ - w_t+)/2.
 // This is the vertex-block form of section 5.1 with the sparse D_k folded in.
+//
+// The Neo-Hookean energy (NH, Tab. 2) Psi = mu/2 (|F|^2 - 3) - mu ln J +
+// lam/2 (ln J)^2 (lam the Lame constant) has the same structure with
+// kappa = (lam ln J - mu) / J in place of lam (J - 1) - mu: P = mu F +
+// kappa cof(F), twist / flip eigenvalues mu +/- kappa sigma_k (that is,
+// (Psi_p +/- Psi_q) / (sigma_p +/- sigma_q)), and the scaling block
+// d2Psi/dsigma_p dsigma_q = lam / (sigma_p sigma_q) + [p = q] (mu +
+// (mu - lam ln J) / sigma_p^2).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
 #pragma unroll
             for (int q = 0; q < 3; ++q) S3[p][q] = lamT + (p == q ? HT(2) * muT : HT(0));
     } else {
+    double Jd = 1.0, lnJ = 0.0;  // NH: J and ln J in FP64
     // ---- gradient (FP64) ----
     {
         double C[3][3];  // cofactor: columns f1 x f2, f2 x f0, f0 x f1
@@ -266,7 +275,11 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         C[1][2] = F[2][0] * F[0][1] - F[0][0] * F[2][1];
         C[2][2] = F[0][0] * F[1][1] - F[1][0] * F[0][1];
         const double J = F[0][0] * C[0][0] + F[1][0] * C[1][0] + F[2][0] * C[2][0];
-        const double k = lam * (J - 1.0) - mu;
+        if (MODEL == BF_MODEL_NH) {
+            Jd = J;
+            lnJ = log(J);
+        }
+        const double k = MODEL == BF_MODEL_NH ? (lam * lnJ - mu) / J : lam * (J - 1.0) - mu;
         const double sc = h2 * V0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -286,7 +299,7 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         for (int c = 0; c < 3; ++c) Ft[r][c] = (HT)F[r][c];
     svd3<HT>(Ft, U, s, V);
     const HT J = s[0] * s[1] * s[2];
-    const HT kap = lamT * (J - HT(1)) - muT;
+    const HT kap = MODEL == BF_MODEL_NH ? (HT)((lam * lnJ - mu) / Jd) : lamT * (J - HT(1)) - muT;
     // twist / flip pairs: (0,1) third 2, (0,2) third 1, (1,2) third 0
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
@@ -297,14 +310,24 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         c1[p][q] = c1[q][p] = HT(0.5) * (wt + wf);
         c2[p][q] = c2[q][p] = HT(0.5) * (wf - wt);
     }
-    // scaling block A3 = mu I + kap [[0 s2 s1][s2 0 s0][s1 s0 0]] + lam g g^T, PSD-projected
+    // scaling block, PSD-projected: SNH A3 = mu I + kap [[0 s2 s1][s2 0 s0][s1 s0 0]] + lam g g^T;
+    // NH A3 = lam r r^T + diag(mu + (mu - lam ln J) r_p^2), r = 1 / s
     {
-        const HT g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
         HT A3[3][3];
+        if (MODEL == BF_MODEL_NH) {
+            const HT r[3] = {HT(1) / s[0], HT(1) / s[1], HT(1) / s[2]};
+            const HT dl = (HT)(mu - lam * lnJ);
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+            for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) A3[p][q] = lamT * g[p] * g[q] + (p == q ? muT : kap * s[3 - p - q]);
+                for (int q = 0; q < 3; ++q) A3[p][q] = lamT * r[p] * r[q] + (p == q ? muT + dl * r[p] * r[p] : HT(0));
+        } else {
+            const HT g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) A3[p][q] = lamT * g[p] * g[q] + (p == q ? muT : kap * s[3 - p - q]);
+        }
         HT w[3], E[3][3];
         sym3_eig<HT>(A3, w, E);
 #pragma unroll
@@ -373,13 +396,17 @@ void launch_elastic(Scene &S, const double *xhat)
     const double h2 = S.prm.dt * S.prm.dt;
     ScopedTimer tm(S, T_ELASTIC);
     const int nb = cdiv(S.nt, 128);
-    const bool cor = S.prm.model == BF_MODEL_COR;
+    const int m = S.prm.model;
     if (S.prm.precision == BF_PREC_MIXED) {
-        auto kern = cor ? k_elastic<float, float, BF_MODEL_COR> : k_elastic<float, float, BF_MODEL_SNH>;
+        auto kern = m == BF_MODEL_COR  ? k_elastic<float, float, BF_MODEL_COR>
+                    : m == BF_MODEL_NH ? k_elastic<float, float, BF_MODEL_NH>
+                                       : k_elastic<float, float, BF_MODEL_SNH>;
         kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.valf,
                                        S.nnzb, S.tblk);
     } else {
-        auto kern = cor ? k_elastic<double, double, BF_MODEL_COR> : k_elastic<double, double, BF_MODEL_SNH>;
+        auto kern = m == BF_MODEL_COR  ? k_elastic<double, double, BF_MODEL_COR>
+                    : m == BF_MODEL_NH ? k_elastic<double, double, BF_MODEL_NH>
+                                       : k_elastic<double, double, BF_MODEL_SNH>;
         kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.val,
                                        S.nnzb, S.tblk);
     }
@@ -538,6 +565,9 @@ __global__ void __launch_bounds__(kThreads) k_energy(
             const double tr = sv[0] + sv[1] + sv[2];
             e = h2 * vol[t] * (m * ((sv[0] - 1.0) * (sv[0] - 1.0) + (sv[1] - 1.0) * (sv[1] - 1.0) +
                                     (sv[2] - 1.0) * (sv[2] - 1.0)) + 0.5 * l * (tr - 3.0) * (tr - 3.0));
+        } else if (model == BF_MODEL_NH) {  // +inf for inverted or flat elements
+            const double L = J > 0.0 ? log(J) : 0.0;
+            e = J > 0.0 ? h2 * vol[t] * (0.5 * m * (I2 - 3.0) - m * L + 0.5 * l * L * L) : INFINITY;
         } else {
             e = h2 * vol[t] * (0.5 * m * (I2 - 3.0) - m * (J - 1.0) + 0.5 * l * (J - 1.0) * (J - 1.0));
         }
@@ -571,6 +601,114 @@ void launch_energy(Scene &S, const double *xtilde, const double *xlin, const dou
                                             S.elam, S.prm.dt * S.prm.dt, S.cv, S.cd, S.cg, S.clam, S.cgam, S.cs, xlin,
                                             S.mu, S.delta, S.nf, S.fv, S.fw, S.fn, S.fk, S.fx0,
                                             S.prm.dt * S.prm.eps_v, S.partials, S.counter, out);
+    ++S.n_launch;
+}
+
+// ---------------------------------------------------------------------------
+// Inversion bound of MaxStepSize (section 4.1, non-invertible materials).
+// One thread per element with a free vertex: along x0 + t (x1 - x0),
+// F(t) = F0 + t dF and p(t) = det F(t) - s det F0 is a cubic whose
+// coefficients follow from the multilinearity of det in the columns (t^k
+// collects the determinants with k columns of dF).  Its first root in
+// (0, 1] is bracketed on the pieces between the real roots of p' (p is
+// monotone on each) and bisected to adjacent doubles, keeping the end with
+// p > 0.  The minimum over elements goes to *tmin (non-negative doubles
+// compare like their bit patterns).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double det_cols(const double a[3], const double b[3], const double c[3])
+{
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+__device__ double cubic_first_root01(double c0, double c1, double c2, double c3)
+{
+    if (!(c0 > 0.0)) return 0.0;
+    auto p = [&](double t) { return ((c3 * t + c2) * t + c1) * t + c0; };
+    // real roots of p'(t) = 3 c3 t^2 + 2 c2 t + c1 (stable quadratic formula)
+    double r[2] = {2.0, 2.0};
+    const double qa = 3.0 * c3, qb = 2.0 * c2;
+    if (qa != 0.0) {
+        const double disc = qb * qb - 4.0 * qa * c1;
+        if (disc >= 0.0) {
+            const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+            r[0] = q / qa;
+            r[1] = q != 0.0 ? c1 / q : r[0];
+        }
+    } else if (qb != 0.0) {
+        r[0] = -c1 / qb;
+    }
+    if (r[0] > r[1]) {
+        const double t = r[0];
+        r[0] = r[1];
+        r[1] = t;
+    }
+    double lo = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double hi = k < 2 ? r[k] : 1.0;
+        if (!(hi > lo) || hi > 1.0) continue;
+        if (p(hi) > 0.0) {
+            lo = hi;
+            continue;
+        }
+        double a = lo, b = hi;
+        for (int it = 0; it < 1100; ++it) {  // adjacent doubles within [0, 1] after at most ~1075 halvings
+            const double m = 0.5 * (a + b);
+            if (!(m > a && m < b)) break;
+            if (p(m) > 0.0) a = m;
+            else b = m;
+        }
+        return a;
+    }
+    return 1.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_inversion_bound(int nt, const int4 *__restrict__ tets,
+                                                              const double *__restrict__ Bm,
+                                                              const uint8_t *__restrict__ dir,
+                                                              const double *__restrict__ x0,
+                                                              const double *__restrict__ x1, double s, double *tmin)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double t = 1.0;
+    if (e < nt) {
+        const int4 t4 = tets[e];
+        const int vid[4] = {t4.x, t4.y, t4.z, t4.w};
+        if (!(dir[vid[0]] && dir[vid[1]] && dir[vid[2]] && dir[vid[3]])) {
+            double D0[3][3], D1[3][3];  // Ds at x0 and Ds(x1) - Ds(x0); row r, column k
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const double a = x0[3 * vid[k + 1] + r] - x0[3 * vid[0] + r];
+                    D0[r][k] = a;
+                    D1[r][k] = (x1[3 * vid[k + 1] + r] - x1[3 * vid[0] + r]) - a;
+                }
+            const double *B = Bm + 9 * (size_t)e;
+            double f[3][3], g[3][3];  // columns of F0 and dF
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    f[c][r] = D0[r][0] * B[c] + D0[r][1] * B[3 + c] + D0[r][2] * B[6 + c];
+                    g[c][r] = D1[r][0] * B[c] + D1[r][1] * B[3 + c] + D1[r][2] * B[6 + c];
+                }
+            const double J0 = det_cols(f[0], f[1], f[2]);
+            const double c1 = det_cols(g[0], f[1], f[2]) + det_cols(f[0], g[1], f[2]) + det_cols(f[0], f[1], g[2]);
+            const double c2 = det_cols(f[0], g[1], g[2]) + det_cols(g[0], f[1], g[2]) + det_cols(g[0], g[1], f[2]);
+            const double c3 = det_cols(g[0], g[1], g[2]);
+            t = cubic_first_root01(J0 - s * J0, c1, c2, c3);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0 && t < 1.0) atomic_min_pos(tmin, t);
+}
+
+void launch_inversion_bound(Scene &S, const double *x0, const double *x1, double *tmin)
+{
+    if (S.nt == 0) return;
+    k_inversion_bound<<<cdiv(S.nt, kThreads), kThreads, 0, S.stream>>>(S.nt, S.tets, S.B, S.dir, x0, x1,
+                                                                       S.prm.s_ccd, tmin);
     ++S.n_launch;
 }
 

@@ -58,7 +58,7 @@ class Params:
     max_ls: int = 30
     max_cg: int = 10000
     precision: int = 0  # 0 = FP64, 1 = mixed (FP32 Hessian/SpMV/preconditioner)
-    model: int = 0      # material: 0 = stable Neo-Hookean (SNH), 1 = corotated linear (COR)
+    model: int = 0      # material: 0 = stable Neo-Hookean (SNH), 1 = corotated linear (COR), 2 = Neo-Hookean (NH)
 
 
 @dataclass
