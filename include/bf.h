@@ -82,7 +82,10 @@ typedef struct {
  * s_ccd is the ACCD conservative rescaling (target gap s_ccd * d(x0)).
  * mu_f and eps_v [m/s] are the friction coefficient and the velocity
  * threshold of the smoothed semi-implicit friction of appendix A (mu_f = 0:
- * no friction; the paper uses k_min = 6 with friction).  model selects the
+ * no friction; the paper uses k_min = 6 with friction).  res_tol > 0
+ * replaces Eq. termination by the IPC-style criterion of section 6: a step's
+ * outer loop ends once the gradient-norm residual (bf_newton_residual) at
+ * x^[k] is below res_tol, checked before every outer iteration (0: off).  model selects the
  * material of every tet: BF_MODEL_SNH (stable Neo-Hookean, section 3),
  * BF_MODEL_COR (corotated linear) or BF_MODEL_NH (Neo-Hookean,
  * Psi = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2, +inf for J <= 0),
@@ -92,7 +95,7 @@ typedef struct {
  * energy infinite. */
 enum { BF_MODEL_SNH = 0, BF_MODEL_COR = 1, BF_MODEL_NH = 2 };
 typedef struct {
-    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
+    double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v, res_tol;
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model;
 } bf_params;
 
@@ -259,6 +262,20 @@ int bf_update_active_set(bf_scene *scene, const double *x, const double *xhat, i
 /* MaxStepSize: alpha = min(1, min_i TOI_i) along x0 -> x1 (*alpha host);
  * with BF_MODEL_NH also at most bf_inversion_step's bound. */
 int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double *alpha);
+
+/* Gradient-norm residual of IPC (section 6): *res (host) =
+ * (1/h) ||H^-1 grad L||_inf at x (device, n_verts*3), L the AL energy
+ * (Eq. total-energy) linearised at x with the scene's active set,
+ * multipliers, decay factors, mu and delta, taken at xhat = x with the
+ * optimal slacks; H its PSD-projected Hessian, solved by the block-Jacobi
+ * PCG to cg_tol.  Overwrites the assembled system.  Synchronises the
+ * scene's stream. */
+int bf_newton_residual(bf_scene *scene, const double *xtilde, const double *x, double *res);
+
+/* Residuals of the last time step's outer iterations when res_tol > 0
+ * (the first at x^t, the last below res_tol unless the step failed):
+ * copies min(cap, count) into out (host), *n (host) = count. */
+int bf_get_residual_log(bf_scene *scene, int32_t cap, int32_t *n, double *out);
 
 /* Inversion bound of MaxStepSize (section 4.1, for non-invertible
  * materials): along x0 + t (x1 - x0) (device, n_verts*3 each) every element

@@ -29,7 +29,7 @@ class OrParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("delta", C.c_double), ("gravity", C.c_double * 3),
                 ("eps", C.c_double), ("cg_tol", C.c_double), ("gamma_decay", C.c_double),
                 ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
-                ("eps_v", C.c_double), ("k_min", C.c_int32),
+                ("eps_v", C.c_double), ("res_tol", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
                 ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32)]
 
@@ -66,9 +66,11 @@ def lib():
         L.or_create.argtypes = [C.c_int32, _D, _D, _D, C.c_int32, _I, _I, C.c_int32, _D, C.c_int32, _I,
                                 C.POINTER(C.c_uint8), C.POINTER(OrParams)]
         L.or_destroy.argtypes = [C.c_void_p]
-        for name in ("or_get_mu", "or_mu_init", "or_assemble", "or_energy_L", "or_max_step_size", "or_inversion_step"):
+        for name in ("or_get_mu", "or_mu_init", "or_assemble", "or_energy_L", "or_max_step_size", "or_inversion_step",
+                     "or_newton_residual"):
             getattr(L, name).restype = C.c_double
         L.or_set_mu_delta.argtypes = [C.c_void_p, C.c_double, C.c_double]
+        L.or_get_residual_log.argtypes = [C.c_void_p, C.c_int32, _D]
         L.or_pcg.argtypes = [C.c_void_p, _D, _D, C.c_double, C.c_int32]
         L.or_accd.argtypes = [C.c_int, _D, _D, C.c_double, C.c_double, C.c_int32, _D]
         L.or_lame.argtypes = [C.c_double, C.c_double, _D, _D]
@@ -241,6 +243,7 @@ def params_struct(p) -> OrParams:
     s.gravity[:] = list(p.gravity)
     s.eps, s.cg_tol, s.gamma_decay, s.c_mu, s.s_ccd = p.eps, p.cg_tol, p.gamma_decay, p.c_mu, p.s_ccd
     s.mu_f, s.eps_v = p.mu_f, p.eps_v
+    s.res_tol = getattr(p, "res_tol", 0.0)
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.precision = p.precision
@@ -395,6 +398,17 @@ class Oracle:
 
     def max_step_size(self, x0, x1):
         return lib().or_max_step_size(C.c_void_p(self.h), _p(_f64(x0)), _p(_f64(x1)))
+
+    def newton_residual(self, xtilde, x):
+        """(1/h) |H^-1 grad L|_inf at x with L linearised at x"""
+        return lib().or_newton_residual(C.c_void_p(self.h), _p(_f64(xtilde)), _p(_f64(x)))
+
+    def residual_log(self):
+        """gradient-norm residuals of the last step's outer iterations"""
+        n = lib().or_get_residual_log(C.c_void_p(self.h), 0, None)
+        out = np.zeros(max(n, 1))
+        lib().or_get_residual_log(C.c_void_p(self.h), n, _p(out))
+        return out[:n]
 
     def inversion_step(self, x0, x1):
         """the inversion bound of MaxStepSize over x0 -> x1 (any model)"""

@@ -54,6 +54,9 @@ struct or_scene {
     int nf, fcap;
     int *fv;
     double *fw, *fn, *fk, *fA;
+    /* gradient-norm residuals of the last step's outer iterations */
+    int nres, rescap;
+    double *res;
 };
 
 /* ------------------------------------------------------------------ */
@@ -924,7 +927,7 @@ void or_destroy(or_scene *S)
     void *ptrs[] = {S->X, S->x, S->v, S->targets, S->grad, S->tets, S->tmat, S->mats, S->dir, S->B,
                     S->vol, S->emu, S->elam, S->mass, S->sv, S->st, S->se, S->tri_key_sorted,
                     S->tri_key_idx, S->rp, S->ci, S->tmap, S->val, S->ctype, S->ca, S->cb,
-                    S->clam, S->cgam, S->cd, S->cs, S->cg, S->fv, S->fw, S->fn, S->fk, S->fA};
+                    S->clam, S->cgam, S->cd, S->cs, S->cg, S->fv, S->fw, S->fn, S->fk, S->fA, S->res};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(S);
 }
@@ -1803,6 +1806,42 @@ double or_max_step_size(or_scene *S, const double *x0, const double *x1)
     return a;
 }
 
+/* Gradient-norm residual of IPC (section 6, convergence of the
+ * gradient-norm residual): r = (1/h) |H^-1 grad L|_inf.  Reading: at an
+ * outer iterate x = x^[k], L is the next subproblem's energy (Eq.
+ * total-energy linearised at x, with the current active set, multipliers,
+ * decay factors, mu and delta, the slacks at their optimal values) taken at
+ * xhat = x, and H its projected Hessian; the solve is the same PCG. */
+double or_newton_residual(or_scene *S, const double *xtilde, const double *x)
+{
+    int n = 3 * S->nv;
+    double *g = (double *)xcalloc(n, sizeof(double)), *p = (double *)xcalloc(n, sizeof(double));
+    or_linearize(S, x, NULL, NULL);
+    or_assemble(S, xtilde, x, x, g);
+    or_pcg(S, g, p, S->p.cg_tol, S->p.max_cg);
+    double m = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (fabs(p[i]) > m) m = fabs(p[i]);
+    free(g);
+    free(p);
+    return m / S->p.dt;
+}
+
+int32_t or_get_residual_log(const or_scene *S, int32_t cap, double *out)
+{
+    for (int i = 0; i < S->nres && i < cap; ++i) out[i] = S->res[i];
+    return S->nres;
+}
+
+static void res_push(or_scene *S, double r)
+{
+    if (S->nres == S->rescap) {
+        S->rescap = S->rescap ? 2 * S->rescap : 64;
+        S->res = (double *)realloc(S->res, S->rescap * sizeof(double));
+    }
+    S->res[S->nres++] = r;
+}
+
 /* Minimum unsigned distance over all admissible PT / EE pairs at x. */
 int32_t or_min_distance(or_scene *S, const double *x, double *dmin)
 {
@@ -1839,7 +1878,10 @@ int32_t or_min_distance(or_scene *S, const double *x, double *dmin)
 /* Readings: mu_init is evaluated at xhat^[0] each time step; the stall  */
 /* rule of section 5.2 (alpha < 1e-4 for 50 consecutive iterations ->   */
 /* mu *= 2, delta /= 2) acts within the step, and delta is reset each    */
-/* step; the outer loop is capped at max_outer (status -7).              */
+/* step; the outer loop is capped at max_outer (status -7).  With        */
+/* res_tol > 0 the loop ends instead once the gradient-norm residual at  */
+/* x^[k] falls below res_tol (the IPC-style termination of section 6),   */
+/* checked before each outer iteration, from x^[0] = x^t on.             */
 /* ------------------------------------------------------------------ */
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log, int32_t alpha_cap)
 {
@@ -1866,7 +1908,16 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
         or_mu_init(S, xh, xtilde);
         double beta = 1.0, asum = 0.0;
         int k = 0, stall = 0;
-        while (beta > S->p.eps) {
+        const int resmode = S->p.res_tol > 0.0;
+        S->nres = 0;
+        for (;;) {
+            if (resmode) {
+                double r = or_newton_residual(S, xtilde, xk);
+                res_push(S, r);
+                if (r < S->p.res_tol) break;
+            } else if (!(beta > S->p.eps)) {
+                break;
+            }
             if (k >= S->p.max_outer) { status = -7; break; }
             memcpy(xhn, xh, n * sizeof(double));
             int32_t cgi = 0, lsf = 0;

@@ -35,6 +35,7 @@ extern "C" {
 
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
+    double res_tol; /* > 0: end the outer loop once the gradient-norm residual is below it (not beta) */
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model; /* model: 0 SNH, 1 COR, 2 NH */
 } or_params;
 
@@ -118,6 +119,12 @@ int32_t or_ccd_hits(or_scene *S, const double *x0, const double *x1, int32_t bru
 int32_t or_update_active_set(or_scene *S, const double *x, const double *xhat);
 double or_max_step_size(or_scene *S, const double *x0, const double *x1);
 double or_inversion_step(or_scene *S, const double *x0, const double *x1);
+/* IPC-style gradient-norm residual (1/h) |H^-1 grad L|_inf at x, L
+ * linearised at x with the current active set, multipliers, mu and delta */
+double or_newton_residual(or_scene *S, const double *xtilde, const double *x);
+/* residuals of the last time step's outer iterations (residual mode):
+ * copies up to cap into out, returns their count */
+int32_t or_get_residual_log(const or_scene *S, int32_t cap, double *out);
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
                 int32_t alpha_cap);
 int32_t or_min_distance(or_scene *S, const double *x, double *dmin);

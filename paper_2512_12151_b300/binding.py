@@ -34,7 +34,7 @@ class bf_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("delta", C.c_double), ("gravity", C.c_double * 3),
                 ("eps", C.c_double), ("cg_tol", C.c_double), ("gamma_decay", C.c_double),
                 ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
-                ("eps_v", C.c_double), ("k_min", C.c_int32),
+                ("eps_v", C.c_double), ("res_tol", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
                 ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32)]
 
@@ -102,6 +102,8 @@ def lib():
         "bf_update_active_set": [_P, _P, _P, C.POINTER(C.c_int32)],
         "bf_max_step_size": [_P, _P, _P, C.POINTER(C.c_double)],
         "bf_inversion_step": [_P, _P, _P, C.POINTER(C.c_double)],
+        "bf_newton_residual": [_P, _P, _P, C.POINTER(C.c_double)],
+        "bf_get_residual_log": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)],
         "bf_accd": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_max_step_size_pairs_noalloc": [C.c_int32, C.c_int32, _P, _P, C.c_double, _P, _P],
         "bf_enable_timers": [_P, C.c_int32],
@@ -165,6 +167,7 @@ def make_params(p) -> bf_params:
     s.gravity[:] = list(p.gravity)
     s.eps, s.cg_tol, s.gamma_decay, s.c_mu, s.s_ccd = p.eps, p.cg_tol, p.gamma_decay, p.c_mu, p.s_ccd
     s.mu_f, s.eps_v = p.mu_f, p.eps_v
+    s.res_tol = getattr(p, "res_tol", 0.0)
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.model = p.model
@@ -358,6 +361,23 @@ def bf_max_step_size(h, x0, x1):
 def bf_accd(ptype, x0, x1, s, toi, stream=None):
     n = toi.numel()
     _check("bf_accd", lib().bf_accd(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(toi), stream))
+
+
+def bf_newton_residual(h, xtilde, x):
+    """gradient-norm residual (1/h) |H^-1 grad L|_inf at x (device tensors)"""
+    r = C.c_double()
+    _check("bf_newton_residual", lib().bf_newton_residual(h, _dptr(xtilde), _dptr(x), C.byref(r)))
+    return r.value
+
+
+def bf_get_residual_log(h):
+    """residuals of the last step's outer iterations (residual mode)"""
+    n = C.c_int32()
+    _check("bf_get_residual_log", lib().bf_get_residual_log(h, 0, C.byref(n), None))
+    out = np.zeros(max(n.value, 1))
+    _check("bf_get_residual_log", lib().bf_get_residual_log(h, n.value, C.byref(n),
+                                                            out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out[: n.value]
 
 
 def bf_inversion_step(h, x0, x1):

@@ -254,6 +254,42 @@ static double mu_init(Scene &S, const double *xtilde, const double *xhat)
     return S.mu;
 }
 
+// |v|_inf of a vector -> *out (zeroed before; non-negative doubles compare
+// like their bit patterns)
+__global__ void k_absmax(int n, const double *__restrict__ v, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = i < n ? fabs(v[i]) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_pos(out, m);
+}
+
+// Gradient-norm residual of IPC (section 6): (1/h) |H^-1 grad L|_inf at x,
+// L linearised at x with the current active set, multipliers, mu and delta
+// and taken at xhat = x.  H p = -G is solved for the unit right-hand side
+// (as in the Newton loop) and |p|_inf scaled back by |G|.
+static int newton_residual(Scene &S, const double *xtilde, const double *x, double *res)
+{
+    const int n = 3 * S.nv;
+    launch_linearize(S, x);
+    int st = assemble(S, xtilde, x, x);
+    if (st) return st;
+    k_norm<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.grad, S.partials, S.counter, S.dscal + S_GNORM);
+    k_neg_unit<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, S.grad, S.dscal + S_GNORM);
+    S.n_launch += 2;
+    int it = 0;
+    st = run_pcg(S, S.cg_b, S.pdir, S.prm.cg_tol, S.prm.max_cg, &it);
+    if (st && st != BF_E_CG_MAXIT) return st;
+    cudaMemsetAsync(S.dscal + S_RESID, 0, sizeof(double), S.stream);
+    k_absmax<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.pdir, S.dscal + S_RESID);
+    ++S.n_launch;
+    st = sync_flags(S);
+    if (st) return st;
+    *res = S.h_scal[S_GNORM] * S.h_scal[S_RESID] / S.prm.dt;
+    return std::isfinite(*res) ? BF_OK : BF_E_NONFINITE;
+}
+
 struct SolveStats {
     int newton = 0, cg = 0, ls_fail = 0, cg_maxit = 0, newton_cap = 0;
 };
@@ -362,7 +398,18 @@ static int step_once(Scene &S, bf_step_stats *out)
     double beta = 1.0, asum = 0.0;
     int k = 0, stall = 0, status = BF_OK;
     SolveStats ss;
-    while (beta > S.prm.eps) {
+    const bool resmode = S.prm.res_tol > 0.0;  // IPC-style termination (section 6) instead of Eq. termination
+    S.res_log.clear();
+    for (;;) {
+        if (resmode) {
+            double r = 0.0;
+            const int rc = newton_residual(S, S.xtilde, S.xk, &r);
+            if (rc) return rc;
+            S.res_log.push_back(r);
+            if (r < S.prm.res_tol) break;
+        } else if (!(beta > S.prm.eps)) {
+            break;
+        }
         if (k >= S.prm.max_outer) {
             status = BF_E_OUTER_MAXIT;
             break;
@@ -463,7 +510,7 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
     if (nv >= (1 << 21) || nt >= (1 << 29)) return BF_E_ARG;  // triangle keys pack 3 vertex ids of 21 bits
     if (prm->dt <= 0 || prm->delta < 0 || prm->eps <= 0 || prm->cg_tol <= 0 || prm->k_min < 1 ||
         prm->max_cg < 1 || prm->max_newton < 1 || prm->max_outer < 1 || prm->max_ls < 0 || prm->s_ccd <= 0 ||
-        prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)) ||
+        prm->s_ccd >= 1 || !(prm->mu_f >= 0) || (prm->mu_f > 0 && !(prm->eps_v > 0)) || !(prm->res_tol >= 0) ||
         (prm->model != BF_MODEL_SNH && prm->model != BF_MODEL_COR && prm->model != BF_MODEL_NH))
         return BF_E_ARG;
     S.nv = nv;
@@ -1279,6 +1326,23 @@ int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double
     SCENE_OR_ARG(scene);
     if (!x0 || !x1 || !alpha) return BF_E_ARG;
     return run_ccd(S, x0, x1, false, alpha, nullptr);
+}
+
+int bf_newton_residual(bf_scene *scene, const double *xtilde, const double *x, double *res)
+{
+    SCENE_OR_ARG(scene);
+    if (!xtilde || !x || !res || !(S.mu > 0)) return BF_E_ARG;
+    return newton_residual(S, xtilde, x, res);
+}
+
+int bf_get_residual_log(bf_scene *scene, int32_t cap, int32_t *n, double *out)
+{
+    SCENE_OR_ARG(scene);
+    if (cap < 0 || (cap > 0 && !out)) return BF_E_ARG;
+    const int m = (int)S.res_log.size();
+    for (int i = 0; i < m && i < cap; ++i) out[i] = S.res_log[i];
+    if (n) *n = m;
+    return BF_OK;
 }
 
 int bf_inversion_step(bf_scene *scene, const double *x0, const double *x1, double *alpha)

@@ -30,7 +30,7 @@ enum { PT = 0, EE = 1 };
 enum {
     S_RZ = 0, S_BB, S_ALPHA, S_BETA, S_RR, S_PQ, S_E0, S_E1, S_MU, S_TOI, S_DOT, S_MAXDIAG,
     S_T_SPMV, S_T_RED1, S_T_UPD, S_T_RED2, S_RES = 16,  // S_RES..S_RES+23: reduction accumulators
-    S_T_STAGE = 40, S_T_ROWS, S_T_CONTACT, S_GNORM,
+    S_T_STAGE = 40, S_T_ROWS, S_T_CONTACT, S_GNORM, S_RESID,
     S_NSCAL = 48
 };
 // device flag slots (dflag)
@@ -61,6 +61,7 @@ struct Scene {
     bf_params prm{};
     double mu = 0.0, delta = 0.0;
     double L_scale = -1.0;  // |L| at the time step's first Newton iterate (< 0: unset)
+    std::vector<double> res_log;  // gradient-norm residuals of the last step (residual mode)
     int has_targets = 0;
     cudaStream_t stream = nullptr;
     bf_allocator alloc{};

@@ -53,6 +53,7 @@ class Params:
     s_ccd: float = 0.1
     mu_f: float = 0.0
     eps_v: float = 1e-3
+    res_tol: float = 0.0  # > 0: end a step's outer loop on the gradient-norm residual instead of beta
     max_outer: int = 1000
     max_newton: int = 50
     max_ls: int = 30
@@ -294,6 +295,42 @@ def colliding_cubes(seed: int = 0, cells: int = 2, side: float = 0.1, gap: float
                 Params(gravity=(0.0, 0.0, 0.0)), 10, {"seed": seed})
     n1 = len(v)
     s.v0[:n1, 0] = speed
+    return s
+
+
+def ball_mesh(cells: int, radius: float):
+    """A ball of `radius` centred at the origin: the Kuhn grid of a cube
+    [-r, r]^3 with `cells` cells per side, each vertex p moved to
+    p |p|_inf / |p|_2 (the cube's shells become spheres), so the surface is
+    a curved polyhedron without flat faces."""
+    v, t = cube_mesh(cells, 2.0 * radius)
+    v = v - radius
+    n2 = np.linalg.norm(v, axis=1)
+    ninf = np.abs(v).max(axis=1)
+    scale = np.where(n2 > 0, ninf / np.where(n2 > 0, n2, 1.0), 1.0)
+    v = v * scale[:, None]
+    d = v[t[:, 1:]] - v[t[:, :1]]
+    assert np.linalg.det(d).min() > 0, "ball mesh has inverted tets"
+    return v, t
+
+
+def colliding_balls(seed: int = 0, cells: int = 6, radius: float = 0.05, gap: float = 0.004,
+                    speed: float = 1.0, offset: float = 0.02, E: float = 1e5) -> Scene:
+    """Two balls, no gravity and no obstacles: the left one moves along +x at
+    `speed` toward the right one at rest, their centres `offset` apart in y
+    (an oblique hit: they collide and separate).  Seeded jitter of 1e-4 x
+    the radius on every vertex, rest shape included."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    v, t = ball_mesh(cells, radius)
+    j = 1e-4 * radius
+    v1 = v + rng.uniform(-j, j, size=v.shape) + np.array([-radius - gap / 2, 0.0, 0.0])
+    v2 = v + rng.uniform(-j, j, size=v.shape) + np.array([radius + gap / 2, offset, 0.0])
+    b.add_solid(v1, t, 0)
+    b.add_solid(v2, t, 0)
+    s = b.build(f"colliding_balls_{cells}_seed{seed}", [[E, 0.4, 1000.0]],
+                Params(gravity=(0.0, 0.0, 0.0)), 10, {"seed": seed})
+    s.v0[: len(v1), 0] = speed
     return s
 
 

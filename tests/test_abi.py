@@ -50,7 +50,7 @@ def test_binding_fails_loudly_without_library(monkeypatch):
 
 def test_struct_layouts_match_header():
     import ctypes as C
-    # bf_params: 12 doubles + 7 int32 (padded to 8 bytes); bf_step_stats: 8 int32 + 6 doubles
-    assert C.sizeof(B.bf_params) == 12 * 8 + 8 * 4
+    # bf_params: 13 doubles + 7 int32 (padded to 8 bytes); bf_step_stats: 8 int32 + 6 doubles
+    assert C.sizeof(B.bf_params) == 13 * 8 + 8 * 4
     assert C.sizeof(B.bf_step_stats) == 8 * 4 + 6 * 8
     assert C.sizeof(B.bf_mesh_desc) == 4 * 4 + 8 * 8
