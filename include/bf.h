@@ -343,6 +343,19 @@ int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
  * blocks and max window vertices per CTA (zeros before the first solve). */
 int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
 
+/* PCG autotuner: on the system assembled last (bf_step or bf_assemble must
+ * have run), times `iters` (>= 8) PCG iterations of each execution
+ * configuration (bf_set_pcg_mode 1, 2, 17, 18, 33, 34 and 0; a persistent
+ * configuration that does not fit is skipped) with CUDA events on the
+ * scene's stream, then sets the fastest per iteration.  modes / us_per_iter
+ * (host, cap entries each) receive the measured configurations in order,
+ * *n_out (host, may be NULL) their count, *best (host) the chosen mode.
+ * The solution buffers it uses are scratch; results of later steps do not
+ * depend on the choice beyond the order of floating-point sums.  Returns
+ * BF_E_ARG when no configuration could be timed (no assembled system). */
+int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes, double *us_per_iter,
+                    int32_t *n_out, int32_t *best);
+
 /* Number of this library's own kernel launches issued for the scene since
  * creation (sorts and scans done by CUB are not counted); *n host. */
 int bf_get_launch_count(bf_scene *scene, int64_t *n);

@@ -109,6 +109,8 @@ def lib():
         "bf_enable_timers": [_P, C.c_int32],
         "bf_get_launch_count": [_P, C.POINTER(C.c_int64)],
         "bf_set_pcg_mode": [_P, C.c_int32],
+        "bf_autotune_pcg": [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "bf_get_pcg_config": [_P, _P],
         "bf_get_timers": [_P, C.c_int32, _P, _P, _P],
         "bf_scene_bytes": [_P, C.POINTER(C.c_int64)],
@@ -396,6 +398,17 @@ def bf_max_step_size_pairs_noalloc(ptype, n, x0, x1, s, alpha, stream=None):
 
 def bf_enable_timers(h, on=True):
     _check("bf_enable_timers", lib().bf_enable_timers(h, int(on)))
+
+
+def bf_autotune_pcg(h, iters=64):
+    """times each PCG execution configuration on the last assembled system
+    and sets the fastest: (best mode, {mode: us per iteration})"""
+    cap = 16
+    modes = (C.c_int32 * cap)()
+    us = (C.c_double * cap)()
+    n, best = C.c_int32(), C.c_int32()
+    _check("bf_autotune_pcg", lib().bf_autotune_pcg(h, iters, cap, modes, us, C.byref(n), C.byref(best)))
+    return best.value, {int(modes[i]): float(us[i]) for i in range(min(n.value, cap))}
 
 
 def bf_set_pcg_mode(h, mode):

@@ -181,6 +181,11 @@ __global__ void k_apply_targets(int nd, const int *__restrict__ ids, const doubl
 }
 
 __global__ void k_set_double(double *p, double v) { *p = v; }
+__global__ void k_fill(int n, double *__restrict__ out, double v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
 
 // ---------------------------------------------------------------------------
 // active set storage
@@ -1391,6 +1396,73 @@ int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
         S.pcg_grid = 0;  // recomputed at the next solve
     }
     return BF_OK;
+}
+
+// PCG autotuner: on the system assembled last, times `iters` iterations of
+// each candidate execution configuration with CUDA events on the scene's
+// stream (after one untimed solve that sets the configuration up and warms
+// it) and keeps the fastest per iteration; the right-hand side is all ones
+// (a converged gradient would end the solves at once).  A persistent
+// candidate that falls back to the per-phase launches (no fitting
+// partition) is skipped.
+int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes, double *us_per_iter,
+                    int32_t *n_out, int32_t *best)
+{
+    SCENE_OR_ARG(scene);
+    if (iters < 8 || cap < 0 || (cap > 0 && (!modes || !us_per_iter)) || !best) return BF_E_ARG;
+    static const int kCand[] = {1, 2, 17, 18, 33, 34, 0};
+    const int n = 3 * S.nv;
+    const int keep_mode = S.pcg_mode == 0 ? 0
+                          : (S.pcg_ctas_per_sm | (S.pcg_allow_resident ? 0 : 16) | (S.pcg_force_global ? 32 : 0));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return BF_E_CUDA;
+    }
+    int nt = 0, best_mode = -1;
+    double best_us = 0.0;
+    int st = BF_OK;
+    k_fill<<<cdiv(n, kThreads), kThreads, 0, S.stream>>>(n, S.cg_b, 1.0);
+    ++S.n_launch;
+    for (int mode : kCand) {
+        bf_set_pcg_mode(scene, mode);
+        int it = 0;
+        st = run_pcg(S, S.cg_b, S.pdir, 1e-30, std::max(1, iters / 4), &it);  // set-up and warm-up
+        if (st && st != BF_E_CG_MAXIT) break;
+        st = BF_OK;
+        if (mode != 0 && S.pcg_mode == 0) continue;  // did not fit: fell back to the per-phase launches
+        cudaEventRecord(e0, S.stream);
+        int st2 = run_pcg(S, S.cg_b, S.pdir, 1e-30, iters, &it);
+        cudaEventRecord(e1, S.stream);
+        if (st2 && st2 != BF_E_CG_MAXIT) {
+            st = st2;
+            break;
+        }
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = BF_E_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it < iters / 2) continue;  // stopped early (breakdown): no usable timing
+        const double us = 1e3 * ms / it;
+        if (nt < cap) {
+            modes[nt] = mode;
+            us_per_iter[nt] = us;
+        }
+        ++nt;
+        if (best_mode < 0 || us < best_us) {
+            best_mode = mode;
+            best_us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bf_set_pcg_mode(scene, best_mode >= 0 ? best_mode : keep_mode);
+    if (n_out) *n_out = nt;
+    *best = best_mode;
+    if (st) return st;
+    return best_mode >= 0 ? BF_OK : BF_E_ARG;
 }
 
 int bf_get_pcg_config(bf_scene *scene, int32_t *cfg)

@@ -4,7 +4,7 @@ scene (8 cubes x 16^3 cells) or of the spiky-ball compression scene (about
 library's default (persistent) mode.
 
     python -m paper_2512_12151_b300.pcg_case [--scene eight_cubes|spiky_balls]
-        [--precision 1] [--steps 14] [--solves 2] [--mode 1] [--timers]
+        [--precision 1] [--steps 14] [--solves 2] [--mode 1] [--timers] [--autotune]
 
 The scene is first advanced `--steps` time steps with the per-phase PCG (so
 that no persistent-PCG launch happens before the timed solves; profilers can
@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--mode", type=int, default=1, help="bf_set_pcg_mode of the timed solves")
     ap.add_argument("--timers", action="store_true", help="also report the per-phase time of CTA 0")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the mode with bf_autotune_pcg on this system instead of --mode")
     args = ap.parse_args(argv)
 
     import torch
@@ -60,6 +62,10 @@ def main(argv=None):
     B.bf_assemble(sim.h, xt, xd, xd, G)
     b = -G
     B.bf_set_pcg_mode(sim.h, args.mode)
+    tuned = None
+    if args.autotune:
+        best, timed = B.bf_autotune_pcg(sim.h, 64)
+        tuned = {"best_mode": best, "us_per_iteration_by_mode": {str(k): round(v, 3) for k, v in timed.items()}}
     B.bf_enable_timers(sim.h, args.timers)
     iters, ms = [], []
     for _ in range(args.solves):
@@ -80,7 +86,8 @@ def main(argv=None):
                       "contacts": len(keys), "iterations": iters, "ms_per_solve": [round(v, 3) for v in ms],
                       "us_per_iteration": [round(1e3 * m / max(i, 1), 3) for m, i in zip(ms, iters)],
                       "pcg_config": B.bf_get_pcg_config(sim.h),
-                      **({"us_per_iteration_by_phase_cta0": phases} if args.timers else {})}))
+                      **({"us_per_iteration_by_phase_cta0": phases} if args.timers else {}),
+                      **({"autotune": tuned} if tuned else {})}))
     sim.close()
     return 0
 

@@ -405,8 +405,10 @@ def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, pr
 def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
     """On a system split over several CTAs (a 20k-tet scene after a few
     steps, with contacts), the resident, streamed and global-vector
-    persistent variants and the per-phase launches reach the tolerance on
-    the library's own operator and agree with each other."""
+    persistent variants at one and two CTAs per SM and the per-phase
+    launches reach the tolerance on the library's own operator and agree
+    with each other; the autotuner then times them and sets one whose solve
+    meets the tolerance."""
     torch = torch_cuda
     from paper_2512_12151_b300 import serving
     s = scenes.batch_scene(11, 1.8e4, 2e4, precision=precision)
@@ -423,7 +425,8 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
         B.bf_assemble(h, xt, xd, xd, G)
         b = -G
         sols, its, grids = [], [], []
-        for mode in (1, 17, 33, 0):
+        modes = (1, 2, 17, 18, 33, 34, 0)
+        for mode in modes:
             B.bf_set_pcg_mode(h, mode)
             p = torch.zeros_like(xd)
             it, _ = B.bf_pcg(h, b, p, 1e-6, 100000)
@@ -434,10 +437,20 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
             sols.append(host(p).reshape(-1))
             its.append(it)
             grids.append(B.bf_get_pcg_config(h))
-        assert grids[0]["ctas"] > 1 and grids[2]["resident"] == 2  # several CTAs; global variant used
-        for k in range(3):
-            assert abs(its[k] - its[3]) <= max(2, its[3] // 20), its
-            assert np.linalg.norm(sols[k] - sols[3]) <= 1e-4 * np.linalg.norm(sols[3])
+        assert grids[0]["ctas"] > 1 and grids[4]["resident"] == 2  # several CTAs; global variant used
+        last = len(modes) - 1
+        for k in range(last):
+            assert abs(its[k] - its[last]) <= max(2, its[last] // 20), its
+            assert np.linalg.norm(sols[k] - sols[last]) <= 1e-4 * np.linalg.norm(sols[last])
+        best, timed = B.bf_autotune_pcg(h, 64)
+        assert best in timed and set(timed) <= set(modes) and 1 in timed and 0 in timed
+        assert all(t > 0 for t in timed.values()) and timed[best] == min(timed.values())
+        assert B.bf_get_pcg_config(h)["mode"] == (0 if best == 0 else 1)
+        p = torch.zeros_like(xd)
+        B.bf_pcg(h, b, p, 1e-6, 100000)
+        Hp = torch.zeros_like(xd)
+        B.bf_hess_apply(h, p, Hp)
+        assert float(torch.linalg.norm(Hp - b) / torch.linalg.norm(b)) <= (1.01e-6 if precision == 0 else 1e-4)
     finally:
         B.bf_scene_destroy(h)
 
