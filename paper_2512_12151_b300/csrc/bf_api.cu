@@ -144,7 +144,7 @@ void flush_timers(Scene &S)
 }
 
 // ---------------------------------------------------------------------------
-// small kernels used by the drivers
+// small kernels used by the host-side step functions
 // ---------------------------------------------------------------------------
 __global__ void k_scale(int n, double *__restrict__ out, const double *__restrict__ in, double s)
 {
