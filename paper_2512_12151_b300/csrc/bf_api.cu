@@ -241,8 +241,11 @@ int active_reserve(Scene &S, int n)
 static int assemble(Scene &S, const double *xtilde, const double *xlin, const double *xhat)
 {
     cudaMemsetAsync(S.dflag + F_ERR, 0, sizeof(int), S.stream);
-    launch_vertex_init(S, xtilde, xhat);
-    launch_elastic(S, xhat);
+    if (!S.elastic_ready) {
+        launch_vertex_init(S, xtilde, xhat);
+        launch_elastic(S, xhat);
+    }
+    S.elastic_ready = false;
     launch_contact_assemble(S, xlin, xhat);
     const int st = launch_friction_assemble(S, xhat);
     if (st) return st;
@@ -277,6 +280,7 @@ __global__ void k_absmax(int n, const double *__restrict__ v, double *out)
 static int newton_residual(Scene &S, const double *xtilde, const double *x, double *res)
 {
     const int n = 3 * S.nv;
+    S.elastic_ready = false;
     launch_linearize(S, x);
     int st = assemble(S, xtilde, x, x);
     if (st) return st;
@@ -373,6 +377,7 @@ static int solve_subproblem(Scene &S, const double *xtilde, const double *xlin, 
 // Alg. 1: one time step.
 static int step_once(Scene &S, bf_step_stats *out)
 {
+    S.elastic_ready = false;
     auto t0 = std::chrono::steady_clock::now();
     const int n = 3 * S.nv;
     const size_t nb = n * sizeof(double);
@@ -400,6 +405,9 @@ static int step_once(Scene &S, bf_step_stats *out)
     } reuse_off{S};
     mu_init(S, S.xtilde, S.xh);
     if (!(S.mu > 0.0) || !std::isfinite(S.mu)) return BF_E_NONFINITE;
+    // the first Newton iterate of the first subproblem is x_hat^[0]: its
+    // inertia and elastic terms are the ones mu_init just assembled
+    S.elastic_ready = true;
     double beta = 1.0, asum = 0.0;
     int k = 0, stall = 0, status = BF_OK;
     SolveStats ss;
@@ -1195,6 +1203,7 @@ int bf_assemble(bf_scene *scene, const double *xtilde, const double *xlin, const
 {
     SCENE_OR_ARG(scene);
     if (!xtilde || !xlin || !xhat) return BF_E_ARG;
+    S.elastic_ready = false;
     if (!(S.mu > 0.0)) return BF_E_ARG;
     int st = assemble(S, xtilde, xlin, xhat);
     if (st) return st;
@@ -1282,6 +1291,7 @@ int bf_solve_subproblem(bf_scene *scene, const double *xtilde, const double *xli
 {
     SCENE_OR_ARG(scene);
     if (!xtilde || !xlin || !xhat || !(S.mu > 0)) return BF_E_ARG;
+    S.elastic_ready = false;
     SolveStats ss;
     S.L_scale = -1.0;  // called alone: the scale comes from this call's first iterate
     const int st = solve_subproblem(S, xtilde, xlin, xhat, ss);

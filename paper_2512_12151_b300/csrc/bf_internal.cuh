@@ -62,6 +62,9 @@ struct Scene {
     double mu = 0.0, delta = 0.0;
     double L_scale = -1.0;  // |L| at the time step's first Newton iterate (< 0: unset)
     std::vector<double> res_log;  // gradient-norm residuals of the last step (residual mode)
+    // the step's mu_init left the inertia and elastic parts of G and H at
+    // the first Newton iterate: the next assembly adds only the rest
+    bool elastic_ready = false;
     int has_targets = 0;
     cudaStream_t stream = nullptr;
     bf_allocator alloc{};
