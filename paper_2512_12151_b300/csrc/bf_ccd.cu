@@ -508,7 +508,7 @@ __device__ __forceinline__ bool box_overlap_f(const float *ql, const float *qh, 
 
 constexpr int kQueryThreads = 128;
 constexpr int kQueryStack = 32;   // a depth-first stack never holds more than the tree depth + 1 nodes
-constexpr int kQuerySplitLog = 3;  // each query is traversed as 8 independent subtree walks
+constexpr int kQuerySplitLog = 5;  // each query is traversed as 32 independent subtree walks
 
 struct QueryTree {
     int nq;              // queries
