@@ -1346,7 +1346,7 @@ int bf_max_step_size(bf_scene *scene, const double *x0, const double *x1, double
 int bf_newton_residual(bf_scene *scene, const double *xtilde, const double *x, double *res)
 {
     SCENE_OR_ARG(scene);
-    if (!xtilde || !x || !res || !(S.mu > 0)) return BF_E_ARG;
+    if (!xtilde || !x || !res || !(S.mu > 0) || S.nv < 1) return BF_E_ARG;
     return newton_residual(S, xtilde, x, res);
 }
 
@@ -1419,7 +1419,7 @@ int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes,
                     int32_t *n_out, int32_t *best)
 {
     SCENE_OR_ARG(scene);
-    if (iters < 8 || cap < 0 || (cap > 0 && (!modes || !us_per_iter)) || !best) return BF_E_ARG;
+    if (iters < 8 || cap < 0 || (cap > 0 && (!modes || !us_per_iter)) || !best || S.nv < 1) return BF_E_ARG;
     static const int kCand[] = {1, 2, 17, 18, 33, 34, 0};
     const int n = 3 * S.nv;
     const int keep_mode = S.pcg_mode == 0 ? 0
