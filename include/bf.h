@@ -347,7 +347,9 @@ int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
  * have run), times `iters` (>= 8) PCG iterations of each execution
  * configuration (bf_set_pcg_mode 1, 2, 17, 18, 33, 34 and 0; a persistent
  * configuration that does not fit is skipped) with CUDA events on the
- * scene's stream, then sets the fastest per iteration.  modes / us_per_iter
+ * scene's stream, then sets the fastest per iteration (a configuration later
+ * in that list replaces the choice so far only when it is more than 2 %
+ * faster, so timing noise does not flip it).  modes / us_per_iter
  * (host, cap entries each) receive the measured configurations in order,
  * *n_out (host, may be NULL) their count, *best (host) the chosen mode.
  * The solution buffers it uses are scratch; results of later steps do not

@@ -444,7 +444,8 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
             assert np.linalg.norm(sols[k] - sols[last]) <= 1e-4 * np.linalg.norm(sols[last])
         best, timed = B.bf_autotune_pcg(h, 64)
         assert best in timed and set(timed) <= set(modes) and 1 in timed and 0 in timed
-        assert all(t > 0 for t in timed.values()) and timed[best] == min(timed.values())
+        # the choice is within 2 % of the fastest (a later candidate must win by more)
+        assert all(t > 0 for t in timed.values()) and 0.98 * timed[best] <= min(timed.values())
         assert B.bf_get_pcg_config(h)["mode"] == (0 if best == 0 else 1)
         p = torch.zeros_like(xd)
         B.bf_pcg(h, b, p, 1e-6, 100000)
