@@ -403,6 +403,15 @@ int bf_batch_info(bf_batch *batch, int64_t *info);
 /* Seconds since bf_batch_create (the clock of t_admit and t_steps). */
 double bf_batch_now(bf_batch *batch);
 
+/* Per-bucket PCG autotuning in the batch (off by default): scenes are
+ * bucketed by floor(log2(matrix blocks + 1)); the first scene of a bucket
+ * is tuned with bf_autotune_pcg after its first step, and every scene of
+ * that bucket takes the chosen configuration at its next turn. */
+int bf_batch_set_autotune(bf_batch *batch, int32_t on);
+/* The tuned buckets so far, ascending: up to cap (bucket, mode) pairs into
+ * buckets / modes (host); *n (host, may be NULL) = their count. */
+int bf_batch_tuned(bf_batch *batch, int32_t cap, int32_t *buckets, int32_t *modes, int32_t *n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,8 @@ def lib():
                             C.POINTER(C.c_double), _P, _P],
         "bf_batch_release": [_P, C.c_int64],
         "bf_batch_info": [_P, _P],
+        "bf_batch_set_autotune": [_P, C.c_int32],
+        "bf_batch_tuned": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -511,6 +513,19 @@ def bf_batch_result(b, ticket, cap):
 
 def bf_batch_release(b, ticket):
     _check("bf_batch_release", lib().bf_batch_release(b, ticket))
+
+
+def bf_batch_set_autotune(b, on=True):
+    _check("bf_batch_set_autotune", lib().bf_batch_set_autotune(b, 1 if on else 0))
+
+
+def bf_batch_tuned(b):
+    """{size bucket: PCG mode} tuned by the batch so far"""
+    cap = 64
+    bk, md = (C.c_int32 * cap)(), (C.c_int32 * cap)()
+    n = C.c_int32()
+    _check("bf_batch_tuned", lib().bf_batch_tuned(b, cap, bk, md, C.byref(n)))
+    return {int(bk[i]): int(md[i]) for i in range(min(n.value, cap))}
 
 
 def bf_batch_info(b):

@@ -7,6 +7,11 @@
 // round (continuous batching) and the kernels of W scenes overlap on the
 // device.  Admission is refused (BF_E_BUDGET) when the device bytes of the
 // unfinished jobs plus the new scene would exceed the batch's HBM budget.
+// With autotuning on (bf_batch_set_autotune), the PCG execution
+// configuration is tuned once per size bucket (log2 of the matrix block
+// count, which grows with the vertex count): the first scene of a bucket is
+// tuned after its first step (bf_autotune_pcg, on its worker), and every
+// scene of the bucket takes that configuration at its next turn.
 // The runner only uses the public scene API; the time steps are the same
 // calls a single scene makes (Alg. 1 per step), so a scene's result does not
 // depend on what else runs beside it beyond the order of floating-point
@@ -21,6 +26,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "bf.h"
@@ -34,6 +40,7 @@ struct Job {
     bf_scene *scene = nullptr;
     int n_steps = 0, done = 0, status = BF_OK, worker = 0;
     int64_t bytes = 0, work = 0;  // device bytes; work estimate per step
+    int bucket = 0, mode = -1;    // autotuning size bucket; PCG mode set by the runner (-1: default)
     double t_admit = 0.0;
     std::vector<double> t_step;  // completion time of each step (s since batch creation)
     std::vector<bf_step_stats> stats;
@@ -53,6 +60,9 @@ struct bf_batch {
     int64_t budget = 0, resident = 0, next_ticket = 1;
     int device = 0, finished = 0;
     bool stop = false;
+    bool autotune = false;
+    std::unordered_map<int, int> tuned;  // size bucket -> PCG mode
+    std::unordered_set<int> tuning;     // buckets being tuned right now
     Clock::time_point epoch;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
@@ -68,6 +78,29 @@ struct bf_batch {
                 if (stop) return;
                 job = queues[w].front();
                 queues[w].pop_front();
+            }
+            int apply = -1;
+            bool tune = false;
+            if (autotune) {
+                std::lock_guard<std::mutex> lk(mu);
+                auto it = tuned.find(job->bucket);
+                if (it != tuned.end()) {
+                    if (job->mode != it->second) apply = it->second;
+                } else if (job->done >= 1 && !tuning.count(job->bucket)) {
+                    tuning.insert(job->bucket);  // this worker tunes the bucket
+                    tune = true;
+                }
+            }
+            if (apply >= 0 && bf_set_pcg_mode(job->scene, apply) == BF_OK) job->mode = apply;
+            if (tune) {  // the scene has assembled a system in its first step
+                int32_t best = -1;
+                const int rc = bf_autotune_pcg(job->scene, 32, 0, nullptr, nullptr, nullptr, &best);
+                std::lock_guard<std::mutex> lk(mu);
+                if (rc == BF_OK && best >= 0) {
+                    tuned[job->bucket] = best;
+                    job->mode = best;
+                }
+                tuning.erase(job->bucket);
             }
             bf_step_stats st{};
             const int rc = bf_step(job->scene, 1, &st);
@@ -143,6 +176,8 @@ int bf_batch_admit(bf_batch *b, bf_scene *scene, int32_t n_steps, int64_t *ticke
     if (!rc) rc = bf_scene_info(scene, info);
     if (rc) return rc;
     const int64_t work = (int64_t)info[3] + 1;  // matrix blocks: a proxy for the work of one step
+    int bucket = 0;
+    while ((int64_t)1 << (bucket + 1) <= work) ++bucket;  // floor(log2(blocks + 1))
     std::unique_lock<std::mutex> lk(b->mu);
     if (b->stop) return BF_E_ARG;
     if (b->resident + bytes > b->budget) return BF_E_BUDGET;
@@ -164,6 +199,7 @@ int bf_batch_admit(bf_batch *b, bf_scene *scene, int32_t n_steps, int64_t *ticke
     job->worker = w;
     job->bytes = bytes;
     job->work = work;
+    job->bucket = bucket;
     job->t_admit = b->now();
     job->t_step.reserve(n_steps);
     job->stats.reserve(n_steps);
@@ -236,5 +272,27 @@ int bf_batch_info(bf_batch *b, int64_t *info)
 }
 
 double bf_batch_now(bf_batch *b) { return b ? b->now() : -1.0; }
+
+int bf_batch_set_autotune(bf_batch *b, int32_t on)
+{
+    if (!b) return BF_E_ARG;
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->autotune = on != 0;
+    return BF_OK;
+}
+
+int bf_batch_tuned(bf_batch *b, int32_t cap, int32_t *buckets, int32_t *modes, int32_t *n)
+{
+    if (!b || cap < 0 || (cap > 0 && (!buckets || !modes))) return BF_E_ARG;
+    std::lock_guard<std::mutex> lk(b->mu);
+    std::vector<std::pair<int, int>> v(b->tuned.begin(), b->tuned.end());
+    std::sort(v.begin(), v.end());
+    for (int i = 0; i < (int)v.size() && i < cap; ++i) {
+        buckets[i] = v[i].first;
+        modes[i] = v[i].second;
+    }
+    if (n) *n = (int)v.size();
+    return BF_OK;
+}
 
 }  // extern "C"

@@ -60,12 +60,15 @@ def _wait(b, t, deadline):
             raise TimeoutError(f"batch ticket {t} did not finish in time")
 
 
-def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30, timeout_s=900.0):
+def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30, timeout_s=900.0, autotune=False):
     """Creates every scene (untimed), then admits them all at once to a batch
     and runs them to completion.  Returns throughput and per-step latency
-    (from the admission of all scenes)."""
+    (from the admission of all scenes); with `autotune`, the batch tunes the
+    PCG configuration per size bucket and the result lists the choices."""
     handles = [create(s) for s in scene_list]
     b = B.bf_batch_create(n_workers, budget_bytes)
+    if autotune:
+        B.bf_batch_set_autotune(b, True)
     try:
         t0 = B.bf_batch_now(b)
         tickets = []
@@ -87,6 +90,8 @@ def run_batched(scene_list, n_steps=None, n_workers=16, budget_bytes=150 << 30, 
             B.bf_batch_release(b, t)
         out = _summary(lat, steps, t_end - t0)
         out.update({"workers": n_workers, "scenes": len(scene_list), "failed": bad})
+        if autotune:
+            out["pcg_mode_by_size_bucket"] = {str(k): v for k, v in B.bf_batch_tuned(b).items()}
         return out, handles
     finally:
         B.bf_batch_destroy(b)

@@ -75,3 +75,28 @@ def test_serve_small_stream(torch_cuda):
     out = serving.serve(reqs, n_steps=3, n_workers=4)
     assert out["failed"] == 0 and out["steps"] == 36, out
     assert out["p99_step_ms"] >= out["p50_step_ms"] > 0
+
+
+def test_alone_equals_in_the_mix_with_autotuning(torch_cuda):
+    """per-bucket PCG autotuning in the batch: the buckets get a tuned
+    configuration and a scene still ends where it ends alone (within the
+    mixed-precision tolerance: the configuration changes only the order of
+    floating-point sums)"""
+    seeds = [3, 7, 11, 19, 23, 31, 37, 41]
+    target = scenes.batch_scene(seeds[0])
+    h, keep = serving.create(target)
+    st, stats = B.bf_step(h, 10)
+    xa, va = B.bf_get_state(h, target.nv)
+    B.bf_scene_destroy(h)
+    mix = [scenes.batch_scene(s) for s in seeds]
+    out, handles = serving.run_batched(mix, n_steps=10, n_workers=3, autotune=True)
+    try:
+        xm, vm = B.bf_get_state(handles[0][0], target.nv)
+    finally:
+        serving.destroy(handles)
+    assert out["failed"] == 0 and out["steps"] == 10 * len(seeds)
+    tuned = out["pcg_mode_by_size_bucket"]
+    assert len(tuned) >= 1 and all(m in (0, 1, 2, 17, 18, 33, 34) for m in tuned.values())
+    tol = 1e-4 * target.bbox_diag()
+    assert np.abs(xa - xm).max() <= tol, np.abs(xa - xm).max()
+    assert np.abs(va - vm).max() <= tol / target.params.dt
