@@ -374,6 +374,8 @@ def main():
                     help="timed steps of the eight-cube scene with the corotated material (0: skip)")
     ap.add_argument("--nh-steps", type=int, default=20,
                     help="timed steps of the eight-cube scene with the Neo-Hookean material (0: skip)")
+    ap.add_argument("--reuse-steps", type=int, default=20,
+                    help="timed steps of the eight-cube scene with the CCD-reuse option (0: skip)")
     ap.add_argument("--pcg-mode", type=int, default=-1,
                     help="fixed PCG execution configuration (bf_set_pcg_mode) instead of the autotuner's choice; "
                          "for runs under a profiler, whose serialised launches distort the tuner's timings")
@@ -567,7 +569,7 @@ def main():
         large = run_large_bounded(args)
         _progress(f"large: {large.get('steps_per_s')} steps/s")
 
-    friction = cor = nh = None
+    friction = cor = nh = reuse = None
     if args.friction_steps > 0:  # from step 15 on the cubes are in contact
         friction = run_variant(args, seed, ws, B, scenes, stream, flush,
                                "the eight-cube scene (196,608 tets) with the friction of appendix A: mu_f = 0.5, "
@@ -584,6 +586,12 @@ def main():
                          "the eight-cube scene (196,608 tets) with the Neo-Hookean material (NH) and the inversion "
                          "bound of MaxStepSize", args.nh_steps, max(args.warmup, 15), model=2)
         _progress(f"nh: {nh['steps_per_s']:.1f} steps/s")
+    if args.reuse_steps > 0:
+        reuse = run_variant(args, seed, ws, B, scenes, stream, flush,
+                            "the eight-cube scene (196,608 tets) with the CCD-reuse option (one CCD per outer "
+                            "iteration serves UpdateActiveSet and MaxStepSize)", args.reuse_steps,
+                            max(args.warmup, 15), ccd_reuse=1)
+        _progress(f"ccd reuse: {reuse['steps_per_s']:.1f} steps/s")
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
@@ -621,6 +629,7 @@ def main():
                 "friction": friction,
                 "cor": cor,
                 "nh": nh,
+                "ccd_reuse": reuse,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "

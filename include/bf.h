@@ -85,7 +85,13 @@ typedef struct {
  * no friction; the paper uses k_min = 6 with friction).  res_tol > 0
  * replaces Eq. termination by the IPC-style criterion of section 6: a step's
  * outer loop ends once the gradient-norm residual (bf_newton_residual) at
- * x^[k] is below res_tol, checked before every outer iteration (0: off).  model selects the
+ * x^[k] is below res_tol, checked before every outer iteration (0: off).
+ * ccd_reuse = 1 updates the active set from the MaxStepSize segment
+ * x^[k] -> xhat^[k+1] instead of Alg. 1's x^[k] -> xhat^[k], so one CCD
+ * (one broad phase, one narrow pass) serves both per outer iteration and
+ * the pairs that cut a step join C one iteration earlier (a CCD fitted to
+ * the constraint-set expansion, the direction the paper's conclusion names;
+ * 0: Alg. 1 as printed).  model selects the
  * material of every tet: BF_MODEL_SNH (stable Neo-Hookean, section 3),
  * BF_MODEL_COR (corotated linear) or BF_MODEL_NH (Neo-Hookean,
  * Psi = mu/2 (|F|^2 - 3) - mu ln J + lam/2 (ln J)^2, +inf for J <= 0),
@@ -97,6 +103,7 @@ enum { BF_MODEL_SNH = 0, BF_MODEL_COR = 1, BF_MODEL_NH = 2 };
 typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v, res_tol;
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model;
+    int32_t ccd_reuse;
 } bf_params;
 
 /* Per-time-step statistics (the columns of Tab. 1 / Tab. 2). */

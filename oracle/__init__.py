@@ -31,7 +31,8 @@ class OrParams(C.Structure):
                 ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
                 ("eps_v", C.c_double), ("res_tol", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
-                ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32)]
+                ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32),
+                ("ccd_reuse", C.c_int32)]
 
 
 class OrStats(C.Structure):
@@ -248,6 +249,7 @@ def params_struct(p) -> OrParams:
                                                              p.max_ls, p.max_cg)
     s.precision = p.precision
     s.model = p.model
+    s.ccd_reuse = getattr(p, "ccd_reuse", 0)
     return s
 
 

@@ -1879,6 +1879,11 @@ int32_t or_min_distance(or_scene *S, const double *x, double *dmin)
 /* rule of section 5.2 (alpha < 1e-4 for 50 consecutive iterations ->   */
 /* mu *= 2, delta /= 2) acts within the step, and delta is reset each    */
 /* step; the outer loop is capped at max_outer (status -7).  With        */
+/* ccd_reuse the active set is updated from the MaxStepSize segment      */
+/* x^[k] -> xhat^[k+1] instead of Alg. 1's x^[k] -> xhat^[k]: one CCD    */
+/* per outer iteration, fitted to the constraint-set expansion (the      */
+/* direction the paper's conclusion names); the pairs that cut this step */
+/* join C one iteration earlier.  With                                   */
 /* res_tol > 0 the loop ends instead once the gradient-norm residual at  */
 /* x^[k] falls below res_tol (the IPC-style termination of section 6),   */
 /* checked before each outer iteration, from x^[0] = x^t on.             */
@@ -1924,7 +1929,7 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
             st.newton_iters += solve_subproblem(S, xtilde, xk, xhn, &cgi, &lsf);
             st.cg_iters += cgi;
             st.ls_fail += lsf;
-            or_update_active_set(S, xk, xh);
+            or_update_active_set(S, xk, S->p.ccd_reuse ? xhn : xh);
             double alpha = or_max_step_size(S, xk, xhn);
             for (int i = 0; i < n; ++i) xk[i] = (1.0 - alpha) * xk[i] + alpha * xhn[i];
             if (k + 1 >= S->p.k_min) beta = (1.0 - alpha) * beta;

@@ -37,6 +37,7 @@ typedef struct {
     double dt, delta, gravity[3], eps, cg_tol, gamma_decay, c_mu, s_ccd, mu_f, eps_v;
     double res_tol; /* > 0: end the outer loop once the gradient-norm residual is below it (not beta) */
     int32_t k_min, max_outer, max_newton, max_ls, max_cg, precision, model; /* model: 0 SNH, 1 COR, 2 NH */
+    int32_t ccd_reuse; /* 1: UpdateActiveSet takes the MaxStepSize segment x^[k] -> xhat^[k+1] */
 } or_params;
 
 typedef struct {

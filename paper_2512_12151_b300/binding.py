@@ -36,7 +36,8 @@ class bf_params(C.Structure):
                 ("c_mu", C.c_double), ("s_ccd", C.c_double), ("mu_f", C.c_double),
                 ("eps_v", C.c_double), ("res_tol", C.c_double), ("k_min", C.c_int32),
                 ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_ls", C.c_int32),
-                ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32)]
+                ("max_cg", C.c_int32), ("precision", C.c_int32), ("model", C.c_int32),
+                ("ccd_reuse", C.c_int32)]
 
 
 class bf_step_stats(C.Structure):
@@ -172,6 +173,7 @@ def make_params(p) -> bf_params:
     s.eps, s.cg_tol, s.gamma_decay, s.c_mu, s.s_ccd = p.eps, p.cg_tol, p.gamma_decay, p.c_mu, p.s_ccd
     s.mu_f, s.eps_v = p.mu_f, p.eps_v
     s.res_tol = getattr(p, "res_tol", 0.0)
+    s.ccd_reuse = getattr(p, "ccd_reuse", 0)
     s.k_min, s.max_outer, s.max_newton, s.max_ls, s.max_cg = (p.k_min, p.max_outer, p.max_newton,
                                                              p.max_ls, p.max_cg)
     s.model = p.model

@@ -434,7 +434,8 @@ static int step_once(Scene &S, bf_step_stats *out)
         // x^k -> xhat^{k+1}: one broad phase serves both
         int nh = 0;
         double alpha = 1.0;
-        rc = run_ccd_two(S, S.xk, S.xh_prev, S.xh, &nh, &alpha);
+        rc = S.prm.ccd_reuse ? run_ccd_reuse(S, S.xk, S.xh, &nh, &alpha)  // one CCD for both
+                             : run_ccd_two(S, S.xk, S.xh_prev, S.xh, &nh, &alpha);
         if (rc) return rc;
         rc = apply_active_set_hits(S, nh);
         if (rc) return rc;

@@ -712,9 +712,8 @@ __global__ void k_narrow(int n, const int2 *__restrict__ cand, const int *__rest
         }
     }
     if (!accd(TYPE, p0, p1, s, 1.0, max_iter, &t)) return;
-    if (mode == 0) {
-        atomic_min_pos(toi_min, t);
-    } else {
+    if (mode != 1) atomic_min_pos(toi_min, t);  // mode 0: min TOI, 1: hits, 2: both
+    if (mode != 0) {
         const int idx = atomicAdd(nhit, 1);
         if (idx < hit_cap) {
             hit_type[idx] = TYPE;
@@ -893,25 +892,24 @@ static int broad_phase(Scene &S, const double *x0, const double *x1, const doubl
     return BF_OK;
 }
 
-// Narrow phase over the listed pairs: min TOI (with NH also the inversion
-// bound) to *alpha_out, or every hit
+// Narrow phase over the listed pairs, mode 0: min TOI (with NH also the
+// inversion bound) to *alpha_out; 1: every hit; 2: both in one pass (the
+// CCD reuse of the active-set update).  Hits:
 // (type, a, b, toi) stored and counted to *nhits_out.  With `filter` the
 // lists cover a wider motion: a pair goes on only if its exact swept boxes
 // along x0 -> x1 overlap, so exactly the candidates of this motion remain.
-static void launch_narrow(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,
-                          bool collect_hits)
+static void launch_narrow(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter, int mode)
 {
     const double s = S.prm.s_ccd;
-    if (collect_hits) {
-        cudaMemsetAsync(S.dflag + F_NHIT, 0, sizeof(int), S.stream);
-    } else {
+    if (mode != 0) cudaMemsetAsync(S.dflag + F_NHIT, 0, sizeof(int), S.stream);
+    if (mode != 1) {
         const double one = 1.0;
         cudaMemcpyAsync(S.dscal + S_TOI, &one, sizeof(double), cudaMemcpyHostToDevice, S.stream);
     }
     ScopedTimer tm(S, T_CCD_NARROW);
     auto launch = [&](auto kern, int n, const int2 *cand) {
         if (!n) return;
-        kern<<<cdiv(n, 128), 128, 0, S.stream>>>(n, cand, S.st, S.se, x0, x1, s, kAccdMaxIter, collect_hits ? 1 : 0,
+        kern<<<cdiv(n, 128), 128, 0, S.stream>>>(n, cand, S.st, S.se, x0, x1, s, kAccdMaxIter, mode,
                                                 S.dscal + S_TOI, S.hit_type, S.hit_a, S.hit_b, S.hit_toi, S.hit_cap,
                                                 S.dflag + F_NHIT);
         ++S.n_launch;
@@ -925,14 +923,14 @@ static void launch_narrow(Scene &S, const double *x0, const double *x1, int npt,
     }
     // NH is not defined for inverted elements: MaxStepSize also keeps every
     // element's volume (section 4.1)
-    if (!collect_hits && S.prm.model == BF_MODEL_NH) launch_inversion_bound(S, x0, x1, S.dscal + S_TOI);
+    if (mode != 1 && S.prm.model == BF_MODEL_NH) launch_inversion_bound(S, x0, x1, S.dscal + S_TOI);
 }
 
 static int narrow_phase(Scene &S, const double *x0, const double *x1, int npt, int nee, bool filter,
                         bool collect_hits, double *alpha_out, int *nhits_out)
 {
     for (int attempt = 0; attempt < 3; ++attempt) {
-        launch_narrow(S, x0, x1, npt, nee, filter, collect_hits);
+        launch_narrow(S, x0, x1, npt, nee, filter, collect_hits ? 1 : 0);
         int st = sync_flags(S);
         if (st) return st;
         if (!collect_hits) {
@@ -969,14 +967,38 @@ int run_ccd_two(Scene &S, const double *x0, const double *xa, const double *xb, 
     int st = broad_phase(S, x0, xa, xb, &npt, &nee);
     if (st) return st;
     for (int attempt = 0; attempt < 3; ++attempt) {  // both narrow passes, one synchronisation
-        launch_narrow(S, x0, xa, npt, nee, true, true);
-        launch_narrow(S, x0, xb, npt, nee, true, false);
+        launch_narrow(S, x0, xa, npt, nee, true, 1);
+        launch_narrow(S, x0, xb, npt, nee, true, 0);
         st = sync_flags(S);
         if (st) return st;
         const int nh = S.h_flag[F_NHIT];
         if (nh <= S.hit_cap) {
             *nhits_a = nh;
             *alpha_b = std::min(1.0, S.h_scal[S_TOI]);
+            return BF_OK;
+        }
+        st = ccd_reserve(S, 0, 0, nh);
+        if (st) return st;
+    }
+    return BF_E_CAPACITY;
+}
+
+// CCD reuse (option ccd_reuse): the MaxStepSize segment x0 -> x1 gives
+// both the step bound and the hits of the active-set update, from one
+// broad phase over the two position sets and one narrow pass.
+int run_ccd_reuse(Scene &S, const double *x0, const double *x1, int *nhits, double *alpha)
+{
+    int npt = 0, nee = 0;
+    int st = broad_phase(S, x0, x1, nullptr, &npt, &nee);
+    if (st) return st;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        launch_narrow(S, x0, x1, npt, nee, false, 2);
+        st = sync_flags(S);
+        if (st) return st;
+        const int nh = S.h_flag[F_NHIT];
+        if (nh <= S.hit_cap) {
+            *nhits = nh;
+            *alpha = std::min(1.0, S.h_scal[S_TOI]);
             return BF_OK;
         }
         st = ccd_reserve(S, 0, 0, nh);

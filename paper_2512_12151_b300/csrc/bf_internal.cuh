@@ -222,6 +222,8 @@ void launch_elastic(Scene &S, const double *xhat);
 double run_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat);
 // L(xhat) into *out (device), no synchronisation
 void launch_energy(Scene &S, const double *xtilde, const double *xlin, const double *xhat, double *out);
+// one CCD along x0 -> x1 for both the active-set hits and the step bound
+int run_ccd_reuse(Scene &S, const double *x0, const double *x1, int *nhits, double *alpha);
 // inversion bound of MaxStepSize along x0 -> x1, min-reduced into *tmin
 void launch_inversion_bound(Scene &S, const double *x0, const double *x1, double *tmin);
 double run_mu_max_diag(Scene &S);

@@ -60,6 +60,7 @@ class Params:
     max_cg: int = 10000
     precision: int = 0  # 0 = FP64, 1 = mixed (FP32 Hessian/SpMV/preconditioner)
     model: int = 0      # material: 0 = stable Neo-Hookean (SNH), 1 = corotated linear (COR), 2 = Neo-Hookean (NH)
+    ccd_reuse: int = 0  # 1: UpdateActiveSet reuses the MaxStepSize CCD (x^[k] -> xhat^[k+1])
 
 
 @dataclass
