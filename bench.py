@@ -251,6 +251,7 @@ def run_large(args, torch, B, scenes, peak, stream):
     step timed with CUDA events; per-kernel timers on for the PCG roofline
     (the matrix no longer fits in shared memory: HBM streaming)."""
     s = scenes.spiky_balls(precision=1)
+    s.params.ccd_reuse = args.large_reuse
     sim = B.Sim(s, stream=stream.cuda_stream)
     B.bf_enable_timers(sim.h, True)
     ms, stats = [], []
@@ -279,7 +280,8 @@ def run_large(args, torch, B, scenes, peak, stream):
     srt = sorted(ms)
     return {"workload": f"spiky balls: 5 balls (radius 0.1 m, 64 spikes 0.02-0.05 m), {s.nt} tets, {s.nv} vertices, "
                         "grid Kuhn mesher (3.9 mm cells), open 0.66 m box, plate moving down at 0.5 m/s; "
-                        "E = 5e4 Pa, nu = 0.45, h = 1/60 s, mixed precision; first steps from rest",
+                        "E = 5e4 Pa, nu = 0.45, h = 1/60 s, mixed precision; first steps from rest" +
+                        ("; CCD-reuse option" if args.large_reuse else ""),
             "steps": args.large_steps, "steps_per_s": args.large_steps / (total / 1e3), "unit": "steps/s",
             "ms_per_step": total / args.large_steps, "p50_step_ms": srt[len(srt) // 2],
             "p99_step_ms": srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))],
@@ -295,11 +297,12 @@ def run_large(args, torch, B, scenes, peak, stream):
                              "pcg_config": cfg}}
 
 
-def run_large_bounded(args):
+def run_large_bounded(args, reuse=0):
     """run_large in a child process with a wall-clock bound, so that one
     exceptionally long time step cannot stall the whole benchmark; the line
     reports what the child finished"""
-    cmd = [sys.executable, os.path.abspath(__file__), "--large-only", "--large-steps", str(args.large_steps)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--large-only", "--large-steps", str(args.large_steps),
+           "--large-reuse", str(reuse)]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=args.large_timeout)
         sys.stderr.write(r.stderr)
@@ -380,6 +383,9 @@ def main():
                     help="fixed PCG execution configuration (bf_set_pcg_mode) instead of the autotuner's choice; "
                          "for runs under a profiler, whose serialised launches distort the tuner's timings")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--large-reuse", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-large-reuse", action="store_true",
+                    help="skip the large scene's second run with the CCD-reuse option")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -564,10 +570,13 @@ def main():
         _progress(f"served: {served['steps_per_s']:.1f} steps/s")
         served["steps_per_s"] = allsum(ws, served["steps"]) / allmax(ws, served["seconds"])
 
-    large = None
+    large = large_reuse = None
     if args.large_steps > 0:
         large = run_large_bounded(args)
         _progress(f"large: {large.get('steps_per_s')} steps/s")
+        if not args.no_large_reuse:
+            large_reuse = run_large_bounded(args, reuse=1)
+            _progress(f"large with CCD reuse: {large_reuse.get('steps_per_s')} steps/s")
 
     friction = cor = nh = reuse = None
     if args.friction_steps > 0:  # from step 15 on the cubes are in contact
@@ -626,6 +635,7 @@ def main():
                 "batched_vs_plain_fp64": (batched["steps_per_s"] / plain["steps_per_s"]) if batched and plain
                 else None,
                 "large": large,
+                "large_ccd_reuse": large_reuse,
                 "friction": friction,
                 "cor": cor,
                 "nh": nh,

@@ -4,7 +4,8 @@ the oracle on sampled outputs: the FP64 gradient and the FP32 Hessian
 action at 300 random free vertices, each computed one by one from the
 oracle's element function (incident tets), the lumped mass and the
 inertia term; the CCD hit set and TOIs of a full-size motion (bit-exact);
-and two time steps of the moving plate that complete."""
+and two time steps of the moving plate that complete, with and without the
+CCD-reuse option."""
 import numpy as np
 import pytest
 
@@ -117,9 +118,11 @@ def test_large_ccd_full_size(torch_cuda, spiky):
     sim.close()
 
 
-def test_large_steps_complete(torch_cuda, spiky):
+@pytest.mark.parametrize("reuse", [0, 1])
+def test_large_steps_complete(torch_cuda, spiky, reuse):
+    """two steps of the moving plate, with and without the CCD-reuse option"""
     s = spiky
-    sim = B.Sim(s)
+    sim = B.Sim(s, scenes.Params(**{**s.params.__dict__, "ccd_reuse": reuse}))
     for i in range(2):
         B.bf_set_obstacle_targets(sim.h, scenes.plate_targets_schedule(s, i))
         st, stats = sim.step(1)
