@@ -368,6 +368,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-workers", type=int, default=32,
+                    help="worker streams of the served stream (more streams: shorter step latency)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="steps of the 2.3M-tet spiky-ball compression scene (0: skip)")
     ap.add_argument("--large-timeout", type=float, default=240.0)
@@ -566,7 +568,7 @@ def main():
     if args.serve_requests > 0:
         from paper_2512_12151_b300 import serving
         reqs = serving.poisson_requests(args.serve_requests, args.serve_rate, seed=1000 + rank)
-        served = serving.serve(reqs, n_steps=10, n_workers=args.batch_workers)
+        served = serving.serve(reqs, n_steps=10, n_workers=args.serve_workers)
         _progress(f"served: {served['steps_per_s']:.1f} steps/s")
         served["steps_per_s"] = allsum(ws, served["steps"]) / allmax(ws, served["seconds"])
 
