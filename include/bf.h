@@ -134,6 +134,11 @@ int bf_scene_create(const bf_mesh_desc *mesh, const bf_params *params, const bf_
 int bf_scene_destroy(bf_scene *scene);
 int bf_set_stream(bf_scene *scene, void *stream);
 
+/* Host waits of the scene's steps: 0 (default) synchronises the stream
+ * (the waiting thread spins: lowest latency); 1 waits on a blocking-sync
+ * event (the thread sleeps: for many worker threads sharing host cores). */
+int bf_set_sync_mode(bf_scene *scene, int32_t blocking);
+
 /* Checkpoint of the evolving state (no counterpart in the paper; lets a
  * server evict a scene and re-admit it later): positions, velocities, the
  * active set with multipliers and decay factors, mu and delta, and the
@@ -415,6 +420,9 @@ double bf_batch_now(bf_batch *batch);
  * is tuned with bf_autotune_pcg after its first step, and every scene of
  * that bucket takes the chosen configuration at its next turn. */
 int bf_batch_set_autotune(bf_batch *batch, int32_t on);
+/* Admitted scenes wait with blocking-sync events (bf_set_sync_mode 1) until
+ * released (off by default). */
+int bf_batch_set_blocking_sync(bf_batch *batch, int32_t on);
 /* The tuned buckets so far, ascending: up to cap (bucket, mode) pairs into
  * buckets / modes (host); *n (host, may be NULL) = their count. */
 int bf_batch_tuned(bf_batch *batch, int32_t cap, int32_t *buckets, int32_t *modes, int32_t *n);

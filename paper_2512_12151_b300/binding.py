@@ -128,6 +128,8 @@ def lib():
         "bf_batch_release": [_P, C.c_int64],
         "bf_batch_info": [_P, _P],
         "bf_batch_set_autotune": [_P, C.c_int32],
+        "bf_batch_set_blocking_sync": [_P, C.c_int32],
+        "bf_set_sync_mode": [_P, C.c_int32],
         "bf_batch_tuned": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     }
     for name, args in sig.items():
@@ -515,6 +517,14 @@ def bf_batch_result(b, ticket, cap):
 
 def bf_batch_release(b, ticket):
     _check("bf_batch_release", lib().bf_batch_release(b, ticket))
+
+
+def bf_batch_set_blocking_sync(b, on=True):
+    _check("bf_batch_set_blocking_sync", lib().bf_batch_set_blocking_sync(b, 1 if on else 0))
+
+
+def bf_set_sync_mode(h, blocking):
+    _check("bf_set_sync_mode", lib().bf_set_sync_mode(h, 1 if blocking else 0))
 
 
 def bf_batch_set_autotune(b, on=True):

@@ -89,7 +89,13 @@ int sync_flags(Scene &S)
 {
     cudaMemcpyAsync(S.h_scal, S.dscal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, S.stream);
     cudaMemcpyAsync(S.h_flag, S.dflag, F_NFLAG * sizeof(int), cudaMemcpyDeviceToHost, S.stream);
-    cudaError_t e = cudaStreamSynchronize(S.stream);
+    cudaError_t e;
+    if (S.sync_blocking && S.sync_ev) {
+        e = cudaEventRecord(S.sync_ev, S.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(S.sync_ev);
+    } else {
+        e = cudaStreamSynchronize(S.stream);
+    }
     if (e != cudaSuccess) return BF_E_CUDA;
     return check_cuda(cudaGetLastError());
 }
@@ -828,6 +834,8 @@ static void destroy(Scene &S)
 {
     if (S.stream) cudaStreamSynchronize(S.stream);
     pcg_release(S);
+    if (S.sync_ev) cudaEventDestroy(S.sync_ev);
+    S.sync_ev = nullptr;
     std::vector<void *> o = S.owned;
     for (void *p : o) dev_free(S, p);
     if (S.h_scal) cudaFreeHost(S.h_scal);
@@ -913,6 +921,18 @@ int bf_scene_destroy(bf_scene *scene)
     if (!scene) return BF_E_ARG;
     destroy(scene->s);
     delete scene;
+    return BF_OK;
+}
+
+int bf_set_sync_mode(bf_scene *scene, int32_t blocking)
+{
+    SCENE_OR_ARG(scene);
+    if (blocking && !S.sync_ev &&
+        cudaEventCreateWithFlags(&S.sync_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+        S.sync_ev = nullptr;
+        return BF_E_CUDA;
+    }
+    S.sync_blocking = blocking != 0;
     return BF_OK;
 }
 

@@ -61,6 +61,7 @@ struct bf_batch {
     int device = 0, finished = 0;
     bool stop = false;
     bool autotune = false;
+    bool blocking = false;  // admitted scenes wait with blocking-sync events
     std::unordered_map<int, int> tuned;  // size bucket -> PCG mode
     std::unordered_set<int> tuning;     // buckets being tuned right now
     Clock::time_point epoch;
@@ -186,6 +187,7 @@ int bf_batch_admit(bf_batch *b, bf_scene *scene, int32_t n_steps, int64_t *ticke
     b->pending[w] += work * n_steps;
     lk.unlock();
     rc = bf_set_stream(scene, b->streams[w]);  // the scene is not running yet
+    if (!rc && b->blocking) rc = bf_set_sync_mode(scene, 1);
     lk.lock();
     if (rc) {
         b->resident -= bytes;
@@ -252,6 +254,7 @@ int bf_batch_release(bf_batch *b, int64_t ticket)
     if (it == b->jobs.end()) return BF_E_NOT_FOUND;
     if (!it->second->finished) return BF_E_ARG;
     bf_set_stream(it->second->scene, nullptr);  // the scene goes back to the default stream
+    bf_set_sync_mode(it->second->scene, 0);
     b->jobs.erase(it);
     return BF_OK;
 }
@@ -272,6 +275,14 @@ int bf_batch_info(bf_batch *b, int64_t *info)
 }
 
 double bf_batch_now(bf_batch *b) { return b ? b->now() : -1.0; }
+
+int bf_batch_set_blocking_sync(bf_batch *b, int32_t on)
+{
+    if (!b) return BF_E_ARG;
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->blocking = on != 0;
+    return BF_OK;
+}
 
 int bf_batch_set_autotune(bf_batch *b, int32_t on)
 {

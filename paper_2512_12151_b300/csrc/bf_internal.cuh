@@ -65,6 +65,10 @@ struct Scene {
     // the step's mu_init left the inertia and elastic parts of G and H at
     // the first Newton iterate: the next assembly adds only the rest
     bool elastic_ready = false;
+    // host waits sleep on a blocking-sync event instead of spinning
+    // (scenes of a batch: many worker threads share the host cores)
+    bool sync_blocking = false;
+    cudaEvent_t sync_ev = nullptr;
     int has_targets = 0;
     cudaStream_t stream = nullptr;
     bf_allocator alloc{};

@@ -150,7 +150,7 @@ def poisson_requests(n, rate, seed=0, t_lo=2e3, t_hi=2e5, precision=1):
 
 
 def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002, timeout_s=900.0,
-          n_creators=8):
+          n_creators=8, blocking_sync=False):
     """Serves a request stream: at each arrival time the request is handed
     to one of `n_creators` host threads, which generates and creates its
     scene and admits it to the running batch (waiting while the HBM budget
@@ -158,9 +158,13 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
     complete.  Returns aggregate steps/s (first arrival to last completion),
     per-step latency p50/p99 (completion of a step minus completion of the
     scene's previous step, or its admission) and the admission wait
-    (admission minus arrival, scene creation included) p50/p99."""
+    (admission minus arrival, scene creation included) p50/p99.  With
+    `blocking_sync` the batch's worker threads sleep in their waits
+    (bf_batch_set_blocking_sync): shorter step latency, longer admission."""
     from concurrent.futures import ThreadPoolExecutor
     b = B.bf_batch_create(n_workers, budget_bytes)
+    if blocking_sync:  # worker threads sleep in their waits, leaving host cores to the creators
+        B.bf_batch_set_blocking_sync(b, True)
     deadline = time.monotonic() + timeout_s
     live = {}  # ticket -> (handle, keep)
     lat, waits, steps, bad, statuses = [], [], 0, 0, []
