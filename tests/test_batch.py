@@ -100,3 +100,20 @@ def test_alone_equals_in_the_mix_with_autotuning(torch_cuda):
     tol = 1e-4 * target.bbox_diag()
     assert np.abs(xa - xm).max() <= tol, np.abs(xa - xm).max()
     assert np.abs(va - vm).max() <= tol / target.params.dt
+
+
+def test_blocking_sync_mode_gives_the_same_steps(torch_cuda):
+    """bf_set_sync_mode changes how the host waits, not what is computed:
+    the same scene stepped with blocking-sync waits ends where the default
+    run ends (up to the order of floating-point atomics)"""
+    s = scenes.batch_scene(5, precision=0)
+    out = []
+    for blocking in (0, 1):
+        h, keep = serving.create(s)
+        B.bf_set_sync_mode(h, blocking)
+        st, stats = B.bf_step(h, 8)
+        assert st == 0
+        out.append(B.bf_get_state(h, s.nv))
+        B.bf_scene_destroy(h)
+    (xa, va), (xb, vb) = out
+    assert np.abs(xa - xb).max() <= 1e-9 * s.bbox_diag()
