@@ -4,7 +4,8 @@ block resting on an incline, mu_f = 0.6 > tan theta), one step in FP64
 (positions within 1e-6 x the bounding-box diagonal, the same contact count
 and outer iterations) and mixed precision (1e-4); and a residual-terminated
 step with friction and NH (the same outer iterations, residual log within
-1e-5 relative, positions within 1e-6)."""
+1e-5 relative, positions within 1e-6); and the CCD-reuse option with
+friction and NH (one FP64 step)."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,23 @@ def test_residual_mode_with_friction_and_nh(torch_cuda):
     log_o, log_g = o.residual_log(), B.bf_get_residual_log(sim.h)
     assert sg[0]["outer_iters"] == so[0]["outer_iters"] and len(log_g) == len(log_o)
     assert np.abs(log_g - log_o).max() <= 1e-5 * log_o.max()
+    xo, _ = o.get_state()
+    xg, _ = sim.state()
+    assert np.abs(xg - xo).max() <= 1e-6 * s.bbox_diag()
+    sim.close()
+
+
+def test_ccd_reuse_with_friction_and_nh(torch_cuda):
+    """the CCD-reuse option with NH and friction: one FP64 step from the
+    resting state equals the oracle's (outer iterations, contact count,
+    positions within 1e-6 x the diagonal)"""
+    state = resting(2)
+    s = state[0]
+    sim, o = make_pair(state, ccd_reuse=1)
+    _, so = o.step(1)
+    st, sg = sim.step(1)
+    assert st == 0
+    assert sg[0]["outer_iters"] == so[0]["outer_iters"] and sg[0]["n_contacts"] == so[0]["n_contacts"]
     xo, _ = o.get_state()
     xg, _ = sim.state()
     assert np.abs(xg - xo).max() <= 1e-6 * s.bbox_diag()
