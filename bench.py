@@ -379,6 +379,8 @@ def main():
                     help="timed steps of the eight-cube scene with the corotated material (0: skip)")
     ap.add_argument("--nh-steps", type=int, default=20,
                     help="timed steps of the eight-cube scene with the Neo-Hookean material (0: skip)")
+    ap.add_argument("--paper-tol-steps", type=int, default=20,
+                    help="timed steps of the eight-cube scene at the paper's CG tolerance 1e-4 (0: skip)")
     ap.add_argument("--reuse-steps", type=int, default=20,
                     help="timed steps of the eight-cube scene with the CCD-reuse option (0: skip)")
     ap.add_argument("--pcg-mode", type=int, default=-1,
@@ -580,7 +582,7 @@ def main():
             large_reuse = run_large_bounded(args, reuse=1)
             _progress(f"large with CCD reuse: {large_reuse.get('steps_per_s')} steps/s")
 
-    friction = cor = nh = reuse = None
+    friction = cor = nh = reuse = paper_tol = None
     if args.friction_steps > 0:  # from step 15 on the cubes are in contact
         friction = run_variant(args, seed, ws, B, scenes, stream, flush,
                                "the eight-cube scene (196,608 tets) with the friction of appendix A: mu_f = 0.5, "
@@ -603,6 +605,12 @@ def main():
                             "iteration serves UpdateActiveSet and MaxStepSize)", args.reuse_steps,
                             max(args.warmup, 15), ccd_reuse=1)
         _progress(f"ccd reuse: {reuse['steps_per_s']:.1f} steps/s")
+    if args.paper_tol_steps > 0:
+        paper_tol = run_variant(args, seed, ws, B, scenes, stream, flush,
+                                "the eight-cube scene (196,608 tets) at the paper's CG relative tolerance 1e-4 "
+                                "(the configured workload uses 1e-6)", args.paper_tol_steps, max(args.warmup, 15),
+                                cg_tol=1e-4)
+        _progress(f"paper tolerance: {paper_tol['steps_per_s']:.1f} steps/s")
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
@@ -642,6 +650,7 @@ def main():
                 "cor": cor,
                 "nh": nh,
                 "ccd_reuse": reuse,
+                "cg_tol_1e-4": paper_tol,
                 "serving": None if served is None else dict(
                     served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at "
                     f"{args.serve_rate:g}/s, scenes 2k-200k tets log-uniform (same generator), 10 steps each, "
