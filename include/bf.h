@@ -307,10 +307,11 @@ int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double 
 
 /* Allocation-free MaxStepSize over explicit pairs: *alpha = min(1, min_i
  * TOI_i) over n pairs of one type (0 = PT, 1 = EE), with TOI_i the additive
- * CCD result that bf_accd returns for the same pair and s (so alpha equals
- * min(1, min of bf_accd's output) exactly).  x0, x1 (device, n*12), alpha
- * (device, 1 double).  stream: cudaStream_t or NULL; the call synchronizes
- * that stream before it returns.
+ * CCD result that bf_accd returns for the same pair and s (so, for finite
+ * inputs, alpha equals min(1, min of bf_accd's output) exactly; a pair with
+ * a non-finite coordinate gives alpha = 0, no step).  x0, x1 (device, n*12),
+ * alpha (device, 1 double).  stream: cudaStream_t or NULL; the call
+ * synchronizes that stream before it returns.
  *
  * The paper has no counterpart of this entry point: it exists for callers
  * that may not allocate device memory once they are running (a host that
@@ -321,7 +322,9 @@ int bf_accd(int32_t type, int32_t n, const double *x0, const double *x1, double 
  * larger n returns BF_E_ARG without launching anything.
  * - The first call on each device looks up the array's device address and
  *   caches it, so make that first call (n may be 0) before any stream
- *   capture.
+ *   capture.  The cached address belongs to the device's primary context
+ *   (the one the CUDA runtime uses); after cudaDeviceReset, or from another
+ *   context, it is stale: do not call the entry point there.
  * - The array is shared by all calls on a device and keeps the previous
  *   call's contents; each call resets the part that must start at zero.
  *   Calls that overlap on the GPU (other streams, threads or processes
@@ -343,21 +346,26 @@ int bf_enable_timers(bf_scene *scene, int32_t on);
  * CTAs per SM (default 1), keeping the matrix in shared memory when it
  * fits, else streaming it, with the per-row vectors in global memory when
  * they do not fit in shared memory either; adding 16 forbids the
- * shared-memory copy of the matrix; adding 32 forces the global-memory
- * variant.  Same arithmetic in every mode. */
+ * shared-memory copy of the matrix; adding 32 forces a global-memory
+ * variant: in mixed precision the symmetric one (upper blocks streamed
+ * once, transposed products by vector reductions into global memory),
+ * else, or with 64 added, the one that streams both triangles.  The same
+ * method in every mode; the order of floating-point sums differs. */
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
 
 /* Configuration of the persistent PCG chosen at the scene's first solve
  * (host int32[8]): mode, CTAs, threads per CTA, shared memory bytes per
  * CTA, variant (0: blocks streamed through the BSR map, vectors in shared
  * memory; 1: blocks resident in shared memory; 2: blocks streamed from a
- * jagged global copy, per-row vectors in global memory), max rows, max
- * blocks and max window vertices per CTA (zeros before the first solve). */
+ * jagged global copy, per-row vectors in global memory; 3: upper blocks
+ * streamed from a jagged global copy, transposed products reduced in global
+ * memory), max rows, max blocks and max window vertices per CTA (zeros
+ * before the first solve). */
 int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
 
 /* PCG autotuner: on the system assembled last (bf_step or bf_assemble must
  * have run), times `iters` (>= 8) PCG iterations of each execution
- * configuration (bf_set_pcg_mode 1, 2, 17, 18, 33, 34 and 0; a persistent
+ * configuration (bf_set_pcg_mode 1, 2, 17, 18, 33, 34, 97, 98 and 0; a persistent
  * configuration that does not fit is skipped) with CUDA events on the
  * scene's stream, then sets the fastest per iteration (a configuration later
  * in that list replaces the choice so far only when it is more than 2 %

@@ -89,6 +89,14 @@ struct PcgArgs {
     int maxit, max_replace, max_rows, max_ent, max_win, max_len, kc;
     double *dscal;
     int *dflag;
+    // symmetric variant: upper blocks in jagged order (9 planes of nup
+    // values), their window offsets, the upper row pointer, and the
+    // accumulation vector of transposed products and contact terms
+    const float *uval;
+    const unsigned short *unbr;
+    const int *urowptr;
+    size_t nup;
+    float4 *yq;
 };
 
 enum { PCG_RUN = 0, PCG_DONE, PCG_MAXIT, PCG_BAD, PCG_FOLD, PCG_ABORT };
@@ -311,8 +319,10 @@ struct PcgLayout {
 // Modes: 0 = blocks read from the BSR values through the full-row map,
 // vectors in shared memory; 1 = blocks resident in shared memory; 2 = blocks
 // streamed from a jagged copy in global memory (coalesced), per-row vectors
-// in global memory (systems whose rows do not fit in shared memory).
-enum { PCG_STREAM = 0, PCG_RESIDENT = 1, PCG_GLOBAL = 2 };
+// in global memory (systems whose rows do not fit in shared memory); 3 =
+// upper blocks only streamed from a jagged copy, transposed products
+// accumulated in global memory (mixed precision; k_pcg_sym below).
+enum { PCG_STREAM = 0, PCG_RESIDENT = 1, PCG_GLOBAL = 2, PCG_SYM = 3 };
 
 __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
                                                 int max_len, int mode, int kc)
@@ -813,6 +823,492 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric variant for systems whose rows do not fit in shared memory
+// (mixed precision).  The matrix is symmetric (section 5.1 stores its upper
+// triangle), so each upper block B_ij (i < j) is streamed once and used
+// twice: B_ij p_j joins row i's sum in registers, and B_ij^T p_i goes to
+// row j through a vector reduction (red.global.add.v4.f32) into the
+// accumulation vector yq, which the owner of row j reads (and clears) after
+// the grid-wide reduction that ends the product.  Contact terms add into
+// yq the same way.  The product p.Hp needs no complete q: with D_i the
+// diagonal blocks, p.Hp = sum_i p_i.D_i p_i + 2 sum_{i<j} p_i.B_ij p_j,
+// which each row's thread forms from its own blocks.
+//
+// Per CTA: rows [part[c], part[c+1]) in order of decreasing upper length
+// (jagged levels as in the full-row variants; level 0 is the diagonal
+// block), the window of p over [part[c], last upper neighbour] in shared
+// memory (16-bit offsets), r and the FP32 increment of x per row in shared
+// memory, the rows' part of q in registers (thread t owns the rows t,
+// t + blockDim.x, ... of the length order in both phases, at most
+// kSymMaxRowsPerThread), FP64 x and H x of the reliable updates in a
+// per-CTA global vector.
+// ---------------------------------------------------------------------------
+constexpr int kSymMaxRowsPerThread = 8;
+
+struct PcgSymLayout {
+    size_t p4, r, xl, rinfo, lvl, cg, cp, cw, cv, cm, total;
+};
+
+__host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win, int max_len, int kc)
+{
+    PcgSymLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    L.p4 = take(16 * (size_t)max_win);
+    L.r = take(12 * (size_t)max_rows);
+    L.xl = take(12 * (size_t)max_rows);
+    L.rinfo = take(4 * (size_t)max_rows);
+    L.lvl = take(4 * ((size_t)max_len + 1));
+    L.cg = take(48 * (size_t)kc);
+    L.cp = take(48 * (size_t)kc);
+    L.cw = take(4 * (size_t)kc);
+    L.cv = take(16 * (size_t)kc);
+    L.cm = take(4 * (size_t)kc);
+    L.total = o;
+    return L;
+}
+
+// per-CTA global vector of the symmetric variant: FP64 x and H x (3 per row each)
+inline size_t pcg_sym_vec_bytes(int max_rows) { return ((48 * (size_t)max_rows) + 255) & ~(size_t)255; }
+
+__device__ __forceinline__ void red_add4(float4 *dst, float a, float b, float c)
+{
+    atomicAdd(dst, make_float4(a, b, c, 0.f));  // vector reduction at L2 (sm_90+)
+}
+
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
+{
+    using CT = float;
+    using VT = float;
+    using RT = float;
+    constexpr int MAXR = kSymMaxRowsPerThread;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PcgCtl ctl;
+    __shared__ float2 red_f[2 * kPcgMaxWarps];
+    const float *__restrict__ gpinv = (const float *)A.pinv;
+    VT *__restrict__ z = (VT *)A.z;
+    VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
+    float4 *__restrict__ yq = A.yq;
+    const float *__restrict__ uv = A.uval;
+    const size_t nup = A.nup;
+    const int c = blockIdx.x;
+    const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
+    const int wlo = A.win[2 * c], whi = A.win[2 * c + 1], nwin = whi - wlo;  // wlo == r0
+    const size_t U0 = (size_t)A.urowptr[r0];  // the CTA's first jagged slot
+    const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int ncached = min(nco, A.kc);
+    const PcgSymLayout L = pcg_sym_layout(A.max_rows, A.max_win, A.max_len, A.kc);
+    const int ld = A.max_rows;  // per-row arrays are component-major: a[k * ld + row]
+    double *g_x = (double *)(A.gvec + (size_t)c * A.gvec_stride);
+    double *g_hx = g_x + 3 * (size_t)ld;
+    CT *s_p4 = (CT *)(smem + L.p4);
+    RT *s_r = (RT *)(smem + L.r);
+    RT *s_xl = (RT *)(smem + L.xl);
+    int *s_rinfo = (int *)(smem + L.rinfo);
+    int *s_lvl = (int *)(smem + L.lvl);
+    CT *s_cg = (CT *)(smem + L.cg);
+    CT *s_cp = (CT *)(smem + L.cp);
+    CT *s_cw = (CT *)(smem + L.cw);
+    int4 *s_cv = (int4 *)(smem + L.cv);
+    int *s_cm = (int *)(smem + L.cm);
+    for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) s_rinfo[t] = A.rinfo[r0 + t];
+    for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
+        const int i = c + k * (int)gridDim.x;
+        s_cv[k] = A.cv[i];
+        s_cm[k] = A.cmask[i];
+        s_cw[k] = (CT)A.cw[i];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) s_cg[12 * k + j] = (CT)A.cg[12 * (size_t)i + j];
+    }
+    for (int i = threadIdx.x; i < 4 * nwin; i += blockDim.x) s_p4[i] = CT(0);  // p_old = 0
+    // z = P r for local row `row` (written to global memory); returns r.z
+    auto precond = [&](int row, const RT *rv) -> CT {
+        const int a = r0 + row;
+        const float *P = gpinv + 9 * (size_t)a;
+        CT zc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            zc[k] = __ldg(P + 3 * k) * rv[0] + __ldg(P + 3 * k + 1) * rv[1] + __ldg(P + 3 * k + 2) * rv[2];
+            z[3 * a + k] = zc[k];
+        }
+        return (rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2];
+    };
+    unsigned nred = 0;
+    auto reduce = [&](auto &acc, auto on_total) {
+        constexpr int K = (int)std::extent<std::remove_reference_t<decltype(acc)>>::value;
+        double blk[K], tot[K];
+        block_sum<K>(acc, blk, red_f);
+        if (threadIdx.x == 0) {
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            else ctl.state = PCG_ABORT;
+        }
+        ++nred;
+        __syncthreads();
+    };
+    unsigned long long tA = 0, tA2 = 0, tB = 0, tB2 = 0, t0 = 0, tS = 0, tR = 0, tC = 0;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    __syncthreads();
+    // ---- init: r = b, x = 0, z = P r, p_old = 0, yq = 0 on the own rows ----
+    {
+        AccF acc[2] = {};
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+            const int a = r0 + i;
+            RT rv[3];
+            double bb = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double bk = A.b[3 * a + k];
+                rv[k] = (RT)bk;
+                s_r[k * ld + i] = rv[k];
+                s_xl[k * ld + i] = RT(0);
+                g_x[k * ld + i] = 0.0;
+                A.qd[3 * a + k] = 0.0;
+                if (A.nc > 0) pb[0][3 * a + k] = VT(0);
+                bb += bk * bk;
+            }
+            yq[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            acc[0].add(precond(i, rv));
+            acc[1].add(bb);
+        }
+        reduce(acc, [&](const double *t) {
+            ctl.rz = t[0];
+            ctl.bb = t[1];
+            ctl.rr = t[1];
+            ctl.rr_ref = t[1];
+            ctl.beta = 0.0;
+            ctl.bt = 0.f;
+            ctl.it = 0;
+            ctl.folds = 0;
+            if (t[1] > 0.0 && isfinite(t[1]) && isfinite(t[0])) ctl.state = PCG_RUN;
+            else ctl.state = t[1] == 0.0 ? PCG_DONE : PCG_BAD;
+        });
+    }
+    int parity = 0;
+    float qreg[MAXR][3];
+    while (ctl.state == PCG_RUN) {
+        VT *pold = pb[parity], *pnew = pb[parity ^ 1];
+        // ---- phase A: p = z + beta p over the window, row sums, transposes ---
+        {
+            if (timer) t0 = globaltimer();
+            const CT bt = (CT)ctl.bt;
+            {
+                const int nf = 3 * nwin, ncf = 12 * ncached, ntot = nf + ncf;
+                const VT *zw = z + 3 * wlo;
+                for (int f0 = threadIdx.x; f0 < ntot; f0 += 8 * blockDim.x) {
+                    VT zz[8], pp[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int f = f0 + k * blockDim.x;
+                        zz[k] = VT(0);
+                        pp[k] = VT(0);
+                        if (f < nf) {
+                            zz[k] = __ldcg(zw + f);
+                        } else if (f < ntot) {
+                            const int g = f - nf, kk = g / 12, q = (g % 12) / 3, j = g % 3;
+                            if (s_cm[kk] >> q & 1) {
+                                const int v = (&s_cv[kk].x)[q];
+                                zz[k] = __ldcg(z + 3 * v + j);
+                                pp[k] = __ldcg(pold + 3 * v + j);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int f = f0 + k * blockDim.x;
+                        if (f < nf) {
+                            CT *d = s_p4 + 4 * (f / 3) + f % 3;
+                            *d = dir_update(zz[k], bt, *d);
+                        } else if (f < ntot) {
+                            s_cp[f - nf] = dir_update(zz[k], bt, pp[k]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (timer) tS += globaltimer() - t0;
+            AccF acc[1] = {};
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m) {
+                qreg[m][0] = qreg[m][1] = qreg[m][2] = 0.f;
+                const int t = threadIdx.x + m * blockDim.x;
+                if (t < nr) {
+                    const int info = s_rinfo[t];
+                    const int row = info >> 8, len = info & 255;
+                    CT pi[3];
+                    load3v(s_p4 + 4 * row, pi);
+                    CT yd[3], yo[3] = {0.f, 0.f, 0.f};
+                    {
+                        const float *v = uv + U0 + s_lvl[0] + t;  // level 0: the diagonal block
+                        CT a[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) a[i] = __ldcs(v + (size_t)i * nup);
+                        yd[0] = a[0] * pi[0] + a[1] * pi[1] + a[2] * pi[2];
+                        yd[1] = a[3] * pi[0] + a[4] * pi[1] + a[5] * pi[2];
+                        yd[2] = a[6] * pi[0] + a[7] * pi[1] + a[8] * pi[2];
+                    }
+#pragma unroll 2
+                    for (int j = 1; j < len; ++j) {
+                        const size_t slot = U0 + s_lvl[j] + t;
+                        const float *v = uv + slot;
+                        CT a[9], pj[3];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) a[i] = __ldcs(v + (size_t)i * nup);
+                        const int vr = __ldcs(A.unbr + slot);
+                        load3v(s_p4 + 4 * vr, pj);
+                        yo[0] += a[0] * pj[0] + a[1] * pj[1] + a[2] * pj[2];
+                        yo[1] += a[3] * pj[0] + a[4] * pj[1] + a[5] * pj[2];
+                        yo[2] += a[6] * pj[0] + a[7] * pj[1] + a[8] * pj[2];
+                        red_add4(yq + wlo + vr, a[0] * pi[0] + a[3] * pi[1] + a[6] * pi[2],
+                                 a[1] * pi[0] + a[4] * pi[1] + a[7] * pi[2], a[2] * pi[0] + a[5] * pi[1] + a[8] * pi[2]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) qreg[m][k] = yd[k] + yo[k];
+                    acc[0].add((pi[0] * yd[0] + pi[1] * yd[1]) + pi[2] * yd[2]);
+                    acc[0].add(2.f * ((pi[0] * yo[0] + pi[1] * yo[1]) + pi[2] * yo[2]));
+                }
+            }
+            if (timer) tR += globaltimer() - t0;
+            // this CTA's contact pairs: yq += mu gamma g (g . p)
+            CT cdot = CT(0);
+            for (int k = threadIdx.x; k < nco; k += blockDim.x) {
+                CT g[12], u[12], w;
+                int vid[4], m;
+                if (k < ncached) {
+                    const int4 v = s_cv[k];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = s_cm[k];
+                    w = s_cw[k];
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        g[j] = s_cg[12 * k + j];
+                        u[j] = s_cp[12 * k + j];
+                    }
+                } else {
+                    const int i = c + k * (int)gridDim.x;
+                    const int4 v = A.cv[i];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = A.cmask[i];
+                    w = (CT)A.cw[i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
+                            u[3 * q + j] = (m >> q & 1) ? dir_update(__ldcg(z + 3 * vid[q] + j), bt,
+                                                                     __ldcg(pold + 3 * vid[q] + j))
+                                                        : CT(0);
+                        }
+                }
+                CT s = CT(0);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) s += g[j] * u[j];
+                const CT t = w * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (m >> q & 1) red_add4(yq + vid[q], t * g[3 * q], t * g[3 * q + 1], t * g[3 * q + 2]);
+                cdot += t * s;
+            }
+            if (timer) tC += globaltimer() - t0;
+            acc[0].add(cdot);
+            if (A.nc > 0)
+                for (int i = threadIdx.x; i < nr; i += blockDim.x) {  // read by other CTAs' pairs
+                    CT p[3];
+                    load3v(s_p4 + 4 * i, p);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) pnew[3 * (r0 + i) + k] = p[k];
+                }
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tA += t1 - t0;
+                t0 = t1;
+            }
+            reduce(acc, [&](const double *t) {
+                const double pq = t[0];
+                if (!isfinite(pq)) ctl.state = PCG_BAD;
+                else if (!(pq > 0.0)) ctl.state = PCG_DONE;
+                else {
+                    ctl.alpha = ctl.rz / pq;
+                    ctl.al = (float)ctl.alpha;
+                }
+            });
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tA2 += t1 - t0;
+                t0 = t1;
+            }
+        }
+        if (ctl.state != PCG_RUN) break;
+        // ---- phase B: x, r, z updates (the same rows per thread as phase A) --
+        {
+            const RT al = ctl.al;
+            AccF acc[2] = {};
+#pragma unroll
+            for (int m = 0; m < MAXR; ++m) {
+                const int t = threadIdx.x + m * blockDim.x;
+                if (t < nr) {
+                    const int row = s_rinfo[t] >> 8, a = r0 + row;
+                    const float4 yg = __ldcg(yq + a);
+                    yq[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    CT pc[3];
+                    load3v(s_p4 + 4 * row, pc);
+                    const float qk[3] = {qreg[m][0] + yg.x, qreg[m][1] + yg.y, qreg[m][2] + yg.z};
+                    RT rv[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        s_xl[k * ld + row] += al * pc[k];
+                        rv[k] = s_r[k * ld + row] - al * qk[k];
+                        s_r[k * ld + row] = rv[k];
+                    }
+                    acc[0].add(precond(row, rv));
+                    acc[1].add((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
+                }
+            }
+            if (timer) {
+                const unsigned long long t1 = globaltimer();
+                tB += t1 - t0;
+                t0 = t1;
+            }
+            reduce(acc, [&](const double *t) {
+                ++ctl.it;
+                ctl.rz_old = ctl.rz;
+                ctl.beta = t[0] / ctl.rz_old;
+                ctl.bt = (float)ctl.beta;
+                ctl.rz = t[0];
+                ctl.rr = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1])) {
+                    ctl.state = PCG_BAD;
+                    return;
+                }
+                const bool done = ctl.rr <= A.tol2 * ctl.bb;
+                if (ctl.folds < A.max_replace && (done || ctl.rr <= 0.01 * ctl.rr_ref)) ctl.state = PCG_FOLD;
+                else if (done) ctl.state = PCG_DONE;
+                else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
+            });
+            if (timer) tB2 += globaltimer() - t0;
+        }
+        parity ^= 1;
+        if (ctl.state == PCG_FOLD) {
+            // reliable update: x += x_l in FP64, then r = b - H x with FP64
+            // vectors (FP32 matrix, the transposed products by FP64 atomics
+            // into qd); the direction p is kept and beta rescaled
+            for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double xv = g_x[k * ld + i] + (double)s_xl[k * ld + i];
+                    g_x[k * ld + i] = xv;
+                    s_xl[k * ld + i] = RT(0);
+                    A.x[3 * (r0 + i) + k] = xv;
+                }
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // x visible to every CTA
+            }
+            if (ctl.state == PCG_ABORT) break;
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                const int info = s_rinfo[t];
+                const int row = info >> 8, len = info & 255;
+                double xi[3], h[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) xi[k] = __ldcg(A.x + 3 * (r0 + row) + k);
+                for (int j = 0; j < len; ++j) {
+                    const size_t slot = U0 + s_lvl[j] + t;
+                    double a[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) a[i] = (double)__ldcs(uv + slot + (size_t)i * nup);
+                    const int vr = j == 0 ? row : (int)__ldcs(A.unbr + slot);
+                    double xj[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) xj[k] = __ldcg(A.x + 3 * (wlo + vr) + k);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) h[k] += a[3 * k] * xj[0] + a[3 * k + 1] * xj[1] + a[3 * k + 2] * xj[2];
+                    if (j > 0)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            atomicAdd(A.qd + 3 * (wlo + vr) + k, a[k] * xi[0] + a[3 + k] * xi[1] + a[6 + k] * xi[2]);
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) g_hx[k * ld + row] = h[k];
+            }
+            for (int k = threadIdx.x; k < nco; k += blockDim.x) {
+                const int i = c + k * (int)gridDim.x;
+                const int4 v = A.cv[i];
+                const int mk = A.cmask[i];
+                const int vid[4] = {v.x, v.y, v.z, v.w};
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) s += A.cg[12 * (size_t)i + 3 * q + j] * __ldcg(A.x + 3 * vid[q] + j);
+                const double t = A.cw[i] * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) atomicAdd(A.qd + 3 * vid[q] + j, t * A.cg[12 * (size_t)i + 3 * q + j]);
+            }
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // transposed and contact parts complete
+            }
+            if (ctl.state == PCG_ABORT) break;
+            AccF acc[2];
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                const int a = r0 + i;
+                RT rv[3];
+                double rr = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double rh = A.b[3 * a + k] - g_hx[k * ld + i] - __ldcg(A.qd + 3 * a + k);
+                    A.qd[3 * a + k] = 0.0;
+                    rr += rh * rh;
+                    rv[k] = (RT)rh;
+                    s_r[k * ld + i] = rv[k];
+                }
+                acc[0].add(precond(i, rv));
+                acc[1].add(rr);
+            }
+            reduce(acc, [&](const double *t) {
+                ++ctl.folds;
+                ctl.beta = t[0] / ctl.rz_old;
+                ctl.bt = (float)ctl.beta;
+                ctl.rz = t[0];
+                ctl.rr = t[1];
+                ctl.rr_ref = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
+                else if (ctl.rr <= A.tol2 * ctl.bb) ctl.state = PCG_DONE;
+                else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
+                else ctl.state = PCG_RUN;
+            });
+        }
+    }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A.x[3 * (r0 + i) + k] = g_x[k * ld + i] + (double)s_xl[k * ld + i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.dflag[F_ITERS] = ctl.it;
+        A.dflag[F_MAXIT] = ctl.state == PCG_MAXIT;
+        A.dflag[F_DONE] = 1;
+        if (ctl.state == PCG_BAD) A.dflag[F_ERR] |= ERR_NONFINITE;
+        A.dscal[S_RR] = ctl.rr;
+        A.dscal[S_BB] = ctl.bb;
+        A.dscal[S_RZ] = ctl.rz;
+        A.dscal[S_T_SPMV] = 1e-6 * (double)tA;
+        A.dscal[S_T_RED1] = 1e-6 * (double)tA2;
+        A.dscal[S_T_UPD] = 1e-6 * (double)tB;
+        A.dscal[S_T_RED2] = 1e-6 * (double)tB2;
+        A.dscal[S_T_STAGE] = 1e-6 * (double)tS;
+        A.dscal[S_T_ROWS] = 1e-6 * (double)tR;
+        A.dscal[S_T_CONTACT] = 1e-6 * (double)tC;
+    }
+}
+
 // Row ranges of the CTAs (about equal block counts), each CTA's vertex
 // window (its rows and all their neighbours), and the jagged shared-memory
 // layout of each CTA's blocks: rows in order of decreasing length (ties by
@@ -903,6 +1399,144 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
     return check_cuda(cudaStreamSynchronize(S.stream));
 }
 
+// Partition of the symmetric variant: row ranges with about equal upper
+// block counts; each CTA's window runs from its first row to its last upper
+// neighbour; the CTA's upper blocks in jagged order (rows by decreasing
+// upper length, ties by row; level 0 is every row's diagonal block, which
+// comes first in its upper row), stored from the CTA's first upper-row
+// position on, so the jagged slots of all CTAs tile [0, nnzb).
+static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int *max_win, int *max_len)
+{
+    const std::vector<int> &rp = S.h_rowptr;
+    const std::vector<int> &col = S.h_col;
+    std::vector<int> part(grid + 1, S.nv);
+    part[0] = 0;
+    const double per = (double)S.nnzb / grid;
+    int r = 0;
+    for (int c = 1; c < grid; ++c) {
+        const double target = per * c;
+        while (r < S.nv && rp[r] < target) ++r;
+        part[c] = std::max(part[c - 1], r);
+    }
+    part[grid] = S.nv;
+    std::vector<int> win(2 * grid), rinfo(S.nv), lvl, lvlptr(grid + 1, 0), uedst(S.nnzb);
+    std::vector<unsigned short> unbr(S.nnzb);
+    int mr = 0, mw = 0, ml = 0;
+    std::vector<int> order;
+    for (int c = 0; c < grid; ++c) {
+        const int a = part[c], b = part[c + 1];
+        if (b - a > kSymMaxRowsPerThread * block) return BF_E_CAPACITY;
+        int hi = b;
+        for (int v = a; v < b; ++v) {
+            if (rp[v + 1] == rp[v] || col[rp[v]] != v) return BF_E_CAPACITY;  // diagonal block first
+            hi = std::max(hi, col[rp[v + 1] - 1] + 1);
+        }
+        if (hi - a > 65535) return BF_E_CAPACITY;
+        win[2 * c] = a;
+        win[2 * c + 1] = hi;
+        order.resize(b - a);
+        for (int v = a; v < b; ++v) order[v - a] = v;
+        auto len = [&](int v) { return rp[v + 1] - rp[v]; };
+        std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return len(u) > len(v); });
+        const int lmax = b > a ? len(order[0]) : 0;
+        if (lmax > 255) return BF_E_CAPACITY;
+        std::vector<int> at(lmax + 1, 0);
+        for (int j = 0; j < lmax; ++j) {
+            int n = 0;
+            while (n < b - a && len(order[n]) > j) ++n;
+            at[j + 1] = at[j] + n;
+        }
+        for (int t = 0; t < b - a; ++t) {
+            const int v = order[t];
+            rinfo[a + t] = (v - a) << 8 | len(v);
+            for (int j = 0; j < len(v); ++j) {
+                const int k = rp[v] + j, d = rp[a] + at[j] + t;
+                uedst[k] = d;
+                unbr[d] = (unsigned short)(col[k] - a);
+            }
+        }
+        lvl.insert(lvl.end(), at.begin(), at.end());
+        lvlptr[c + 1] = (int)lvl.size();
+        mr = std::max(mr, b - a);
+        mw = std::max(mw, hi - a);
+        ml = std::max(ml, lmax);
+    }
+    auto put = [&](auto *&dst, const auto &host) -> int {
+        using T = std::remove_reference_t<decltype(*dst)>;
+        if (dst) dev_free(S, dst);
+        dst = (T *)dev_alloc(S, std::max<size_t>(host.size(), 1) * sizeof(T));
+        if (!dst) return BF_E_OOM;
+        if (!host.empty())
+            cudaMemcpyAsync(dst, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, S.stream);
+        return BF_OK;
+    };
+    int st = put(S.part, part);
+    if (!st) st = put(S.win, win);
+    if (!st) st = put(S.pcg_rinfo, rinfo);
+    if (!st) st = put(S.pcg_lvl, lvl);
+    if (!st) st = put(S.pcg_lvlptr, lvlptr);
+    if (!st) st = put(S.pcg_uedst, uedst);
+    if (!st) st = put(S.pcg_unbr, unbr);
+    if (st) return st;
+    *max_rows = mr;
+    *max_win = mw;
+    *max_len = ml;
+    return check_cuda(cudaStreamSynchronize(S.stream));
+}
+
+// symmetric variant: the upper blocks in jagged order, 9 planes
+__global__ void k_jagged_gather_upper(int nnzb, const int *__restrict__ uedst, const float *__restrict__ val,
+                                      float *__restrict__ uval)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnzb) return;
+    const size_t d = (size_t)uedst[k];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) uval[(size_t)i * nnzb + d] = val[9 * (size_t)k + i];
+}
+
+// Sets up the symmetric variant at `cps` CTAs per SM, if it fits.
+static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
+{
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_pcg_sym) != cudaSuccess) return BF_E_CUDA;
+    const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nnzb, kPcgEntriesPerCta / 2)));
+    if (grid > kPcgMaxGrid) return BF_E_CAPACITY;
+    const int block = (kPcgThreads / cps) & ~31;
+    int mr = 0, mw = 0, ml = 0;
+    int st = make_partition_sym(S, grid, block, &mr, &mw, &ml);
+    if (st) return st;
+    const size_t avail = smem_optin - fa.sharedSizeBytes;
+    const PcgSymLayout L0 = pcg_sym_layout(mr, mw, ml, 0);
+    if (L0.total > avail) return BF_E_CAPACITY;
+    int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(4));
+    while (kc > 0 && pcg_sym_layout(mr, mw, ml, kc).total > avail) --kc;
+    const PcgSymLayout L = pcg_sym_layout(mr, mw, ml, kc);
+    cudaFuncSetAttribute(k_pcg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_sym, block, L.total);
+    if (occ < cps) return BF_E_CAPACITY;
+    const size_t stride = pcg_sym_vec_bytes(mr);
+    if (S.pcg_gvec) dev_free(S, S.pcg_gvec);
+    if (S.pcg_uval) dev_free(S, S.pcg_uval);
+    if (S.pcg_yq) dev_free(S, S.pcg_yq);
+    S.pcg_gvec = (unsigned char *)dev_alloc(S, stride * grid);
+    S.pcg_uval = (float *)dev_alloc(S, 9 * (size_t)S.nnzb * sizeof(float));
+    S.pcg_yq = (float4 *)dev_alloc(S, (size_t)S.nv * sizeof(float4));
+    if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq) return BF_E_OOM;
+    S.pcg_gvec_stride = stride;
+    S.pcg_grid = grid;
+    S.pcg_block = block;
+    S.pcg_smem = (int)L.total;
+    S.pcg_resident = PCG_SYM;
+    S.pcg_max_rows = mr;
+    S.pcg_max_ent = S.nnzb;
+    S.pcg_max_win = mw;
+    S.pcg_max_len = ml;
+    S.pcg_kc = kc;
+    return BF_OK;
+}
+
 
 // Chooses the launch: the resident variant when the blocks fit in shared
 // memory at the requested CTAs per SM (falling back to fewer CTAs per SM),
@@ -920,10 +1554,21 @@ static int setup_persistent(Scene &S)
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return BF_E_CUDA;
     const int per_sm = std::min(4, std::max(1, S.pcg_ctas_per_sm));
-    const int modes[3] = {PCG_RESIDENT, PCG_STREAM, PCG_GLOBAL};
+    const int modes[4] = {PCG_RESIDENT, PCG_STREAM, PCG_SYM, PCG_GLOBAL};
     for (int mode : modes) {
         if (mode == PCG_RESIDENT && !S.pcg_allow_resident) continue;
-        if (mode != PCG_GLOBAL && S.pcg_force_global) continue;
+        if ((mode == PCG_RESIDENT || mode == PCG_STREAM) && S.pcg_force_global) continue;
+        if (mode == PCG_SYM) {  // mixed precision only (FP32 blocks and vector reductions)
+            if constexpr (mixed && std::is_same<MT, float>::value) {
+                if (S.pcg_no_sym) continue;
+                for (int cps = per_sm; cps >= 1; --cps) {
+                    const int st = setup_sym(S, nsm, cps, (size_t)smem_optin);
+                    if (st == BF_OK) return BF_OK;
+                    if (st != BF_E_CAPACITY) return st;
+                }
+            }
+            continue;
+        }
         const void *kern = mode == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
                            : mode == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
                                                 : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
@@ -1094,6 +1739,20 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
                                                                               (MT *)S.pcg_jval);
         ++S.n_launch;
     }
+    A.uval = S.pcg_uval;
+    A.unbr = S.pcg_unbr;
+    A.urowptr = S.rowptr;
+    A.nup = (size_t)S.nnzb;
+    A.yq = S.pcg_yq;
+    if (S.pcg_resident == PCG_SYM) {
+        if constexpr (std::is_same<MT, float>::value) {
+            k_jagged_gather_upper<<<cdiv(S.nnzb, kThreads), kThreads, 0, S.stream>>>(S.nnzb, S.pcg_uedst, val,
+                                                                                   S.pcg_uval);
+            ++S.n_launch;
+        } else {
+            return BF_E_ARG;
+        }
+    }
     A.kc = S.pcg_kc;
     A.dscal = S.dscal;
     A.dflag = S.dflag;
@@ -1113,6 +1772,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         ScopedTimer tm(S, T_PCG_PERSISTENT);
         const void *kern = S.pcg_resident == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
                            : S.pcg_resident == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
+                           : S.pcg_resident == PCG_SYM    ? (const void *)k_pcg_sym
                                                           : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
         e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(S.pcg_block), args, (size_t)S.pcg_smem, S.stream);
         ++S.n_launch;

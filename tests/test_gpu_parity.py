@@ -405,10 +405,11 @@ def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, pr
 def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
     """On a system split over several CTAs (a 20k-tet scene after a few
     steps, with contacts), the resident, streamed and global-vector
-    persistent variants at one and two CTAs per SM and the per-phase
-    launches reach the tolerance on the library's own operator and agree
-    with each other; the autotuner then times them and sets one whose solve
-    meets the tolerance."""
+    persistent variants (in mixed precision both the symmetric one and the
+    one streaming both triangles) at one and two CTAs per SM and the
+    per-phase launches reach the tolerance on the library's own operator and
+    agree with each other; the autotuner then times them and sets one whose
+    solve meets the tolerance."""
     torch = torch_cuda
     from paper_2512_12151_b300 import serving
     s = scenes.batch_scene(11, 1.8e4, 2e4, precision=precision)
@@ -425,7 +426,7 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
         B.bf_assemble(h, xt, xd, xd, G)
         b = -G
         sols, its, grids = [], [], []
-        modes = (1, 2, 17, 18, 33, 34, 0)
+        modes = (1, 2, 17, 18, 33, 34, 97, 98, 0)
         for mode in modes:
             B.bf_set_pcg_mode(h, mode)
             p = torch.zeros_like(xd)
@@ -437,7 +438,9 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
             sols.append(host(p).reshape(-1))
             its.append(it)
             grids.append(B.bf_get_pcg_config(h))
-        assert grids[0]["ctas"] > 1 and grids[4]["resident"] == 2  # several CTAs; global variant used
+        # several CTAs; the symmetric variant (mixed) or the full-row one (FP64) under 33, the full-row one under 97
+        assert grids[0]["ctas"] > 1 and grids[4]["resident"] == (3 if precision else 2)
+        assert grids[6]["resident"] == 2
         last = len(modes) - 1
         for k in range(last):
             assert abs(its[k] - its[last]) <= max(2, its[last] // 20), its
