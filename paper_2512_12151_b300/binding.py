@@ -366,8 +366,20 @@ def bf_max_step_size(h, x0, x1):
     return a.value
 
 
+def _check_pairs(n, x0, x1, out):
+    """the kernels read 12 n doubles of x0 and x1 and write out: refuse
+    tensors that are too small or of another type before the launch"""
+    import torch
+    assert out is not None and out.dtype == torch.float64 and out.is_cuda, "output must be a float64 CUDA tensor"
+    if n > 0:
+        for t in (x0, x1):
+            assert t is not None and t.dtype == torch.float64 and t.is_cuda, "x0, x1 must be float64 CUDA tensors"
+            assert t.is_contiguous() and t.numel() >= 12 * n, "x0, x1 need 12 contiguous doubles per pair"
+
+
 def bf_accd(ptype, x0, x1, s, toi, stream=None):
     n = toi.numel()
+    _check_pairs(n, x0, x1, toi)
     _check("bf_accd", lib().bf_accd(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(toi), stream))
 
 
@@ -398,6 +410,8 @@ def bf_inversion_step(h, x0, x1):
 def bf_max_step_size_pairs_noalloc(ptype, n, x0, x1, s, alpha, stream=None):
     """alpha[0] = min(1, min TOI) over the first n pairs of x0 -> x1, with no
     device allocation (see include/bf.h for the limits)."""
+    _check_pairs(n, x0, x1, alpha)
+    assert alpha.numel() >= 1
     _check("bf_max_step_size_pairs_noalloc",
            lib().bf_max_step_size_pairs_noalloc(ptype, n, _dptr(x0), _dptr(x1), s, _dptr(alpha), stream))
 

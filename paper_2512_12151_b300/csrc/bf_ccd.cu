@@ -764,7 +764,16 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_min_toi_noalloc(int type, i
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double t = 1.0;
     double toi;
-    if (i < n && accd(type, x0 + 12 * (size_t)i, x1 + 12 * (size_t)i, s, 1.0, max_iter, &toi)) t = fmin(t, toi);
+    if (i < n) {
+        // a pair with a non-finite coordinate allows no step (t = 0): its
+        // TOI cannot be trusted, and fmin would drop a NaN
+        bool finite = true;
+        for (int k = 0; k < 12; ++k)
+            finite = finite && isfinite(x0[12 * (size_t)i + k]) && isfinite(x1[12 * (size_t)i + k]);
+        if (!finite) t = 0.0;
+        else if (accd(type, x0 + 12 * (size_t)i, x1 + 12 * (size_t)i, s, 1.0, max_iter, &toi))
+            t = toi == toi ? fmin(t, toi) : 0.0;
+    }
     unsigned long long b = (unsigned long long)__double_as_longlong(t);
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);

@@ -55,17 +55,26 @@ def test_noalloc_matches_accd_two_calls(torch_cuda):
     x0[:, 0:3] = torch.tensor([0.2, 0.2, 1.0], dtype=torch.float64)
     B.bf_max_step_size_pairs_noalloc(0, 64, x0, x0.clone(), 0.1, alpha)
     assert float(alpha[0]) == 1.0
+    # a non-finite coordinate allows no step, wherever the pair sits
+    x1 = x0.clone()
+    x1[37, 4] = float("nan")
+    for _ in range(2):
+        alpha.fill_(-1.0)
+        B.bf_max_step_size_pairs_noalloc(0, 64, x0, x1, 0.1, alpha)
+        assert float(alpha[0]) == 0.0
+    B.bf_max_step_size_pairs_noalloc(0, 64, x0, x0.clone(), 0.1, alpha)
+    assert float(alpha[0]) == 1.0
 
 
 def test_noalloc_limits(torch_cuda):
     torch = torch_cuda
     n_max = 1 << 20
-    x0, x1 = _pairs(11, n_max, 0.12)
+    x0, x1 = _pairs(11, n_max + 1, 0.12)  # one pair more than a call may take
     x0 = torch.tensor(x0, device="cuda")
     x1 = torch.tensor(x1, device="cuda")
     alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
     B.bf_max_step_size_pairs_noalloc(1, n_max, x0, x1, 0.1, alpha)
-    assert float(alpha[0]) == _expected(torch, 1, x0, x1, 0.1)
+    assert float(alpha[0]) == _expected(torch, 1, x0[:n_max], x1[:n_max], 0.1)
     with pytest.raises(B.BfError):
         B.bf_max_step_size_pairs_noalloc(1, n_max + 1, x0, x1, 0.1, alpha)
     with pytest.raises(B.BfError):
