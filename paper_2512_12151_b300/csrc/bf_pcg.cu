@@ -839,13 +839,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 // (jagged levels as in the full-row variants; level 0 is the diagonal
 // block), the window of p over [part[c], last upper neighbour] in shared
 // memory (16-bit offsets), r and the FP32 increment of x per row in shared
-// memory, the rows' part of q in registers (thread t owns the rows t,
-// t + blockDim.x, ... of the length order in both phases, at most
-// kSymMaxRowsPerThread), FP64 x and H x of the reliable updates in a
-// per-CTA global vector.
+// memory, the rows' part of q, FP64 x and H x of the reliable updates in a
+// per-CTA global vector (L2-resident).
 // ---------------------------------------------------------------------------
-constexpr int kSymMaxRowsPerThread = 8;
-
 struct PcgSymLayout {
     size_t p4, r, xl, rinfo, lvl, cg, cp, cw, cv, cm, total;
 };
@@ -873,8 +869,11 @@ __host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win
     return L;
 }
 
-// per-CTA global vector of the symmetric variant: FP64 x and H x (3 per row each)
-inline size_t pcg_sym_vec_bytes(int max_rows) { return ((48 * (size_t)max_rows) + 255) & ~(size_t)255; }
+// per-CTA global vector of the symmetric variant: FP64 x and H x, FP32 row
+// sums q (3 per row each)
+inline size_t pcg_sym_vec_bytes(int max_rows) { return ((60 * (size_t)max_rows) + 255) & ~(size_t)255; }
+
+constexpr int kSymRowBatch = 2;  // rows per thread whose update-phase loads are issued together
 
 __device__ __forceinline__ void red_add4(float4 *dst, float a, float b, float c)
 {
@@ -886,7 +885,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     using CT = float;
     using VT = float;
     using RT = float;
-    constexpr int MAXR = kSymMaxRowsPerThread;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PcgCtl ctl;
     __shared__ float2 red_f[2 * kPcgMaxWarps];
@@ -906,6 +904,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     const int ld = A.max_rows;  // per-row arrays are component-major: a[k * ld + row]
     double *g_x = (double *)(A.gvec + (size_t)c * A.gvec_stride);
     double *g_hx = g_x + 3 * (size_t)ld;
+    float *g_q = (float *)(g_hx + 3 * (size_t)ld);
     CT *s_p4 = (CT *)(smem + L.p4);
     RT *s_r = (RT *)(smem + L.r);
     RT *s_xl = (RT *)(smem + L.xl);
@@ -951,8 +950,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         ++nred;
         __syncthreads();
     };
-    unsigned long long tA = 0, tA2 = 0, tB = 0, tB2 = 0, t0 = 0, tS = 0, tR = 0, tC = 0;
+    // per-phase device time seen by thread 0 of CTA 0 (kept in shared
+    // memory: 64-bit counters in registers would cost the hot loops 16)
+    __shared__ unsigned long long tm[8];  // A, A2, B, B2, t0, S, R, C
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) tm[i] = 0;
     __syncthreads();
     // ---- init: r = b, x = 0, z = P r, p_old = 0, yq = 0 on the own rows ----
     {
@@ -990,12 +993,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         });
     }
     int parity = 0;
-    float qreg[MAXR][3];
     while (ctl.state == PCG_RUN) {
         VT *pold = pb[parity], *pnew = pb[parity ^ 1];
         // ---- phase A: p = z + beta p over the window, row sums, transposes ---
         {
-            if (timer) t0 = globaltimer();
+            if (timer) tm[4] = globaltimer();
             const CT bt = (CT)ctl.bt;
             {
                 const int nf = 3 * nwin, ncf = 12 * ncached, ntot = nf + ncf;
@@ -1031,49 +1033,55 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 }
             }
             __syncthreads();
-            if (timer) tS += globaltimer() - t0;
+            if (timer) tm[5] += globaltimer() - tm[4];
+            // Row sums in batches of four levels: the loads of a batch are
+            // issued together, before its products and vector reductions (a
+            // reduction keeps the loads that follow it behind it).
             AccF acc[1] = {};
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                const int info = s_rinfo[t];
+                const int row = info >> 8, len = info & 255;
+                CT pi[3];
+                load3v(s_p4 + 4 * row, pi);
+                CT yd[3] = {0.f, 0.f, 0.f}, yo[3] = {0.f, 0.f, 0.f};
+                for (int j0 = 0; j0 < len; j0 += 4) {
+                    CT a[4][9];
+                    int vr[4];
 #pragma unroll
-            for (int m = 0; m < MAXR; ++m) {
-                qreg[m][0] = qreg[m][1] = qreg[m][2] = 0.f;
-                const int t = threadIdx.x + m * blockDim.x;
-                if (t < nr) {
-                    const int info = s_rinfo[t];
-                    const int row = info >> 8, len = info & 255;
-                    CT pi[3];
-                    load3v(s_p4 + 4 * row, pi);
-                    CT yd[3], yo[3] = {0.f, 0.f, 0.f};
-                    {
-                        const float *v = uv + U0 + s_lvl[0] + t;  // level 0: the diagonal block
-                        CT a[9];
+                    for (int u = 0; u < 4; ++u) {
+                        vr[u] = -1;
+                        if (j0 + u < len) {
+                            const size_t slot = U0 + s_lvl[j0 + u] + t;
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) a[i] = __ldcs(v + (size_t)i * nup);
-                        yd[0] = a[0] * pi[0] + a[1] * pi[1] + a[2] * pi[2];
-                        yd[1] = a[3] * pi[0] + a[4] * pi[1] + a[5] * pi[2];
-                        yd[2] = a[6] * pi[0] + a[7] * pi[1] + a[8] * pi[2];
-                    }
-#pragma unroll 2
-                    for (int j = 1; j < len; ++j) {
-                        const size_t slot = U0 + s_lvl[j] + t;
-                        const float *v = uv + slot;
-                        CT a[9], pj[3];
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) a[i] = __ldcs(v + (size_t)i * nup);
-                        const int vr = __ldcs(A.unbr + slot);
-                        load3v(s_p4 + 4 * vr, pj);
-                        yo[0] += a[0] * pj[0] + a[1] * pj[1] + a[2] * pj[2];
-                        yo[1] += a[3] * pj[0] + a[4] * pj[1] + a[5] * pj[2];
-                        yo[2] += a[6] * pj[0] + a[7] * pj[1] + a[8] * pj[2];
-                        red_add4(yq + wlo + vr, a[0] * pi[0] + a[3] * pi[1] + a[6] * pi[2],
-                                 a[1] * pi[0] + a[4] * pi[1] + a[7] * pi[2], a[2] * pi[0] + a[5] * pi[1] + a[8] * pi[2]);
+                            for (int i = 0; i < 9; ++i) a[u][i] = __ldcs(uv + slot + (size_t)i * nup);
+                            vr[u] = __ldcs(A.unbr + slot);  // level 0: the row itself (diagonal block)
+                        }
                     }
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) qreg[m][k] = yd[k] + yo[k];
-                    acc[0].add((pi[0] * yd[0] + pi[1] * yd[1]) + pi[2] * yd[2]);
-                    acc[0].add(2.f * ((pi[0] * yo[0] + pi[1] * yo[1]) + pi[2] * yo[2]));
+                    for (int u = 0; u < 4; ++u) {
+                        if (vr[u] >= 0) {
+                            CT pj[3];
+                            load3v(s_p4 + 4 * vr[u], pj);
+                            const CT s0 = a[u][0] * pj[0] + a[u][1] * pj[1] + a[u][2] * pj[2];
+                            const CT s1 = a[u][3] * pj[0] + a[u][4] * pj[1] + a[u][5] * pj[2];
+                            const CT s2 = a[u][6] * pj[0] + a[u][7] * pj[1] + a[u][8] * pj[2];
+                            if (j0 + u == 0) {
+                                yd[0] = s0; yd[1] = s1; yd[2] = s2;
+                            } else {
+                                yo[0] += s0; yo[1] += s1; yo[2] += s2;
+                                red_add4(yq + wlo + vr[u], a[u][0] * pi[0] + a[u][3] * pi[1] + a[u][6] * pi[2],
+                                         a[u][1] * pi[0] + a[u][4] * pi[1] + a[u][7] * pi[2],
+                                         a[u][2] * pi[0] + a[u][5] * pi[1] + a[u][8] * pi[2]);
+                            }
+                        }
+                    }
                 }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) g_q[k * ld + row] = yd[k] + yo[k];
+                acc[0].add((pi[0] * yd[0] + pi[1] * yd[1]) + pi[2] * yd[2]);
+                acc[0].add(2.f * ((pi[0] * yo[0] + pi[1] * yo[1]) + pi[2] * yo[2]));
             }
-            if (timer) tR += globaltimer() - t0;
+            if (timer) tm[6] += globaltimer() - tm[4];
             // this CTA's contact pairs: yq += mu gamma g (g . p)
             CT cdot = CT(0);
             for (int k = threadIdx.x; k < nco; k += blockDim.x) {
@@ -1114,7 +1122,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                     if (m >> q & 1) red_add4(yq + vid[q], t * g[3 * q], t * g[3 * q + 1], t * g[3 * q + 2]);
                 cdot += t * s;
             }
-            if (timer) tC += globaltimer() - t0;
+            if (timer) tm[7] += globaltimer() - tm[4];
             acc[0].add(cdot);
             if (A.nc > 0)
                 for (int i = threadIdx.x; i < nr; i += blockDim.x) {  // read by other CTAs' pairs
@@ -1125,8 +1133,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 }
             if (timer) {
                 const unsigned long long t1 = globaltimer();
-                tA += t1 - t0;
-                t0 = t1;
+                tm[0] += t1 - tm[4];
+                tm[4] = t1;
             }
             reduce(acc, [&](const double *t) {
                 const double pq = t[0];
@@ -1139,40 +1147,62 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             });
             if (timer) {
                 const unsigned long long t1 = globaltimer();
-                tA2 += t1 - t0;
-                t0 = t1;
+                tm[1] += t1 - tm[4];
+                tm[4] = t1;
             }
         }
         if (ctl.state != PCG_RUN) break;
-        // ---- phase B: x, r, z updates (the same rows per thread as phase A) --
+        // ---- phase B: x, r, z updates ---------------------------------------
         {
             const RT al = ctl.al;
             AccF acc[2] = {};
+            // kSymRowBatch rows per thread at a time, their global loads issued together
+            for (int row0 = threadIdx.x; row0 < nr; row0 += kSymRowBatch * blockDim.x) {
+                float4 yg[kSymRowBatch];
+                float gq[kSymRowBatch][3], P[kSymRowBatch][9];
 #pragma unroll
-            for (int m = 0; m < MAXR; ++m) {
-                const int t = threadIdx.x + m * blockDim.x;
-                if (t < nr) {
-                    const int row = s_rinfo[t] >> 8, a = r0 + row;
-                    const float4 yg = __ldcg(yq + a);
-                    yq[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    CT pc[3];
-                    load3v(s_p4 + 4 * row, pc);
-                    const float qk[3] = {qreg[m][0] + yg.x, qreg[m][1] + yg.y, qreg[m][2] + yg.z};
-                    RT rv[3];
+                for (int u = 0; u < kSymRowBatch; ++u) {
+                    const int row = row0 + u * blockDim.x;
+                    if (row < nr) {
+                        const int a = r0 + row;
+                        yg[u] = __ldcg(yq + a);
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        s_xl[k * ld + row] += al * pc[k];
-                        rv[k] = s_r[k * ld + row] - al * qk[k];
-                        s_r[k * ld + row] = rv[k];
+                        for (int k = 0; k < 3; ++k) gq[u][k] = __ldcg(g_q + k * ld + row);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) P[u][i] = __ldg(gpinv + 9 * (size_t)a + i);
                     }
-                    acc[0].add(precond(row, rv));
-                    acc[1].add((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
+                }
+#pragma unroll
+                for (int u = 0; u < kSymRowBatch; ++u) {
+                    const int row = row0 + u * blockDim.x;
+                    if (row < nr) {
+                        const int a = r0 + row;
+                        yq[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        CT pc[3];
+                        load3v(s_p4 + 4 * row, pc);
+                        const float qk[3] = {gq[u][0] + yg[u].x, gq[u][1] + yg[u].y, gq[u][2] + yg[u].z};
+                        RT rv[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            s_xl[k * ld + row] += al * pc[k];
+                            rv[k] = s_r[k * ld + row] - al * qk[k];
+                            s_r[k * ld + row] = rv[k];
+                        }
+                        CT zc[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            zc[k] = P[u][3 * k] * rv[0] + P[u][3 * k + 1] * rv[1] + P[u][3 * k + 2] * rv[2];
+                            z[3 * a + k] = zc[k];
+                        }
+                        acc[0].add((rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2]);
+                        acc[1].add((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
+                    }
                 }
             }
             if (timer) {
                 const unsigned long long t1 = globaltimer();
-                tB += t1 - t0;
-                t0 = t1;
+                tm[2] += t1 - tm[4];
+                tm[4] = t1;
             }
             reduce(acc, [&](const double *t) {
                 ++ctl.it;
@@ -1190,7 +1220,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 else if (done) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
             });
-            if (timer) tB2 += globaltimer() - t0;
+            if (timer) tm[3] += globaltimer() - tm[4];
         }
         parity ^= 1;
         if (ctl.state == PCG_FOLD) {
@@ -1299,13 +1329,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         A.dscal[S_RR] = ctl.rr;
         A.dscal[S_BB] = ctl.bb;
         A.dscal[S_RZ] = ctl.rz;
-        A.dscal[S_T_SPMV] = 1e-6 * (double)tA;
-        A.dscal[S_T_RED1] = 1e-6 * (double)tA2;
-        A.dscal[S_T_UPD] = 1e-6 * (double)tB;
-        A.dscal[S_T_RED2] = 1e-6 * (double)tB2;
-        A.dscal[S_T_STAGE] = 1e-6 * (double)tS;
-        A.dscal[S_T_ROWS] = 1e-6 * (double)tR;
-        A.dscal[S_T_CONTACT] = 1e-6 * (double)tC;
+        A.dscal[S_T_SPMV] = 1e-6 * (double)tm[0];
+        A.dscal[S_T_RED1] = 1e-6 * (double)tm[1];
+        A.dscal[S_T_UPD] = 1e-6 * (double)tm[2];
+        A.dscal[S_T_RED2] = 1e-6 * (double)tm[3];
+        A.dscal[S_T_STAGE] = 1e-6 * (double)tm[5];
+        A.dscal[S_T_ROWS] = 1e-6 * (double)tm[6];
+        A.dscal[S_T_CONTACT] = 1e-6 * (double)tm[7];
     }
 }
 
@@ -1425,7 +1455,6 @@ static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int 
     std::vector<int> order;
     for (int c = 0; c < grid; ++c) {
         const int a = part[c], b = part[c + 1];
-        if (b - a > kSymMaxRowsPerThread * block) return BF_E_CAPACITY;
         int hi = b;
         for (int v = a; v < b; ++v) {
             if (rp[v + 1] == rp[v] || col[rp[v]] != v) return BF_E_CAPACITY;  // diagonal block first
