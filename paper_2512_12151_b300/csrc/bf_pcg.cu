@@ -859,7 +859,7 @@ __host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win
     L.r = take(12 * (size_t)max_rows);
     L.xl = take(12 * (size_t)max_rows);
     L.rinfo = take(4 * (size_t)max_rows);
-    L.lvl = take(4 * ((size_t)max_len + 1));
+    L.lvl = take(8 * (size_t)max_len);  // chunk table: max_len = entries per CTA
     L.cg = take(48 * (size_t)kc);
     L.cp = take(48 * (size_t)kc);
     L.cw = take(4 * (size_t)kc);
@@ -874,6 +874,14 @@ __host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win
 inline size_t pcg_sym_vec_bytes(int max_rows) { return ((60 * (size_t)max_rows) + 255) & ~(size_t)255; }
 
 constexpr int kSymRowBatch = 2;  // rows per thread whose update-phase loads are issued together
+constexpr int kSymPrefetchBytes = 32768;  // bytes per bulk L2 prefetch instruction
+
+// bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, a multiple of
+// 16 bytes; a hint: nothing waits for it)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void red_add4(float4 *dst, float a, float b, float c)
 {
@@ -892,12 +900,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     VT *__restrict__ z = (VT *)A.z;
     VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
     float4 *__restrict__ yq = A.yq;
-    const float *__restrict__ uv = A.uval;
-    const size_t nup = A.nup;
+    const unsigned char *__restrict__ ub = (const unsigned char *)A.uval;
     const int c = blockIdx.x;
     const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
     const int wlo = A.win[2 * c], whi = A.win[2 * c + 1], nwin = whi - wlo;  // wlo == r0
-    const size_t U0 = (size_t)A.urowptr[r0];  // the CTA's first jagged slot
+    const int ntab = A.lvlptr[c + 1] - A.lvlptr[c];  // chunk-table entries
+    const int rounds = (nr + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lm = rounds > 0 ? (ntab - 1) / rounds : 0;  // levels per round
     const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int ncached = min(nco, A.kc);
     const PcgSymLayout L = pcg_sym_layout(A.max_rows, A.max_win, A.max_len, A.kc);
@@ -909,13 +918,24 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     RT *s_r = (RT *)(smem + L.r);
     RT *s_xl = (RT *)(smem + L.xl);
     int *s_rinfo = (int *)(smem + L.rinfo);
-    int *s_lvl = (int *)(smem + L.lvl);
+    int2 *s_tab = (int2 *)(smem + L.lvl);
     CT *s_cg = (CT *)(smem + L.cg);
     CT *s_cp = (CT *)(smem + L.cp);
     CT *s_cw = (CT *)(smem + L.cw);
     int4 *s_cv = (int4 *)(smem + L.cv);
     int *s_cm = (int *)(smem + L.cm);
-    for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
+    for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = ((const int2 *)A.lvl)[A.lvlptr[c] + j];
+    // round q of the CTA's blocks: bytes [tab[q lm], tab[(q + 1) lm]); the
+    // first round goes to L2 now, each later one while the previous is used
+    auto prefetch_round = [&](int q) {
+        if (q < rounds) {
+            const int b0 = ((const int2 *)A.lvl)[A.lvlptr[c] + q * lm].x;
+            const int b1 = ((const int2 *)A.lvl)[A.lvlptr[c] + (q + 1) * lm].x;
+            for (int o = b0; o < b1; o += kSymPrefetchBytes)
+                prefetch_l2(ub + o, (unsigned)min(kSymPrefetchBytes, b1 - o));
+        }
+    };
+    if (threadIdx.x == 0) prefetch_round(0);
     for (int t = threadIdx.x; t < nr; t += blockDim.x) s_rinfo[t] = A.rinfo[r0 + t];
     for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
         const int i = c + k * (int)gridDim.x;
@@ -1038,9 +1058,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             // issued together, before its products and vector reductions (a
             // reduction keeps the loads that follow it behind it).
             AccF acc[1] = {};
-            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            for (int q = 0; q < rounds; ++q) {
+                if (threadIdx.x == 0) prefetch_round(q + 1);
+                const int u = threadIdx.x, t = q * (int)blockDim.x + u;
+                if (t >= nr) continue;
                 const int info = s_rinfo[t];
                 const int row = info >> 8, len = info & 255;
+                const int2 *tq = s_tab + q * lm;
                 CT pi[3];
                 load3v(s_p4 + 4 * row, pi);
                 CT yd[3] = {0.f, 0.f, 0.f}, yo[3] = {0.f, 0.f, 0.f};
@@ -1048,30 +1072,32 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                     CT a[4][9];
                     int vr[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        vr[u] = -1;
-                        if (j0 + u < len) {
-                            const size_t slot = U0 + s_lvl[j0 + u] + t;
+                    for (int w = 0; w < 4; ++w) {
+                        vr[w] = -1;
+                        if (j0 + w < len) {
+                            const int2 e = tq[j0 + w];  // chunk of level j0 + w: offset, padded row count
+                            const float *pl = (const float *)(ub + e.x) + u;
 #pragma unroll
-                            for (int i = 0; i < 9; ++i) a[u][i] = __ldcs(uv + slot + (size_t)i * nup);
-                            vr[u] = __ldcs(A.unbr + slot);  // level 0: the row itself (diagonal block)
+                            for (int i = 0; i < 9; ++i) a[w][i] = __ldcs(pl + (size_t)i * e.y);
+                            // level 0: the row itself (diagonal block)
+                            vr[w] = __ldcs((const unsigned short *)(ub + e.x + 36 * (size_t)e.y) + u);
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (vr[u] >= 0) {
+                    for (int w = 0; w < 4; ++w) {
+                        if (vr[w] >= 0) {
                             CT pj[3];
-                            load3v(s_p4 + 4 * vr[u], pj);
-                            const CT s0 = a[u][0] * pj[0] + a[u][1] * pj[1] + a[u][2] * pj[2];
-                            const CT s1 = a[u][3] * pj[0] + a[u][4] * pj[1] + a[u][5] * pj[2];
-                            const CT s2 = a[u][6] * pj[0] + a[u][7] * pj[1] + a[u][8] * pj[2];
-                            if (j0 + u == 0) {
+                            load3v(s_p4 + 4 * vr[w], pj);
+                            const CT s0 = a[w][0] * pj[0] + a[w][1] * pj[1] + a[w][2] * pj[2];
+                            const CT s1 = a[w][3] * pj[0] + a[w][4] * pj[1] + a[w][5] * pj[2];
+                            const CT s2 = a[w][6] * pj[0] + a[w][7] * pj[1] + a[w][8] * pj[2];
+                            if (j0 + w == 0) {
                                 yd[0] = s0; yd[1] = s1; yd[2] = s2;
                             } else {
                                 yo[0] += s0; yo[1] += s1; yo[2] += s2;
-                                red_add4(yq + wlo + vr[u], a[u][0] * pi[0] + a[u][3] * pi[1] + a[u][6] * pi[2],
-                                         a[u][1] * pi[0] + a[u][4] * pi[1] + a[u][7] * pi[2],
-                                         a[u][2] * pi[0] + a[u][5] * pi[1] + a[u][8] * pi[2]);
+                                red_add4(yq + wlo + vr[w], a[w][0] * pi[0] + a[w][3] * pi[1] + a[w][6] * pi[2],
+                                         a[w][1] * pi[0] + a[w][4] * pi[1] + a[w][7] * pi[2],
+                                         a[w][2] * pi[0] + a[w][5] * pi[1] + a[w][8] * pi[2]);
                             }
                         }
                     }
@@ -1081,6 +1107,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 acc[0].add((pi[0] * yd[0] + pi[1] * yd[1]) + pi[2] * yd[2]);
                 acc[0].add(2.f * ((pi[0] * yo[0] + pi[1] * yo[1]) + pi[2] * yo[2]));
             }
+            if (threadIdx.x == 0) prefetch_round(0);  // the next product's first round, during the reductions
             if (timer) tm[6] += globaltimer() - tm[4];
             // this CTA's contact pairs: yq += mu gamma g (g . p)
             CT cdot = CT(0);
@@ -1243,15 +1270,17 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             for (int t = threadIdx.x; t < nr; t += blockDim.x) {
                 const int info = s_rinfo[t];
                 const int row = info >> 8, len = info & 255;
+                const int q = t / (int)blockDim.x, u = t - q * (int)blockDim.x;
                 double xi[3], h[3] = {0.0, 0.0, 0.0};
 #pragma unroll
                 for (int k = 0; k < 3; ++k) xi[k] = __ldcg(A.x + 3 * (r0 + row) + k);
                 for (int j = 0; j < len; ++j) {
-                    const size_t slot = U0 + s_lvl[j] + t;
+                    const int2 e = s_tab[q * lm + j];
+                    const float *pl = (const float *)(ub + e.x) + u;
                     double a[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) a[i] = (double)__ldcs(uv + slot + (size_t)i * nup);
-                    const int vr = j == 0 ? row : (int)__ldcs(A.unbr + slot);
+                    for (int i = 0; i < 9; ++i) a[i] = (double)__ldcs(pl + (size_t)i * e.y);
+                    const int vr = j == 0 ? row : (int)__ldcs((const unsigned short *)(ub + e.x + 36 * (size_t)e.y) + u);
                     double xj[3];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) xj[k] = __ldcg(A.x + 3 * (wlo + vr) + k);
@@ -1431,11 +1460,20 @@ static int make_partition(Scene &S, int grid, int *max_rows, int *max_ent, int *
 
 // Partition of the symmetric variant: row ranges with about equal upper
 // block counts; each CTA's window runs from its first row to its last upper
-// neighbour; the CTA's upper blocks in jagged order (rows by decreasing
-// upper length, ties by row; level 0 is every row's diagonal block, which
-// comes first in its upper row), stored from the CTA's first upper-row
-// position on, so the jagged slots of all CTAs tile [0, nnzb).
-static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int *max_win, int *max_len)
+// neighbour.  A CTA's rows are ordered by decreasing upper length (ties by
+// row) and taken in rounds of `block` rows, thread t of the CTA owning row
+// r * block + t of that order in round r.  The upper blocks are stored in
+// the order the CTA consumes them: round by round, and within a round level
+// by level (level 0 is every row's diagonal block, first in its upper row;
+// level j the j-th upper block of the rows longer than j, a prefix of the
+// round), each (round, level) chunk as 9 planes of FP32 values followed by
+// the 16-bit window offsets of the neighbours, its row count padded to 32
+// and its start aligned to 128 bytes.  A CTA's chunks are contiguous, so a
+// round can be prefetched into L2 as one range.  The chunk table of CTA c
+// (byte offset and padded count per round and level, then the end of its
+// last round) starts at entry tabptr[c].
+static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int *max_win, int *max_len,
+                              int *max_tab, size_t *bytes)
 {
     const std::vector<int> &rp = S.h_rowptr;
     const std::vector<int> &col = S.h_col;
@@ -1449,12 +1487,13 @@ static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int 
         part[c] = std::max(part[c - 1], r);
     }
     part[grid] = S.nv;
-    std::vector<int> win(2 * grid), rinfo(S.nv), lvl, lvlptr(grid + 1, 0), uedst(S.nnzb);
+    std::vector<int> win(2 * grid), rinfo(S.nv), tab, tabptr(grid + 1, 0), uedst(2 * (size_t)S.nnzb);
     std::vector<unsigned short> unbr(S.nnzb);
-    int mr = 0, mw = 0, ml = 0;
+    int mr = 0, mw = 0, ml = 0, mt = 0;
+    size_t off = 0;
     std::vector<int> order;
     for (int c = 0; c < grid; ++c) {
-        const int a = part[c], b = part[c + 1];
+        const int a = part[c], b = part[c + 1], nr = b - a;
         int hi = b;
         for (int v = a; v < b; ++v) {
             if (rp[v + 1] == rp[v] || col[rp[v]] != v) return BF_E_CAPACITY;  // diagonal block first
@@ -1463,32 +1502,43 @@ static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int 
         if (hi - a > 65535) return BF_E_CAPACITY;
         win[2 * c] = a;
         win[2 * c + 1] = hi;
-        order.resize(b - a);
+        order.resize(nr);
         for (int v = a; v < b; ++v) order[v - a] = v;
         auto len = [&](int v) { return rp[v + 1] - rp[v]; };
         std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return len(u) > len(v); });
-        const int lmax = b > a ? len(order[0]) : 0;
+        const int lmax = nr > 0 ? len(order[0]) : 0;
         if (lmax > 255) return BF_E_CAPACITY;
-        std::vector<int> at(lmax + 1, 0);
-        for (int j = 0; j < lmax; ++j) {
-            int n = 0;
-            while (n < b - a && len(order[n]) > j) ++n;
-            at[j + 1] = at[j] + n;
-        }
-        for (int t = 0; t < b - a; ++t) {
-            const int v = order[t];
-            rinfo[a + t] = (v - a) << 8 | len(v);
-            for (int j = 0; j < len(v); ++j) {
-                const int k = rp[v] + j, d = rp[a] + at[j] + t;
-                uedst[k] = d;
-                unbr[d] = (unsigned short)(col[k] - a);
+        const int rounds = cdiv(nr, block);
+        const size_t tab0 = tab.size();
+        tab.resize(tab0 + 2 * ((size_t)rounds * lmax + 1));
+        for (int q = 0; q < rounds; ++q) {
+            const int t0 = q * block, t1 = std::min(nr, t0 + block);
+            for (int j = 0; j < lmax; ++j) {
+                int n = 0;
+                while (t0 + n < t1 && len(order[t0 + n]) > j) ++n;
+                const int np = (n + 31) & ~31;
+                off = (off + 127) & ~(size_t)127;
+                if (off + 38 * (size_t)np > 0x7fffffffu) return BF_E_CAPACITY;
+                tab[tab0 + 2 * ((size_t)q * lmax + j)] = (int)off;
+                tab[tab0 + 2 * ((size_t)q * lmax + j) + 1] = np;
+                for (int u = 0; u < n; ++u) {
+                    const int v = order[t0 + u], k = rp[v] + j;
+                    uedst[2 * (size_t)k] = (int)off;
+                    uedst[2 * (size_t)k + 1] = np << 16 | u;
+                    unbr[k] = (unsigned short)(col[k] - a);
+                }
+                off += 38 * (size_t)np;
             }
         }
-        lvl.insert(lvl.end(), at.begin(), at.end());
-        lvlptr[c + 1] = (int)lvl.size();
-        mr = std::max(mr, b - a);
+        off = (off + 127) & ~(size_t)127;
+        tab[tab.size() - 2] = (int)off;  // end of the CTA's last round
+        tab[tab.size() - 1] = 0;
+        tabptr[c + 1] = (int)(tab.size() / 2);
+        for (int t = 0; t < nr; ++t) rinfo[a + t] = (order[t] - a) << 8 | len(order[t]);
+        mr = std::max(mr, nr);
         mw = std::max(mw, hi - a);
         ml = std::max(ml, lmax);
+        mt = std::max(mt, rounds * lmax + 1);
     }
     auto put = [&](auto *&dst, const auto &host) -> int {
         using T = std::remove_reference_t<decltype(*dst)>;
@@ -1502,26 +1552,32 @@ static int make_partition_sym(Scene &S, int grid, int block, int *max_rows, int 
     int st = put(S.part, part);
     if (!st) st = put(S.win, win);
     if (!st) st = put(S.pcg_rinfo, rinfo);
-    if (!st) st = put(S.pcg_lvl, lvl);
-    if (!st) st = put(S.pcg_lvlptr, lvlptr);
+    if (!st) st = put(S.pcg_lvl, tab);
+    if (!st) st = put(S.pcg_lvlptr, tabptr);
     if (!st) st = put(S.pcg_uedst, uedst);
     if (!st) st = put(S.pcg_unbr, unbr);
     if (st) return st;
     *max_rows = mr;
     *max_win = mw;
     *max_len = ml;
+    *max_tab = mt;
+    *bytes = off;
     return check_cuda(cudaStreamSynchronize(S.stream));
 }
 
-// symmetric variant: the upper blocks in jagged order, 9 planes
-__global__ void k_jagged_gather_upper(int nnzb, const int *__restrict__ uedst, const float *__restrict__ val,
-                                      float *__restrict__ uval)
+// symmetric variant: the upper blocks (9 FP32 planes) and their neighbour
+// offsets into the chunks of the consumption order
+__global__ void k_jagged_gather_upper(int nnzb, const int2 *__restrict__ uedst, const unsigned short *__restrict__ unbr,
+                                      const float *__restrict__ val, unsigned char *__restrict__ ubuf)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnzb) return;
-    const size_t d = (size_t)uedst[k];
+    const int2 e = uedst[k];
+    const int np = e.y >> 16, u = e.y & 0xffff;
+    float *pl = (float *)(ubuf + e.x) + u;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) uval[(size_t)i * nnzb + d] = val[9 * (size_t)k + i];
+    for (int i = 0; i < 9; ++i) pl[(size_t)i * np] = val[9 * (size_t)k + i];
+    ((unsigned short *)(ubuf + e.x + 36 * (size_t)np))[u] = unbr[k];
 }
 
 // Sets up the symmetric variant at `cps` CTAs per SM, if it fits.
@@ -1532,15 +1588,16 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nnzb, kPcgEntriesPerCta / 2)));
     if (grid > kPcgMaxGrid) return BF_E_CAPACITY;
     const int block = (kPcgThreads / cps) & ~31;
-    int mr = 0, mw = 0, ml = 0;
-    int st = make_partition_sym(S, grid, block, &mr, &mw, &ml);
+    int mr = 0, mw = 0, ml = 0, mt = 0;
+    size_t ubytes = 0;
+    int st = make_partition_sym(S, grid, block, &mr, &mw, &ml, &mt, &ubytes);
     if (st) return st;
     const size_t avail = smem_optin - fa.sharedSizeBytes;
-    const PcgSymLayout L0 = pcg_sym_layout(mr, mw, ml, 0);
+    const PcgSymLayout L0 = pcg_sym_layout(mr, mw, mt, 0);
     if (L0.total > avail) return BF_E_CAPACITY;
     int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(4));
-    while (kc > 0 && pcg_sym_layout(mr, mw, ml, kc).total > avail) --kc;
-    const PcgSymLayout L = pcg_sym_layout(mr, mw, ml, kc);
+    while (kc > 0 && pcg_sym_layout(mr, mw, mt, kc).total > avail) --kc;
+    const PcgSymLayout L = pcg_sym_layout(mr, mw, mt, kc);
     cudaFuncSetAttribute(k_pcg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_sym, block, L.total);
@@ -1550,7 +1607,7 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     if (S.pcg_uval) dev_free(S, S.pcg_uval);
     if (S.pcg_yq) dev_free(S, S.pcg_yq);
     S.pcg_gvec = (unsigned char *)dev_alloc(S, stride * grid);
-    S.pcg_uval = (float *)dev_alloc(S, 9 * (size_t)S.nnzb * sizeof(float));
+    S.pcg_uval = (float *)dev_alloc(S, std::max<size_t>(ubytes, 128));
     S.pcg_yq = (float4 *)dev_alloc(S, (size_t)S.nv * sizeof(float4));
     if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq) return BF_E_OOM;
     S.pcg_gvec_stride = stride;
@@ -1561,7 +1618,7 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     S.pcg_max_rows = mr;
     S.pcg_max_ent = S.nnzb;
     S.pcg_max_win = mw;
-    S.pcg_max_len = ml;
+    S.pcg_max_len = mt;  // chunk-table entries per CTA (rounds x levels + 1)
     S.pcg_kc = kc;
     return BF_OK;
 }
@@ -1775,8 +1832,8 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.yq = S.pcg_yq;
     if (S.pcg_resident == PCG_SYM) {
         if constexpr (std::is_same<MT, float>::value) {
-            k_jagged_gather_upper<<<cdiv(S.nnzb, kThreads), kThreads, 0, S.stream>>>(S.nnzb, S.pcg_uedst, val,
-                                                                                   S.pcg_uval);
+            k_jagged_gather_upper<<<cdiv(S.nnzb, kThreads), kThreads, 0, S.stream>>>(
+                S.nnzb, (const int2 *)S.pcg_uedst, S.pcg_unbr, val, (unsigned char *)S.pcg_uval);
             ++S.n_launch;
         } else {
             return BF_E_ARG;
