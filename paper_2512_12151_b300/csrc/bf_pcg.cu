@@ -89,13 +89,11 @@ struct PcgArgs {
     int maxit, max_replace, max_rows, max_ent, max_win, max_len, kc;
     double *dscal;
     int *dflag;
-    // symmetric variant: upper blocks in jagged order (9 planes of nup
-    // values), their window offsets, the upper row pointer, and the
-    // accumulation vector of transposed products and contact terms
-    const float *uval;
-    const unsigned short *unbr;
-    const int *urowptr;
-    size_t nup;
+    // symmetric variant: the upper blocks in consumption order (chunks of 9
+    // FP32 planes and 16-bit neighbour offsets; chunk table in lvl, its
+    // per-CTA start in lvlptr) and the accumulation vector of transposed
+    // products and contact terms
+    const void *uval;
     float4 *yq;
 };
 
@@ -835,12 +833,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
 // diagonal blocks, p.Hp = sum_i p_i.D_i p_i + 2 sum_{i<j} p_i.B_ij p_j,
 // which each row's thread forms from its own blocks.
 //
-// Per CTA: rows [part[c], part[c+1]) in order of decreasing upper length
-// (jagged levels as in the full-row variants; level 0 is the diagonal
-// block), the window of p over [part[c], last upper neighbour] in shared
-// memory (16-bit offsets), r and the FP32 increment of x per row in shared
-// memory, the rows' part of q, FP64 x and H x of the reliable updates in a
-// per-CTA global vector (L2-resident).
+// Per CTA: rows [part[c], part[c+1]) in order of decreasing upper length,
+// taken in rounds of blockDim.x rows (one per thread); the blocks stream in
+// the order they are consumed (round, then level; level 0 is the diagonal
+// block) and each round is prefetched into L2 while the previous one is
+// summed, the first during the reductions before the product; the window
+// of p over [part[c], last upper neighbour] in shared memory (16-bit
+// offsets); r and the FP32 increment of x per row in shared memory; the
+// rows' part of q, FP64 x and H x of the reliable updates in a per-CTA
+// global vector (L2-resident).
 // ---------------------------------------------------------------------------
 struct PcgSymLayout {
     size_t p4, r, xl, rinfo, lvl, cg, cp, cw, cv, cm, total;
@@ -1826,9 +1827,6 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         ++S.n_launch;
     }
     A.uval = S.pcg_uval;
-    A.unbr = S.pcg_unbr;
-    A.urowptr = S.rowptr;
-    A.nup = (size_t)S.nnzb;
     A.yq = S.pcg_yq;
     if (S.pcg_resident == PCG_SYM) {
         if constexpr (std::is_same<MT, float>::value) {
