@@ -441,6 +441,21 @@ class Oracle:
         E = lib().or_friction_eval(C.c_void_p(self.h), _p(_f64(xhat, 3 * self.nv)), _p(g), _p(A))
         return E, g, A[:nf]
 
+    def step_logged(self, max_iters=200):
+        """one time step with its logs: (status, stats, alphas, xhats) where
+        alphas[k] = alpha^[k+1] and xhats[k] = xhat^[k+1] of outer iteration k"""
+        n = 3 * self.nv
+        buf = np.zeros((max_iters, n))
+        lib().or_set_xhat_log(C.c_void_p(self.h), _p(buf), C.c_int32(max_iters))
+        try:
+            status, st, alog = self.step(1, alpha_cap=max_iters)
+            m = lib().or_xhat_log_count(C.c_void_p(self.h))
+        finally:
+            lib().or_set_xhat_log(C.c_void_p(self.h), None, C.c_int32(0))
+        k = st[0]["outer_iters"]
+        assert m == k <= max_iters
+        return status, st, alog[:k], buf[:k].reshape(k, self.nv, 3)
+
     def step(self, n=1, alpha_cap=0):
         st = (OrStats * max(n, 1))()
         alog = np.zeros(max(alpha_cap, 1))

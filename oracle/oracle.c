@@ -57,6 +57,10 @@ struct or_scene {
     /* gradient-norm residuals of the last step's outer iterations */
     int nres, rescap;
     double *res;
+    /* optional log of the intermediate states xhat^[k] of the next time
+     * steps' outer iterations (caller-owned, 3 nv doubles each) */
+    double *xhat_log;
+    int xhat_cap, xhat_n;
 };
 
 /* ------------------------------------------------------------------ */
@@ -1888,6 +1892,20 @@ int32_t or_min_distance(or_scene *S, const double *x, double *dmin)
 /* x^[k] falls below res_tol (the IPC-style termination of section 6),   */
 /* checked before each outer iteration, from x^[0] = x^t on.             */
 /* ------------------------------------------------------------------ */
+/* The intermediate states xhat^[1], xhat^[2], ... of the outer iterations
+ * of the following or_step calls are copied into buf (cap states of 3 nv
+ * doubles; NULL stops the log); returns the count logged so far.  Test
+ * hook for the expansion of x^[k] in the termination criterion. */
+int32_t or_set_xhat_log(or_scene *S, double *buf, int32_t cap)
+{
+    S->xhat_log = buf;
+    S->xhat_cap = buf ? cap : 0;
+    S->xhat_n = 0;
+    return 0;
+}
+
+int32_t or_xhat_log_count(const or_scene *S) { return S->xhat_n; }
+
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log, int32_t alpha_cap)
 {
     int n = 3 * S->nv;
@@ -1930,6 +1948,8 @@ int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
             st.cg_iters += cgi;
             st.ls_fail += lsf;
             or_update_active_set(S, xk, S->p.ccd_reuse ? xhn : xh);
+            if (S->xhat_log && S->xhat_n < S->xhat_cap)
+                memcpy(S->xhat_log + (size_t)n * S->xhat_n++, xhn, n * sizeof(double));
             double alpha = or_max_step_size(S, xk, xhn);
             for (int i = 0; i < n; ++i) xk[i] = (1.0 - alpha) * xk[i] + alpha * xhn[i];
             if (k + 1 >= S->p.k_min) beta = (1.0 - alpha) * beta;

@@ -128,6 +128,10 @@ double or_newton_residual(or_scene *S, const double *xtilde, const double *x);
 int32_t or_get_residual_log(const or_scene *S, int32_t cap, double *out);
 int32_t or_step(or_scene *S, int32_t nsteps, or_stats *stats, double *alpha_log,
                 int32_t alpha_cap);
+/* test hook: log xhat^[k] of the following steps' outer iterations into
+ * buf (cap states of 3 nv doubles; NULL stops); the count logged so far */
+int32_t or_set_xhat_log(or_scene *S, double *buf, int32_t cap);
+int32_t or_xhat_log_count(const or_scene *S);
 int32_t or_min_distance(or_scene *S, const double *x, double *dmin);
 
 /* ---- semi-implicit friction (appendix A) ---- */

@@ -215,27 +215,46 @@ def test_broad_phase_sweep_equals_brute_force():
     assert A == B
 
 
-def test_beta_closed_form_and_penetration_free():
-    """beta from the logged alphas (Eq. termination) and a positive minimum
-    distance after every step (section 3 path constraint)."""
+def _beta_weights(alphas):
+    """beta_i^[K], i = 0..K, of the termination criterion written out from
+    its definition: alpha^[i] times the product of (1 - alpha^[j]) for j > i,
+    with alpha^[0] = 1 (so x^[K] = sum_i beta_i x_hat^[i], x_hat^[0] = x^t)"""
+    a = np.concatenate([[1.0], alphas])
+    K = len(alphas)
+    return np.array([a[i] * np.prod(1.0 - a[i + 1:K + 1]) for i in range(K + 1)])
+
+
+@pytest.mark.parametrize("k_min", [1, 2, 3])
+def test_beta_expansion_and_termination(k_min):
+    """Eq. termination from its definition, not from the loop's recurrence:
+    x^[K] equals the weighted sum of x^t and the logged intermediate states
+    x_hat^[i] with the weights beta_i^[K] computed from the logged step
+    sizes; the weights sum to one; the reported beta is the total weight of
+    the first K_min states (indices 0..K_min-1), below eps, while the same
+    sum after K - 1 iterations was not (the loop could not stop earlier);
+    and every step stays penetration-free (section 3 path constraint)."""
     s = scenes.two_cubes(0)
-    o = O.Oracle(s)
+    p = scenes.Params(**{**s.params.__dict__, "k_min": k_min})
+    o = O.Oracle(s, p)
     total = 0
-    for step in range(10):
-        status, st, alog = o.step(1, alpha_cap=2000)
+    for step in range(8):
+        xt, _ = o.get_state()
+        status, st, alphas, xhats = o.step_logged()
         assert status == 0
-        k = st[0]["outer_iters"]
-        a = alog[:k]
-        beta = 1.0
-        for i, al in enumerate(a):
-            if i + 1 >= s.params.k_min:
-                beta = (1 - al) * beta
-        assert beta == st[0]["beta"] and beta <= s.params.eps
-        assert (a > 0).all() and (a <= 1).all()
+        K = st[0]["outer_iters"]
+        assert K >= k_min and (alphas > 0).all() and (alphas <= 1).all()
+        w = _beta_weights(alphas)
         x, _ = o.get_state()
+        recon = w[0] * xt + np.tensordot(w[1:], xhats, axes=1)
+        assert np.abs(recon - x).max() <= 1e-12 * max(1.0, np.abs(x).max())
+        assert abs(w.sum() - 1.0) <= 1e-12
+        beta = w[:k_min].sum()
+        assert abs(beta - st[0]["beta"]) <= 1e-14 and beta <= s.params.eps
+        if K > k_min:  # with K = k_min the loop could not have stopped earlier anyway
+            assert _beta_weights(alphas[:-1])[:k_min].sum() > s.params.eps
         assert o.min_distance(x) > 0
-        total += k
-    assert total > 20
+        total += K
+    assert total > 16
 
 
 def test_moving_boundary_error_bound():
