@@ -761,9 +761,9 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         BF_ALLOC(S.cg_pf2, float, n3);
         BF_ALLOC(S.cg_qcf, float, n3);
     } else {
-        BF_ALLOC(S.val, double, 9 * (size_t)S.nnzb);
         BF_ALLOC(S.pinv, double, 9 * (size_t)nv);
     }
+    BF_ALLOC(S.val, double, 9 * (size_t)S.nnzb);  // FP64 block sums (the FP32 copy in mixed precision)
     BF_ALLOC(S.cdiag, double, 9 * (size_t)nv);
     BF_ALLOC(S.grad, double, n3);
     BF_ALLOC(S.cg_x, double, n3);

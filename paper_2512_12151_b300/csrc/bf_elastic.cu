@@ -390,6 +390,13 @@ __global__ void __launch_bounds__(128) k_elastic(int nt, const int4 *__restrict_
         }
 }
 
+// FP32 copy of the FP64 block sums (mixed precision)
+__global__ void k_round_blocks(size_t n, const double *__restrict__ v64, float *__restrict__ v32)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v32[i] = (float)v64[i];
+}
+
 void launch_elastic(Scene &S, const double *xhat)
 {
     if (S.nt == 0) return;
@@ -398,11 +405,19 @@ void launch_elastic(Scene &S, const double *xhat)
     const int nb = cdiv(S.nt, 128);
     const int m = S.prm.model;
     if (S.prm.precision == BF_PREC_MIXED) {
-        auto kern = m == BF_MODEL_COR  ? k_elastic<float, float, BF_MODEL_COR>
-                    : m == BF_MODEL_NH ? k_elastic<float, float, BF_MODEL_NH>
-                                       : k_elastic<float, float, BF_MODEL_SNH>;
-        kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.valf,
+        // FP32 element Hessians, summed into the blocks in FP64 and stored
+        // in FP32: the order of the atomics then moves only the last bits
+        // of an FP64 sum, which the FP32 rounding almost always hides, so
+        // a step does not depend on the scheduling of its kernels (scenes
+        // alone or in a batch take the same steps)
+        auto kern = m == BF_MODEL_COR  ? k_elastic<float, double, BF_MODEL_COR>
+                    : m == BF_MODEL_NH ? k_elastic<float, double, BF_MODEL_NH>
+                                       : k_elastic<float, double, BF_MODEL_SNH>;
+        kern<<<nb, 128, 0, S.stream>>>(S.nt, S.tets, S.B, S.vol, S.emu, S.elam, S.dir, xhat, h2, S.grad, S.val,
                                        S.nnzb, S.tblk);
+        ++S.n_launch;
+        const size_t nval = 9 * (size_t)S.nnzb;
+        k_round_blocks<<<cdiv((long long)nval, kThreads), kThreads, 0, S.stream>>>(nval, S.val, S.valf);
     } else {
         auto kern = m == BF_MODEL_COR  ? k_elastic<double, double, BF_MODEL_COR>
                     : m == BF_MODEL_NH ? k_elastic<double, double, BF_MODEL_NH>
@@ -438,15 +453,10 @@ __global__ void k_vertex_init(int nv, int nnzb, const int *__restrict__ diagblk,
 void launch_vertex_init(Scene &S, const double *xtilde, const double *xhat)
 {
     const int nb = cdiv(S.nv, kThreads);
-    if (S.prm.precision == BF_PREC_MIXED) {
-        cudaMemsetAsync(S.valf, 0, 9 * (size_t)S.nnzb * sizeof(float), S.stream);
-        k_vertex_init<float><<<nb, kThreads, 0, S.stream>>>(S.nv, S.nnzb, S.diagblk, S.mass, S.dir, xtilde, xhat,
-                                                            S.grad, S.valf, S.cdiag); ++S.n_launch;
-    } else {
-        cudaMemsetAsync(S.val, 0, 9 * (size_t)S.nnzb * sizeof(double), S.stream);
-        k_vertex_init<double><<<nb, kThreads, 0, S.stream>>>(S.nv, S.nnzb, S.diagblk, S.mass, S.dir, xtilde, xhat,
-                                                             S.grad, S.val, S.cdiag); ++S.n_launch;
-    }
+    // the blocks are summed in FP64 in both precisions (launch_elastic)
+    cudaMemsetAsync(S.val, 0, 9 * (size_t)S.nnzb * sizeof(double), S.stream);
+    k_vertex_init<double><<<nb, kThreads, 0, S.stream>>>(S.nv, S.nnzb, S.diagblk, S.mass, S.dir, xtilde, xhat,
+                                                         S.grad, S.val, S.cdiag); ++S.n_launch;
 }
 
 // max over free DoFs of the diagonal entries (section 5.2 mu_init)

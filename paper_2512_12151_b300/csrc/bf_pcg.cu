@@ -81,7 +81,7 @@ struct PcgArgs {
     const void *pinv;
     const double *b;
     double *x;
-    void *z, *p0, *p1, *qc;  // qc: contact part of H p (atomics)
+    void *z, *p0, *p1, *qc;  // qc: unused by the persistent kernels (contact parts go to qd)
     double *qd;               // FP64 contact part of H x (reliable updates)
     double *res;
     unsigned *bar;
@@ -381,7 +381,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
     const MT *__restrict__ gpinv = (const MT *)A.pinv;
     VT *__restrict__ z = (VT *)A.z;
     VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
-    VT *__restrict__ qc = (VT *)A.qc;
+    // contact part of H p, accumulated in FP64 in both precisions (the order
+    // of the atomics then changes only the last bits of an FP64 sum)
+    double *__restrict__ qcd = A.qd;
     const int c = blockIdx.x;
     const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
     const int wlo = A.win[2 * c], whi = A.win[2 * c + 1], nwin = whi - wlo;
@@ -518,8 +520,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 s_r[k * ld + i] = rv[k];
                 s_x[k * ld + i] = 0.0;
                 if (mixed) s_xl[k * ld + i] = RT(0);
-                qc[3 * a + k] = VT(0);
-                if (mixed) A.qd[3 * a + k] = 0.0;
+                qcd[3 * a + k] = 0.0;
                 if (A.nc > 0) pb[0][3 * a + k] = VT(0);
                 bb += bk * bk;  // |b|^2 in FP64
             }
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             auto getp = [&](int vr, CT *o) { load3v(s_p4 + 4 * vr, o); };
             row_sums<2, CT>(nr, s_rinfo, getp, ent, s_q, ld);
             if (timer) tR += globaltimer() - t0;
-            // this CTA's contact pairs: y += mu gamma g (g . p) into qc
+            // this CTA's contact pairs: y += mu gamma g (g . p) into qcd
             CT cdot = CT(0);
             for (int k = threadIdx.x; k < nco; k += blockDim.x) {
                 CT g[12], u[12], w;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 for (int q = 0; q < 4; ++q)
                     if (m >> q & 1)
 #pragma unroll
-                        for (int j = 0; j < 3; ++j) atomicAdd(qc + 3 * vid[q] + j, (VT)(t * g[3 * q + j]));
+                        for (int j = 0; j < 3; ++j) atomicAdd(qcd + 3 * vid[q] + j, (double)(t * g[3 * q + j]));
                 cdot += t * s;
             }
             __syncthreads();
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 const int a = r0 + i;
                 VT qg[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) qg[k] = __ldcg(qc + 3 * a + k);
+                for (int k = 0; k < 3; ++k) qg[k] = (VT)__ldcg(qcd + 3 * a + k);
                 CT pc[3];
                 load3v(s_p4 + 4 * (a - wlo), pc);
                 RT rv[3];
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                     else s_x[k * ld + i] += alpha * (double)pc[k];
                     rv[k] = s_r[k * ld + i] - al * ((RT)s_q[k * ld + i] + (RT)qg[k]);
                     s_r[k * ld + i] = rv[k];
-                    qc[3 * a + k] = VT(0);
+                    qcd[3 * a + k] = 0.0;
                 }
                 acc_add(acc[0], precond(i, rv));
                 acc_add(acc[1], ((CT)rv[0] * (CT)rv[0] + (CT)rv[1] * (CT)rv[1]) + (CT)rv[2] * (CT)rv[2]);
@@ -1806,7 +1807,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.p0 = p0;
     A.p1 = p1;
     A.qc = qc;
-    A.qd = S.cg_qc;  // FP64 scratch of the reliable updates (mixed only; qc is FP32 then)
+    A.qd = S.cg_qc;  // FP64 contact part of H p, and of H x in the reliable updates
     A.res = S.dscal + S_RES;
     A.bar = S.bar;
     A.tol2 = tol * tol;

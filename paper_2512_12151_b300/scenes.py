@@ -264,6 +264,16 @@ def batch_scene(seed: int, t_lo: float = 1e3, t_hi: float = 2e4, precision: int 
                    {"seed": seed, "cells": cells, "cubes": k, "E": E, "nu": nu, "target_tets": target})
 
 
+def batch_scene_size(seed: int, t_lo: float = 1e3, t_hi: float = 2e4) -> int:
+    """tet count of batch_scene(seed, t_lo, t_hi) without building it (the
+    same seeded draws)"""
+    rng = np.random.default_rng(seed)
+    target = math.exp(rng.uniform(math.log(t_lo), math.log(t_hi)))
+    k = 1 + int(rng.random() < 0.5)
+    cells = max(2, int(round((target / (6 * k)) ** (1.0 / 3.0))))
+    return 6 * k * cells ** 3
+
+
 def single_cube(seed: int = 0, cells: int = 2, side: float = 0.1, z: float = 0.5,
                 v0=(0.0, 0.0, 0.0), with_ground: bool = False, gravity=(0.0, 0.0, -9.8),
                 xy=(0.0, 0.0)) -> Scene:

@@ -149,8 +149,34 @@ def poisson_requests(n, rate, seed=0, t_lo=2e3, t_hi=2e5, precision=1):
     return [(float(a), int(rng.integers(1 << 30)), t_lo, t_hi, precision) for a in arrivals]
 
 
+def waits_bounded(w):
+    """Whether admission waits (in arrival order) stay bounded over a run:
+    below a saturated server they grow with every request, so the mean wait
+    of the last third of the requests exceeds twice that of the first third
+    (plus 50 ms for the jitter of scene creation)."""
+    n = len(w) // 3
+    if n == 0:
+        return True
+    return bool(np.mean(w[-n:]) <= 2.0 * np.mean(w[:n]) + 0.05)
+
+
+def rate_sweep(rates, n_requests, n_steps=10, n_workers=16, seed=0, **kw):
+    """Serves `n_requests` requests at each arrival rate; per rate the
+    throughput, admission waits and whether they stay bounded, and the
+    highest rate at which they do (the sustainable rate, None if none)"""
+    runs = []
+    for r in rates:
+        res = serve(poisson_requests(n_requests, r, seed=seed), n_steps=n_steps, n_workers=n_workers, **kw)
+        runs.append({"rate_per_s": r, "steps_per_s": res["steps_per_s"],
+                     "admission_wait_p50_ms": res["admission_wait_p50_ms"],
+                     "admission_wait_p99_ms": res["admission_wait_p99_ms"],
+                     "bounded": res["admission_wait_bounded"], "failed": res["failed"]})
+    ok = [x["rate_per_s"] for x in runs if x["bounded"] and x["failed"] == 0]
+    return {"sustainable_rate_per_s": max(ok) if ok else None, "runs": runs, "requests_per_rate": n_requests}
+
+
 def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.002, timeout_s=900.0,
-          n_creators=8, blocking_sync=False):
+          n_creators=8, blocking_sync=False, keep_states=()):
     """Serves a request stream: at each arrival time the request is handed
     to one of `n_creators` host threads, which generates and creates its
     scene and admits it to the running batch (waiting while the HBM budget
@@ -160,32 +186,47 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
     scene's previous step, or its admission) and the admission wait
     (admission minus arrival, scene creation included) p50/p99.  With
     `blocking_sync` the batch's worker threads sleep in their waits
-    (bf_batch_set_blocking_sync): shorter step latency, longer admission."""
+    (bf_batch_set_blocking_sync): shorter step latency, longer admission.
+    For the request indices in `keep_states` the result also holds the end
+    positions (`states`) and how many other scenes were in the batch when
+    each was admitted (`live_at_admission`)."""
     from concurrent.futures import ThreadPoolExecutor
     b = B.bf_batch_create(n_workers, budget_bytes)
     if blocking_sync:  # worker threads sleep in their waits, leaving host cores to the creators
         B.bf_batch_set_blocking_sync(b, True)
     deadline = time.monotonic() + timeout_s
-    live = {}  # ticket -> (handle, keep)
+    live = {}  # ticket -> (handle, keep, request index, vertices)
     lat, waits, steps, bad, statuses = [], [], 0, 0, []
+    states, live_at = {}, {}
+    t_gen, t_create = [], []  # host seconds per request: mesh generation, bf_scene_create
+    keep_states = set(keep_states)
     lock = threading.Lock()
     t0 = B.bf_batch_now(b)
 
-    def admit(req):
+    def admit(idx, req):
         arrival, seed, t_lo, t_hi, prec = req
+        c0 = time.perf_counter()
         s = scenes.batch_scene(seed, t_lo, t_hi, precision=prec)
+        c1 = time.perf_counter()
         h, keep = create(s)
+        c2 = time.perf_counter()
+        with lock:
+            t_gen.append(c1 - c0)
+            t_create.append(c2 - c1)
         while True:
-            t = B.bf_batch_admit(b, h, n_steps)
-            if t is not None:
-                break
+            with lock:
+                n_live = len(live)
+                t = B.bf_batch_admit(b, h, n_steps)
+                if t is not None:
+                    waits.append((arrival, B.bf_batch_now(b) - t0 - arrival))
+                    live[t] = (h, keep, idx, s.nv)
+                    if idx in keep_states:
+                        live_at[idx] = n_live
+                    break
             if time.monotonic() > deadline:
                 B.bf_scene_destroy(h)
                 raise TimeoutError("admission kept being refused by the HBM budget")
             time.sleep(poll_s)
-        with lock:
-            waits.append(B.bf_batch_now(b) - t0 - arrival)
-            live[t] = (h, keep)
 
     def reap(block=False):
         nonlocal steps, bad
@@ -198,7 +239,10 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
                 continue
             r = B.bf_batch_result(b, t, n_steps)
             with lock:
-                h, _keep = live.pop(t)
+                h, _keep, idx, nv = live.pop(t)
+            if idx in keep_states:
+                states[idx] = B.bf_get_state(h, nv)[0]
+            with lock:
                 lat.extend(_latencies(r))
                 steps += r["steps_done"]
                 bad += r["status"] != 0
@@ -210,11 +254,11 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
     pool = ThreadPoolExecutor(max_workers=n_creators)
     try:
         futures = []
-        for req in requests:
+        for idx, req in enumerate(requests):
             while B.bf_batch_now(b) - t0 < req[0]:
                 reap()
                 time.sleep(min(poll_s, max(0.0, req[0] - (B.bf_batch_now(b) - t0))))
-            futures.append(pool.submit(admit, req))
+            futures.append(pool.submit(admit, idx, req))
         for f in futures:
             f.result(timeout=max(1.0, deadline - time.monotonic()))
         with lock:
@@ -224,15 +268,21 @@ def serve(requests, n_steps=10, n_workers=16, budget_bytes=150 << 30, poll_s=0.0
         last_done = B.bf_batch_now(b)
         reap(block=True)
         out = _summary(lat, steps, last_done - t0 - requests[0][0] if requests else 0.0)
-        w = np.asarray(waits)
-        out.update({"requests": len(requests), "failed": bad, "failed_status": statuses, "workers": n_workers,
+        w = np.asarray([x[1] for x in sorted(waits)])  # in arrival order
+        out.update({"admission_wait_bounded": waits_bounded(w),"requests": len(requests), "failed": bad, "failed_status": statuses, "workers": n_workers,
                     "creators": n_creators,
                     "admission_wait_p50_ms": float(np.percentile(w, 50) * 1e3) if len(w) else None,
                     "admission_wait_p99_ms": float(np.percentile(w, 99) * 1e3) if len(w) else None,
-                    "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None})
+                    "offered_rate_per_s": len(requests) / requests[-1][0] if requests else None,
+                    "host_generate_ms_mean": float(np.mean(t_gen) * 1e3) if t_gen else None,
+                    "host_create_ms_mean": float(np.mean(t_create) * 1e3) if t_create else None,
+                    "host_create_ms_p99": float(np.percentile(t_create, 99) * 1e3) if t_create else None})
+        if keep_states:
+            out["states"] = states
+            out["live_at_admission"] = live_at
         return out
     finally:
         pool.shutdown(wait=True)
         B.bf_batch_destroy(b)  # stops the workers after their current step
-        for h, _k in list(live.values()):
+        for h, *_rest in list(live.values()):
             B.bf_scene_destroy(h)

@@ -130,3 +130,42 @@ def test_large_steps_complete(torch_cuda, spiky, reuse):
         x, v = sim.state()
         assert np.isfinite(x).all() and np.isfinite(v).all()
     sim.close()
+
+
+def test_large_subproblem_teacher_forced(torch_cuda):
+    """One outer iteration of the compression, teacher-forced from the same
+    state on both sides, on the spiky-ball scene meshed at twice the cell
+    size (287,448 tets, 1/8 of the full scene's; the same generator): the
+    plate's targets 6 cm lower, into the top ball's spikes; UpdateActiveSet
+    along x^t -> xhat^[0] gives the same pairs; the AL subproblem (Alg. 2,
+    mixed precision on the GPU, FP64 in the oracle) lands within 1e-4 x the
+    bounding-box diagonal with the same multiplier signs and decay factors;
+    MaxStepSize from the oracle's xhat^[1] is bit-identical."""
+    torch = torch_cuda
+    s = scenes.spiky_balls(0, cell=0.0078, precision=1)
+    assert 250_000 < s.nt < 330_000
+    o = O.Oracle(s, scenes.Params(**{**s.params.__dict__, "precision": 0}))
+    sim = B.Sim(s)
+    x = s.x0
+    xh = x.copy()
+    xh[s.meta["plate_vertices"], 2] -= 0.06
+    xt = o.xtilde()
+    mu = o.mu_init(xh, xt)
+    B.bf_set_mu(sim.h, mu, s.params.delta)
+    o.update_active_set(x, xh)
+    B.bf_update_active_set(sim.h, dev(torch, x), dev(torch, xh))
+    ko, lo, go = o.active_get()
+    kg, lg, gg = B.bf_get_active_set(sim.h)
+    assert len(ko) > 20 and (ko == kg).all() and (go == gg).all()
+    xh_o, nn_o, cg_o, lsf_o = o.solve_subproblem(xt, x, xh)
+    xh_g = dev(torch, xh)
+    nn_g, cg_g = B.bf_solve_subproblem(sim.h, dev(torch, xt), dev(torch, x), xh_g)
+    err = np.abs(host(xh_g) - xh_o).max() / s.bbox_diag()
+    print(f"subproblem: Newton {nn_g} (oracle {nn_o}), CG {cg_g} ({cg_o}), max error / diagonal {err:.2e}")
+    assert err <= 1e-4
+    ko, lo, go = o.active_get()
+    kg, lg, gg = B.bf_get_active_set(sim.h)
+    assert (ko == kg).all() and (go == gg).all()
+    assert np.abs(lg - lo).max() <= 1e-3 * max(1e-12, np.abs(lo).max())
+    assert B.bf_max_step_size(sim.h, dev(torch, x), dev(torch, xh_o)) == o.max_step_size(x, xh_o)
+    sim.close()
