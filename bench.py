@@ -238,16 +238,40 @@ def schedule(s, scenes):
 # the oracle on the host cores: the CPU baseline and the reference values of
 # the error against FP64 (the only part of this file that runs oracle/)
 # ---------------------------------------------------------------------------
-def oracle_leg(prefix, seconds):
-    """Child process, started before any CUDA call.  (1) The eight-cube
+def _oracle_batch_scene(i):
+    """one batched scene, 10 steps, in a worker process of the all-core leg"""
+    import oracle as O
+    from paper_2512_12151_b300 import scenes
+    o = O.Oracle(scenes.batch_scene(i))
+    t0 = time.perf_counter()
+    status, _ = o.step(10)
+    return 10, time.perf_counter() - t0, status
+
+
+def oracle_leg(prefix, seconds, batch_scenes=0):
+    """Child process, started before any CUDA call.  (0) The two-cube scene
+    in FP64, all 20 steps, positions after each saved.  (1) The eight-cube
     scene from the oracle's own stored state after 16 steps (in contact):
     two steps timed, positions saved.  (2) The spiky-ball scene from rest:
     whole steps with the plate schedule until `seconds` have elapsed (at
-    least one), the positions after the first step saved.  Prints one JSON
-    line."""
+    least one), the positions after the first step saved.  (3) Once the
+    file prefix_go exists (the GPU runs are over): the first `batch_scenes`
+    batched scenes, 10 steps each, one scene per host core (spawned
+    workers).  Prints one JSON line after each part."""
     import oracle as O
     from paper_2512_12151_b300 import scenes
     out = {}
+    s = scenes.two_cubes(0)
+    o = O.Oracle(s)
+    xs = []
+    t0 = time.perf_counter()
+    for _ in range(s.n_steps):
+        status, _st = o.step(1)
+        xs.append(o.get_state()[0])
+    el = time.perf_counter() - t0
+    np.save(prefix + "_two.npy", np.array(xs))
+    out["two"] = {"value": s.n_steps / el, "seconds": el, "steps": s.n_steps, "status": status}
+    print(json.dumps(out), flush=True)
     g = np.load(GOLDEN)
     s = scenes.eight_cubes(0)
     o = O.Oracle(s)
@@ -281,16 +305,31 @@ def oracle_leg(prefix, seconds):
     out["large"] = {"value": n / el, "seconds": el, "steps": n, "status": status,
                     "outer_iters": [x["outer_iters"] for x in stats], "contacts": [x["n_contacts"] for x in stats]}
     print(json.dumps(out), flush=True)
+    # the all-core part waits until the GPU runs are over (their host threads
+    # would otherwise compete with it for the cores)
+    deadline = time.monotonic() + 1800
+    while batch_scenes > 0 and not os.path.exists(prefix + "_go") and time.monotonic() < deadline:
+        time.sleep(0.5)
+    if batch_scenes > 0:
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_batch_scene, range(batch_scenes), chunksize=1)
+        el = time.perf_counter() - t0
+        out["batched"] = {"value": sum(r[0] for r in res) / el, "seconds": el, "scenes": batch_scenes,
+                          "cores": cores, "failed": sum(1 for r in res if r[2] != 0)}
+        print(json.dumps(out), flush=True)
     return 0
 
 
-def start_oracle_leg(seconds):
+def start_oracle_leg(seconds, batch_scenes):
     """the oracle leg in a child process (fork + exec: no CUDA state is shared)"""
     import tempfile
     prefix = os.path.join(tempfile.mkdtemp(prefix="bf_oracle_"), "leg")
     proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-leg", prefix,
-                             "--cpu-seconds", str(seconds)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
-                            text=True)
+                             "--cpu-seconds", str(seconds), "--cpu-batch-scenes", str(batch_scenes)],
+                            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     return proc, prefix
 
 
@@ -513,16 +552,21 @@ def run_large(args, torch, B, scenes, stream, ws, peak, peak_kind):
         torch.cuda.synchronize()
         barrier(ws)
         e2e_s = 0.0
+        st3 = []
         for i in range(lo, hi):
             tg = scenes.plate_targets_schedule(s, i)
             t0 = time.perf_counter()
             B.bf_set_obstacle_targets(sim.h, tg)
-            B.bf_step_host(sim.h, xin, vin, xin, vin)
+            st3.append(B.bf_step_host(sim.h, xin, vin, xin, vin))
             e2e_s += time.perf_counter() - t0
         e2e_s = allmax(ws, e2e_s)
         nbytes = 2 * s.nv * 3 * 8
         e2e = {"value": allsum(ws, K) / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nbytes + tg.nbytes,
-               "d2h_bytes_per_step": nbytes}
+               "d2h_bytes_per_step": nbytes,
+               "mean_outer_iters": statistics.mean(x["outer_iters"] for x in st3),
+               "mean_cg_iters_per_step": statistics.mean(x["cg_iters"] for x in st3),
+               "note": "the same window replayed from a checkpoint; contact decisions may differ from pass 1 in "
+                       "the last bits of FP32 vector reductions, so the iteration counts are given"}
         _progress(f"large pass 3 (end to end): {e2e['value']:.3f} steps/s")
     # ---- the release: the rest of the schedule ----------------------------
     for i in range(hi, N):
@@ -719,6 +763,36 @@ def run_eight(args, torch, B, scenes, stream, flush, ws, peak, peak_kind, seed):
             "tuned": (tuned_mode, tuned_us)}
 
 
+def run_two(torch, B, scenes, stream, flush, ws):
+    """The small plain-FP64 configuration: two cubes (4^3 cells, 384 tets
+    each), all 20 steps from rest, each timed with CUDA events after the L2
+    flush; the positions after each step for the comparison with the
+    oracle's run of the same steps."""
+    s = scenes.two_cubes(0)
+    sim = B.Sim(s, stream=stream.cuda_stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(s.n_steps)]
+    xs, stats = [], []
+    for i in range(s.n_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        _, st = sim.step(1)
+        ev[i][1].record(stream)
+        stats.append(st[0])
+        xs.append(sim.state()[0])
+    torch.cuda.synchronize()
+    sim.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    p50, p99 = _pcts(ms)
+    return {"workload": "two_cubes: 2 cubes x 4^3 cells (768 tets, 250 verts), the upper 1 mm above the lower, "
+                        "falling onto a static ground quad; SNH E=1e5 nu=0.4 rho=1000, h=0.01, delta=1e-3, CG tol "
+                        "1e-6, FP64 throughout; all 20 steps from rest, L2 flushed before each",
+            "steps": s.n_steps, "steps_per_s": allsum(ws, s.n_steps) / (allmax(ws, sum(ms)) / 1e3), "unit": "steps/s",
+            "p50_step_ms": round(p50, 3), "p99_step_ms": round(p99, 3),
+            "mean_outer_iters": statistics.mean(x["outer_iters"] for x in stats),
+            "max_contacts": max(x["n_contacts"] for x in stats), "_x": np.array(xs), "_diag": s.bbox_diag()}
+
+
 def run_variant(args, seed, ws, B, scenes, stream, flush, workload, K, W, **params):
     """The eight-cube scene with modified parameters (friction, material),
     mixed precision: W warm-up steps, then each step timed with CUDA events
@@ -763,6 +837,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=30.0,
                     help="oracle budget on the spiky-ball scene (at least one whole step is always timed)")
+    ap.add_argument("--cpu-batch-scenes", type=int, default=64,
+                    help="batched scenes the oracle runs one per host core for the batched line's CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--large-start", type=int, default=-1,
@@ -770,6 +846,7 @@ def main():
                          "compression)")
     ap.add_argument("--large-reuse", type=int, default=0, help="headline with the CCD-reuse option")
     ap.add_argument("--eight-cubes", type=int, default=1, help="the eight-cube line (0: skip)")
+    ap.add_argument("--two-cubes", type=int, default=1, help="the two-cube FP64 line (0: skip)")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="independent scenes of 1k-20k tets for the batched line, split over the ranks (0: skip)")
     ap.add_argument("--batch-workers", type=int, default=16)
@@ -789,7 +866,7 @@ def main():
     ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_leg:
-        return oracle_leg(args.oracle_leg, args.cpu_seconds)
+        return oracle_leg(args.oracle_leg, args.cpu_seconds, args.cpu_batch_scenes)
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
@@ -797,7 +874,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     leg = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:  # before any CUDA call
-        leg = start_oracle_leg(args.cpu_seconds)
+        leg = start_oracle_leg(args.cpu_seconds, args.cpu_batch_scenes)
 
     ws, rank, local = dist_init(args)
     import torch
@@ -818,6 +895,9 @@ def main():
     lo, hi = L["window"]
     _progress(f"large: {L['value']:.3f} steps/s over steps {lo}..{hi - 1}; whole schedule "
               f"{L['schedule']['steps_per_s']:.3f} steps/s")
+
+    # ---- the two-cube scene, FP64 (the small configuration) --------------------
+    T = run_two(torch, B, scenes, stream, flush, ws) if args.two_cubes else None
 
     # ---- the eight-cube scene ------------------------------------------------
     E = run_eight(args, torch, B, scenes, stream, flush, ws, peak, peak_kind, rank) if args.eight_cubes else None
@@ -878,6 +958,7 @@ def main():
     leg_res = {}
     if leg is not None:
         proc, prefix = leg
+        open(prefix + "_go", "w").close()
         leg_res = finish_oracle_leg(proc, timeout=900)
     cpu = large_err = None
     eight_cpu = eight_err = None
@@ -893,6 +974,23 @@ def main():
             large_err = float(np.abs(L["x_first"] - xo).max() / L["diag"])
         except OSError:
             pass
+    if T:
+        T["cpu_baseline"] = None
+        if "two" in leg_res:
+            r = leg_res["two"]
+            T["cpu_baseline"] = {"value": r["value"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"the same 20 steps from rest ({r['seconds']:.2f} s, single-threaded FP64 "
+                                           "C oracle)"}
+            try:
+                xo = np.load(prefix + "_two.npy")
+                err = [float(np.abs(T["_x"][i] - xo[i]).max() / T["_diag"]) for i in range(len(xo))]
+                T["error_vs_fp64_oracle"] = {"free_running_per_step": [float("%.3g" % e) for e in err],
+                                             "max": max(err), "bound": 1e-6,
+                                             "note": "max |x_gpu - x_oracle| / bbox diagonal after each step, "
+                                                     "both from rest"}
+            except OSError:
+                pass
+        del T["_x"], T["_diag"]
     if "eight" in leg_res and E:
         r = leg_res["eight"]
         eight_cpu = {"value": r["value"], "unit": "steps/s", "cores": 1, "kind": "oracle",
@@ -957,7 +1055,16 @@ def main():
                                            "contact); the bound is 1e-4"},
                 "pcg_autotune": {"best_mode": E["tuned"][0],
                                  "us_per_iteration_by_mode": {str(k): round(v, 3) for k, v in E["tuned"][1].items()}}}
+        if T:
+            line["two_cubes_fp64"] = T
         if batched:
+            if "batched" in leg_res:
+                r = leg_res["batched"]
+                batched["cpu_baseline"] = {
+                    "value": r["value"], "unit": "steps/s", "cores": r["cores"], "kind": "oracle",
+                    "sample": f"the first {r['scenes']} scenes of the list, 10 steps each, one scene per host core "
+                              f"({r['seconds']:.1f} s; spawned single-threaded FP64 C oracle processes, run after the "
+                              "GPU lines)"}
             line["batched"] = dict(
                 batched, workload=f"{args.batched_scenes} independent scenes (seeded; split over the ranks by size): "
                 "1k-20k tets log-uniform, one cube or a stack of two on a ground quad, E log-uniform 1e4-1e6 Pa, "
