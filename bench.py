@@ -238,11 +238,13 @@ def schedule(s, scenes):
 # the oracle on the host cores: the CPU baseline and the reference values of
 # the error against FP64 (the only part of this file that runs oracle/)
 # ---------------------------------------------------------------------------
-def _oracle_batch_scene(i):
-    """one batched scene, 10 steps, in a worker process of the all-core leg"""
+def _oracle_batch_scene(arg):
+    """one batched scene (a seed, or the (seed, t_lo, t_hi) of a served
+    request), 10 steps, in a worker process of the all-core leg"""
     import oracle as O
     from paper_2512_12151_b300 import scenes
-    o = O.Oracle(scenes.batch_scene(i))
+    s = scenes.batch_scene(arg) if isinstance(arg, int) else scenes.batch_scene(*arg)
+    o = O.Oracle(s)
     t0 = time.perf_counter()
     status, _ = o.step(10)
     return 10, time.perf_counter() - t0, status
@@ -320,6 +322,17 @@ def oracle_leg(prefix, seconds, batch_scenes=0):
         el = time.perf_counter() - t0
         out["batched"] = {"value": sum(r[0] for r in res) / el, "seconds": el, "scenes": batch_scenes,
                           "cores": cores, "failed": sum(1 for r in res if r[2] != 0)}
+        print(json.dumps(out), flush=True)
+        # the served stream's first requests (the same list as the GPU's
+        # served line, rank 0's seed), one per core
+        from paper_2512_12151_b300 import serving
+        reqs = serving.poisson_requests(cores, 200.0, seed=1000)
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_batch_scene, [(r[1], r[2], r[3]) for r in reqs], chunksize=1)
+        el = time.perf_counter() - t0
+        out["served"] = {"value": sum(r[0] for r in res) / el, "seconds": el, "requests": len(reqs),
+                         "cores": cores, "failed": sum(1 for r in res if r[2] != 0)}
         print(json.dumps(out), flush=True)
     return 0
 
@@ -1078,6 +1091,13 @@ def main():
                                                     "on one stream", unit="steps/s")
             line["batched_vs_plain_fp64"] = batched["steps_per_s"] / plain["steps_per_s"]
         if served:
+            if "served" in leg_res:
+                r = leg_res["served"]
+                served["cpu_baseline"] = {
+                    "value": r["value"], "unit": "steps/s", "cores": r["cores"], "kind": "oracle",
+                    "sample": f"the first {r['requests']} requests of the list, 10 steps each, one scene per host "
+                              f"core ({r['seconds']:.1f} s, until the largest finished; spawned single-threaded "
+                              "FP64 C oracle processes, run after the GPU lines, no arrival waits)"}
             line["serving"] = dict(
                 served, workload=f"{args.serve_requests} requests per GPU, Poisson arrivals at {args.serve_rate:g}/s, "
                 "scenes 2k-200k tets log-uniform (same generator), 10 steps each, mixed precision, HBM budget "

@@ -759,7 +759,6 @@ static int create(Scene &S, const bf_mesh_desc *m, const bf_params *prm)
         BF_ALLOC(S.cg_qf, float, n3);
         BF_ALLOC(S.cg_zf, float, n3);
         BF_ALLOC(S.cg_pf2, float, n3);
-        BF_ALLOC(S.cg_qcf, float, n3);
     } else {
         BF_ALLOC(S.pinv, double, 9 * (size_t)nv);
     }

@@ -108,7 +108,7 @@ struct Scene {
     // PCG work vectors (n = 3 nv)
     double *cg_x = nullptr, *cg_r = nullptr, *cg_b = nullptr, *cg_p = nullptr, *cg_q = nullptr,
            *cg_z = nullptr, *pdir = nullptr;
-    float *cg_pf = nullptr, *cg_qf = nullptr, *cg_zf = nullptr, *cg_pf2 = nullptr, *cg_qcf = nullptr;
+    float *cg_pf = nullptr, *cg_qf = nullptr, *cg_zf = nullptr, *cg_pf2 = nullptr;
     double *cg_qc = nullptr;  // contact part of H p (accumulated with atomics)
     double *cg_p2 = nullptr;  // second direction buffer of the persistent PCG
     unsigned *bar = nullptr;  // grid barrier: count, generation

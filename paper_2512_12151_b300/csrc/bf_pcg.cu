@@ -81,7 +81,7 @@ struct PcgArgs {
     const void *pinv;
     const double *b;
     double *x;
-    void *z, *p0, *p1, *qc;  // qc: unused by the persistent kernels (contact parts go to qd)
+    void *z, *p0, *p1;
     double *qd;               // FP64 contact part of H x (reliable updates)
     double *res;
     unsigned *bar;
@@ -1773,7 +1773,7 @@ static void release_pcg_slots(Scene &S)
 }
 
 template <class MT, class VT>
-static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *p1, VT *qc, VT *z, const double *b,
+static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *p1, VT *z, const double *b,
                            double *x, double tol, int maxit, int *iters, bool defer)
 {
     if (S.pcg_grid == 0) {
@@ -1804,7 +1804,6 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.z = z;
     A.p0 = p0;
     A.p1 = p1;
-    A.qc = qc;
     A.qd = S.cg_qc;  // FP64 contact part of H p, and of H x in the reliable updates
     A.res = S.dscal + S_RES;
     A.bar = S.bar;
@@ -1899,10 +1898,10 @@ static int persistent_entry(Scene &S, const double *b, double *x, double tol, in
 {
     int st;
     if (S.prm.precision == BF_PREC_MIXED)
-        st = persistent_impl<float, float>(S, S.valf, S.pinvf, S.cg_pf, S.cg_pf2, S.cg_qcf, S.cg_zf, b, x, tol, maxit,
+        st = persistent_impl<float, float>(S, S.valf, S.pinvf, S.cg_pf, S.cg_pf2, S.cg_zf, b, x, tol, maxit,
                                            iters, defer);
     else
-        st = persistent_impl<double, double>(S, S.val, S.pinv, S.cg_p, S.cg_p2, S.cg_qc, S.cg_z, b, x, tol, maxit,
+        st = persistent_impl<double, double>(S, S.val, S.pinv, S.cg_p, S.cg_p2, S.cg_z, b, x, tol, maxit,
                                              iters, defer);
     if (st == BF_E_CAPACITY && S.pcg_grid == 0) {
         S.pcg_mode = 0;

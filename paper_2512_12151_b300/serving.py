@@ -168,6 +168,7 @@ def rate_sweep(rates, n_requests, n_steps=10, n_workers=16, seed=0, **kw):
     for r in rates:
         res = serve(poisson_requests(n_requests, r, seed=seed), n_steps=n_steps, n_workers=n_workers, **kw)
         runs.append({"rate_per_s": r, "steps_per_s": res["steps_per_s"],
+                     "p50_step_ms": res["p50_step_ms"], "p99_step_ms": res["p99_step_ms"],
                      "admission_wait_p50_ms": res["admission_wait_p50_ms"],
                      "admission_wait_p99_ms": res["admission_wait_p99_ms"],
                      "bounded": res["admission_wait_bounded"], "failed": res["failed"]})
