@@ -590,11 +590,16 @@ def run_large(args, torch, B, scenes, stream, ws, peak, peak_kind):
     sim.close()
     allms = [sched[i]["ms"] for i in sorted(sched)]
     sp50, sp99 = _pcts(allms)
+    first = [sched[i]["ms"] for i in range(min(20, N)) if i in sched]
+    f50, f99 = _pcts(first)
     whole = {"steps": len(allms), "steps_per_s": len(allms) / (sum(allms) / 1e3), "p50_step_ms": round(sp50, 3),
              "p99_step_ms": round(sp99, 3), "max_contacts": max(sched[i]["n_contacts"] for i in sched),
              "mean_outer_iters": round(statistics.mean(sched[i]["outer_iters"] for i in sched), 2),
              "mean_cg_iters_per_step": round(statistics.mean(sched[i]["cg_iters"] for i in sched), 1),
              "failed_steps": sum(1 for i in sched if sched[i]["status"] != 0),
+             "first_20_steps": {"steps_per_s": len(first) / (sum(first) / 1e3), "p50_step_ms": round(f50, 3),
+                                "p99_step_ms": round(f99, 3),
+                                "max_contacts": max(sched[i]["n_contacts"] for i in range(len(first)))},
              "per_step": [[i, round(sched[i]["ms"], 1), sched[i]["outer_iters"], sched[i]["cg_iters"],
                            sched[i]["n_contacts"], round(scenes.plate_schedule_z(s, i), 4)] for i in sorted(sched)],
              "per_step_columns": ["step", "ms", "outer_iters", "cg_iters", "contacts", "plate_z_m"]}
