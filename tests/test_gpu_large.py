@@ -174,3 +174,40 @@ def test_large_subproblem_teacher_forced(torch_cuda):
     assert all(abs(Ao[k][0] - Ag[k][0]) <= 1e-3 * lmax for k in Ao)
     assert B.bf_max_step_size(sim.h, dev(torch, x), dev(torch, xh_o)) == o.max_step_size(x, xh_o)
     sim.close()
+
+
+def test_large_pcg_symmetric_matches_full_rows(torch_cuda, spiky):
+    """At full size the default PCG is the symmetric variant (upper blocks
+    streamed once, transposed products by vector reductions); on the
+    assembled Newton system of the compression it reaches the tolerance on
+    the library's own operator and agrees with the variant that streams
+    both triangles (bf_set_pcg_mode 97) and with the per-phase launches."""
+    torch = torch_cuda
+    s = spiky
+    sim = B.Sim(s)
+    x = s.x0
+    xd = dev(torch, x)
+    xt = torch.zeros_like(xd)
+    B.bf_xtilde(sim.h, xt)
+    B.bf_mu_init(sim.h, xt, xd)
+    B.bf_linearize(sim.h, xd)
+    G = torch.zeros_like(xd)
+    B.bf_assemble(sim.h, xt, xd, xd, G)
+    b = -G
+    sols, its = [], []
+    for mode in (1, 97, 0):
+        B.bf_set_pcg_mode(sim.h, mode)
+        p = torch.zeros_like(xd)
+        it, _ = B.bf_pcg(sim.h, b, p, 1e-6, 100000)
+        if mode == 1:
+            assert B.bf_get_pcg_config(sim.h)["resident"] == 3  # the symmetric variant
+        Hp = torch.zeros_like(xd)
+        B.bf_hess_apply(sim.h, p, Hp)
+        res = float(torch.linalg.norm(Hp - b) / torch.linalg.norm(b))
+        assert res <= 1e-4, (mode, res)
+        sols.append(host(p).reshape(-1))
+        its.append(it)
+    assert abs(its[0] - its[1]) <= max(2, its[1] // 20), its
+    for k in (0, 1):
+        assert np.linalg.norm(sols[k] - sols[2]) <= 1e-4 * np.linalg.norm(sols[2])
+    sim.close()
