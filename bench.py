@@ -610,6 +610,44 @@ def run_large(args, torch, B, scenes, stream, ws, peak, peak_kind):
             "nnzb": info["nnzb"]}
 
 
+def run_large_window(args, torch, B, scenes, stream, ws, **params):
+    """The headline scene with modified parameters (the CCD-reuse option):
+    the same window around peak compression, steps before it untimed, each
+    timed step with CUDA events; no replays and no release."""
+    s = scenes.spiky_balls(precision=1)
+    for k, v in params.items():
+        setattr(s.params, k, v)
+    P, N = schedule(s, scenes)
+    K, W = args.steps, args.warmup
+    S0 = args.large_start if args.large_start >= 0 else max(0, P - W - K // 2)
+    lo, hi = S0 + W, S0 + W + K
+    sim = B.Sim(s, stream=stream.cuda_stream)
+    for i in range(lo):
+        B.bf_set_obstacle_targets(sim.h, scenes.plate_targets_schedule(s, i))
+        sim.step(1)
+    if args.pcg_mode >= 0:
+        B.bf_set_pcg_mode(sim.h, args.pcg_mode)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    for k, i in enumerate(range(lo, hi)):
+        B.bf_set_obstacle_targets(sim.h, scenes.plate_targets_schedule(s, i))
+        ev[k][0].record(stream)
+        _, st = sim.step(1)
+        ev[k][1].record(stream)
+        stats.append(st[0])
+    torch.cuda.synchronize()
+    sim.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    p50, p99 = _pcts(ms)
+    return {"steps": K, "timed_steps": f"{lo}..{hi - 1}",
+            "steps_per_s": allsum(ws, K) / (allmax(ws, sum(ms)) / 1e3), "unit": "steps/s",
+            "p50_step_ms": round(p50, 3), "p99_step_ms": round(p99, 3),
+            "mean_outer_iters": statistics.mean(x["outer_iters"] for x in stats),
+            "mean_cg_iters_per_step": statistics.mean(x["cg_iters"] for x in stats),
+            "mean_contacts": statistics.mean(x["n_contacts"] for x in stats)}
+
+
 # ---------------------------------------------------------------------------
 # batched scenes over the ranks
 # ---------------------------------------------------------------------------
@@ -866,6 +904,8 @@ def main():
                     help="first warm-up step of the spiky-ball window (default: the window centred on peak "
                          "compression)")
     ap.add_argument("--large-reuse", type=int, default=0, help="headline with the CCD-reuse option")
+    ap.add_argument("--large-reuse-line", type=int, default=1,
+                    help="the headline window again with the CCD-reuse option, as an extra line (0: skip)")
     ap.add_argument("--eight-cubes", type=int, default=1, help="the eight-cube line (0: skip)")
     ap.add_argument("--two-cubes", type=int, default=1, help="the two-cube FP64 line (0: skip)")
     ap.add_argument("--batched-scenes", type=int, default=256,
@@ -916,6 +956,14 @@ def main():
     lo, hi = L["window"]
     _progress(f"large: {L['value']:.3f} steps/s over steps {lo}..{hi - 1}; whole schedule "
               f"{L['schedule']['steps_per_s']:.3f} steps/s")
+
+    # ---- the headline scene with the CCD-reuse option ------------------------
+    LR = None
+    if args.large_reuse_line:
+        LR = run_large_window(args, torch, B, scenes, stream, ws, ccd_reuse=1)
+        LR["workload"] = ("the spiky-ball compression with the CCD-reuse option (one CCD per outer iteration serves "
+                          "UpdateActiveSet and MaxStepSize), the same window, mixed precision")
+        _progress(f"large with CCD reuse: {LR['steps_per_s']:.3f} steps/s")
 
     # ---- the two-cube scene, FP64 (the small configuration) --------------------
     T = run_two(torch, B, scenes, stream, flush, ws) if args.two_cubes else None
@@ -1076,6 +1124,8 @@ def main():
                                            "contact); the bound is 1e-4"},
                 "pcg_autotune": {"best_mode": E["tuned"][0],
                                  "us_per_iteration_by_mode": {str(k): round(v, 3) for k, v in E["tuned"][1].items()}}}
+        if LR:
+            line["large_ccd_reuse"] = LR
         if T:
             line["two_cubes_fp64"] = T
         if batched:
