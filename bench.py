@@ -1073,6 +1073,9 @@ def main():
         except OSError:
             pass
 
+    if leg is not None:  # the leg's files are read: remove its temporary directory
+        import shutil
+        shutil.rmtree(os.path.dirname(leg[1]), ignore_errors=True)
     if rank == 0:
         stats = L["stats"]
         line = {"metric": METRIC, "value": L["value"], "unit": "steps/s", "n_gpus": ws, "steps": K, "warmup": W,
