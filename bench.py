@@ -747,6 +747,7 @@ def run_eight(args, torch, B, scenes, stream, flush, ws, peak, peak_kind, seed):
     stats = []
     torch.cuda.synchronize()
     barrier(ws)
+    torch.cuda.nvtx.range_push("eight_cubes_window")
     for i in range(K):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -755,6 +756,7 @@ def run_eight(args, torch, B, scenes, stream, flush, ws, peak, peak_kind, seed):
         ev[i][1].record(stream)
         stats.append(st[0])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     sim.close()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = allmax(ws, sum(step_ms))
