@@ -369,8 +369,10 @@ def test_empty_and_edge_cases(torch_cuda):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, precision):
-    """The persistent cooperative PCG and the one-launch-per-phase PCG run
-    the same recurrences; both solve the oracle's system to the tolerance
+    """The persistent cooperative PCG (resident, streamed, and the two
+    global-memory variants: in mixed precision the symmetric one under mode
+    33 and the full-row one under 97) and the one-launch-per-phase PCG run
+    the same recurrences; all solve the oracle's system to the tolerance
     (mixed precision: FP32 matrix, so the FP64 residual is looser)."""
     torch = torch_cuda
     s, x, v, keys, lam, gam = contact_state
@@ -386,18 +388,22 @@ def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, pr
     b = -G_o
     H = o.hess_dense()
     sols, its = [], []
-    for mode in (1, 17, 33, 0):  # resident, streamed, global vectors, per-phase launches
+    modes = (1, 17, 33, 97, 0)  # resident, streamed, global (symmetric in mixed), full-row global, per-phase
+    for mode in modes:
         B.bf_set_pcg_mode(sim.h, mode)
         xg = torch.zeros_like(G_g)
         it, _ = B.bf_pcg(sim.h, dev(torch, b), xg, 1e-6, 100000)
+        if mode in (33, 97):
+            assert B.bf_get_pcg_config(sim.h)["resident"] == (3 if precision and mode == 33 else 2)
         sols.append(host(xg).reshape(-1))
         its.append(it)
     bar = 1e-6 * 1.01 if precision == 0 else 1e-4
     for p in sols:
         assert np.linalg.norm(H @ p - b.reshape(-1)) <= bar * np.linalg.norm(b)
-    for k in range(3):
-        assert abs(its[k] - its[3]) <= max(2, its[3] // 20)
-        assert np.linalg.norm(sols[k] - sols[3]) <= 1e-4 * np.linalg.norm(sols[3])
+    last = len(modes) - 1
+    for k in range(last):
+        assert abs(its[k] - its[last]) <= max(2, its[last] // 20)
+        assert np.linalg.norm(sols[k] - sols[last]) <= 1e-4 * np.linalg.norm(sols[last])
     sim.close()
 
 
