@@ -56,8 +56,9 @@ extern "C" {
 #define BF_E_BUDGET (-11)      /* batch admission refused: the HBM budget would be exceeded */
 
 #define BF_PREC_FP64 0  /* everything FP64 */
-#define BF_PREC_MIXED 1 /* FP32 Hessian blocks / SpMV / preconditioner; FP64 gradient,
-                           dots, residuals, energies, CCD, TOI and multipliers */
+#define BF_PREC_MIXED 1 /* FP32 Hessian blocks (summed in FP64, stored in FP32) / SpMV /
+                           preconditioner; FP64 gradient, dots, residuals, energies, CCD,
+                           TOI and multipliers */
 
 typedef struct bf_scene bf_scene;
 
