@@ -343,31 +343,38 @@ int bf_max_step_size_pairs_noalloc(int32_t type, int32_t n, const double *x0, co
 int bf_enable_timers(bf_scene *scene, int32_t on);
 /* PCG execution.  0 = three launches per iteration with the scalar
  * recurrences kept on the device.  1..4 = one persistent cooperative launch
- * per solve with two grid-wide reductions per iteration and up to `mode`
- * CTAs per SM (default 1), keeping the matrix in shared memory when it
- * fits, else streaming it, with the per-row vectors in global memory when
- * they do not fit in shared memory either; adding 16 forbids the
- * shared-memory copy of the matrix; adding 32 forces a global-memory
+ * per solve with up to `mode` CTAs per SM (default 1), keeping the matrix
+ * in shared memory when it fits, else streaming it, with the per-row
+ * vectors in global memory when they do not fit in shared memory either.
+ * With the matrix in shared memory the iteration is the single-reduction
+ * recurrence of Chronopoulos and Gear (one grid-wide reduction per
+ * iteration); adding 128 selects the two-reduction form there.  The
+ * streamed variants use two reductions per iteration.  Adding 16 forbids
+ * the shared-memory copy of the matrix; adding 32 forces a global-memory
  * variant: in mixed precision the symmetric one (upper blocks streamed
  * once, transposed products by vector reductions into global memory),
  * else, or with 64 added, the one that streams both triangles.  The same
- * method in every mode; the order of floating-point sums differs. */
+ * Krylov method in every mode (the same iterates in exact arithmetic); the
+ * order of floating-point sums differs. */
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
 
 /* Configuration of the persistent PCG chosen at the scene's first solve
  * (host int32[8]): mode, CTAs, threads per CTA, shared memory bytes per
  * CTA, variant (0: blocks streamed through the BSR map, vectors in shared
- * memory; 1: blocks resident in shared memory; 2: blocks streamed from a
- * jagged global copy, per-row vectors in global memory; 3: upper blocks
- * streamed from a jagged global copy, transposed products reduced in global
- * memory), max rows, max blocks and max window vertices per CTA (zeros
- * before the first solve). */
+ * memory; 1: blocks resident in shared memory, two reductions per
+ * iteration; 2: blocks streamed from a jagged global copy, per-row vectors
+ * in global memory; 3: upper blocks streamed from a jagged global copy,
+ * transposed products reduced in global memory; 4: blocks resident in
+ * shared memory, one reduction per iteration), max rows, max blocks and max
+ * window vertices per CTA (zeros before the first solve). */
 int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
 
 /* PCG autotuner: on the system assembled last (bf_step or bf_assemble must
  * have run), times `iters` (>= 8) PCG iterations of each execution
- * configuration (bf_set_pcg_mode 1, 2, 17, 18, 33, 34, 97, 98 and 0; a persistent
- * configuration that does not fit is skipped) with CUDA events on the
+ * configuration (bf_set_pcg_mode 1, 2, 129, 130, 17, 18, 33, 34, 97, 98 and
+ * 0; a persistent configuration that does not fit is skipped, and so are 129
+ * and 130 where the matrix is not resident, as they then equal 1 and 2) with
+ * CUDA events on the
  * scene's stream, then sets the fastest per iteration (a configuration later
  * in that list replaces the choice so far only when it is more than 2 %
  * faster, so timing noise does not flip it).  modes / us_per_iter

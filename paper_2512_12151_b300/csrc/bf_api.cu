@@ -1417,13 +1417,14 @@ int bf_enable_timers(bf_scene *scene, int32_t on)
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
 {
     SCENE_OR_ARG(scene);
-    if (mode < 0 || mode > 127) return BF_E_ARG;
+    if (mode < 0 || mode > 255) return BF_E_ARG;
     S.pcg_mode = mode == 0 ? 0 : 1;
     if (mode > 0) {
         S.pcg_ctas_per_sm = mode & 15;
         S.pcg_allow_resident = (mode & 16) ? 0 : 1;
         S.pcg_force_global = (mode & 32) ? 1 : 0;
         S.pcg_no_sym = (mode & 64) ? 1 : 0;
+        S.pcg_cg1 = (mode & 128) ? 0 : 1;
         S.pcg_grid = 0;  // recomputed at the next solve
     }
     return BF_OK;
@@ -1443,11 +1444,11 @@ int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes,
 {
     SCENE_OR_ARG(scene);
     if (iters < 8 || cap < 0 || (cap > 0 && (!modes || !us_per_iter)) || !best || S.nv < 1) return BF_E_ARG;
-    static const int kCand[] = {1, 2, 17, 18, 33, 34, 97, 98, 0};
+    static const int kCand[] = {1, 2, 129, 130, 17, 18, 33, 34, 97, 98, 0};
     const int n = 3 * S.nv;
     const int keep_mode = S.pcg_mode == 0 ? 0
                           : (S.pcg_ctas_per_sm | (S.pcg_allow_resident ? 0 : 16) | (S.pcg_force_global ? 32 : 0) |
-                             (S.pcg_no_sym ? 64 : 0));
+                             (S.pcg_no_sym ? 64 : 0) | (S.pcg_cg1 ? 0 : 128));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -1465,6 +1466,7 @@ int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes,
         if (st && st != BF_E_CG_MAXIT) break;
         st = BF_OK;
         if (mode != 0 && S.pcg_mode == 0) continue;  // did not fit: fell back to the per-phase launches
+        if ((mode & 128) && S.pcg_resident != 1) continue;  // not resident: the same as mode & 127
         cudaEventRecord(e0, S.stream);
         int st2 = run_pcg(S, S.cg_b, S.pdir, 1e-30, iters, &it);
         cudaEventRecord(e1, S.stream);

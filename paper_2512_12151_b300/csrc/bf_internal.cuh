@@ -98,7 +98,8 @@ struct Scene {
     std::vector<int> h_frowptr;
     int *part = nullptr;      // persistent PCG: CTA row ranges (grid + 1)
     int pcg_smem = 0;         // dynamic shared memory of the persistent PCG (bytes)
-    int pcg_resident = 0;     // persistent PCG variant: 0 streamed via the BSR, 1 resident, 2 global vectors, 3 symmetric
+    int pcg_resident = 0;     // persistent PCG variant: 0 streamed via the BSR, 1 resident, 2 global vectors, 3 symmetric,
+                              // 4 resident with one reduction per iteration
     double *val = nullptr;  // 9 planes FP64
     float *valf = nullptr;  // 9 planes FP32 (mixed)
     double *grad = nullptr;
@@ -129,6 +130,8 @@ struct Scene {
     size_t pcg_gvec_stride = 0;
     int pcg_kc = 0;               // persistent PCG: contacts per CTA cached in shared memory
     int pcg_no_sym = 0;           // persistent PCG: skip the symmetric (upper-only) variant
+    int pcg_cg1 = 1;              // persistent PCG: single-reduction recurrence when the blocks are resident
+    unsigned char *pcg_cg1buf = nullptr;  // ... its published row sums, contact parts, (r, s) and H x
     int *pcg_uedst = nullptr;             // symmetric variant: jagged position of each upper block
     unsigned short *pcg_unbr = nullptr;   // ... window offset of each jagged slot
     float *pcg_uval = nullptr;            // ... jagged copy of the upper blocks (9 planes, FP32)

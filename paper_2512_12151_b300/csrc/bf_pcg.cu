@@ -95,16 +95,36 @@ struct PcgArgs {
     // products and contact terms
     const void *uval;
     float4 *yq;
+    // single-reduction variant: published row sums, FP64 contact parts,
+    // owners' (r, s), FP64 H x of the reliable updates
+    void *cwq, *crs, *cpp;
+    double *cqc, *chx;
+    unsigned char *cfl;
 };
 
 enum { PCG_RUN = 0, PCG_DONE, PCG_MAXIT, PCG_BAD, PCG_FOLD, PCG_ABORT };
 
 // scalar state of the recurrence, maintained by thread 0 of each CTA
+// (rr_done = tol^2 |b|^2 and rr_fold, the |r|^2 of the next reliable update,
+// are formed once, not in every reduction)
 struct PcgCtl {
-    double alpha, beta, rz, rz_old, rr, rr_ref, bb;
+    double alpha, beta, rz, rz_old, rr, rr_done, rr_fold, bb;
     float al, bt;
     int it, folds, state;
 };
+
+// num / den rounded to FP32, for the scalars that only reach FP32 vector
+// updates: an FP32 division of the rounded operands when both lie within
+// [2^-100, 2^100] in magnitude (short: this GPU's FP64 pipe is narrow and
+// an FP64 division sits on the path through every grid-wide reduction),
+// else the FP64 quotient rounded.  Every CTA computes the same bits.
+__device__ __forceinline__ float div_to_f32(double num, double den)
+{
+    const int en = (__double2hiint(num) >> 20) & 0x7ff, ed = (__double2hiint(den) >> 20) & 0x7ff;
+    if (en > 923 && en < 1123 && ed > 923 && ed < 1123)
+        return __fdiv_rn(__double2float_rn(num), __double2float_rn(den));
+    return __double2float_rn(num / den);
+}
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 {
@@ -319,8 +339,10 @@ struct PcgLayout {
 // streamed from a jagged copy in global memory (coalesced), per-row vectors
 // in global memory (systems whose rows do not fit in shared memory); 3 =
 // upper blocks only streamed from a jagged copy, transposed products
-// accumulated in global memory (mixed precision; k_pcg_sym below).
-enum { PCG_STREAM = 0, PCG_RESIDENT = 1, PCG_GLOBAL = 2, PCG_SYM = 3 };
+// accumulated in global memory (mixed precision; k_pcg_sym below); 4 =
+// blocks resident in shared memory, one grid-wide reduction per iteration
+// (k_pcg_cg1 below).
+enum { PCG_STREAM = 0, PCG_RESIDENT = 1, PCG_GLOBAL = 2, PCG_SYM = 3, PCG_CG1 = 4 };
 
 __host__ __device__ inline PcgLayout pcg_layout(bool mixed, int ct, int mt, int max_rows, int max_win, int max_ent,
                                                 int max_len, int mode, int kc)
@@ -531,7 +553,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             ctl.rz = t[0];
             ctl.bb = t[1];
             ctl.rr = t[1];
-            ctl.rr_ref = t[1];
+            ctl.rr_done = A.tol2 * t[1];
+            ctl.rr_fold = 0.01 * t[1];
             ctl.beta = 0.0;
             ctl.bt = 0.f;
             ctl.it = 0;
@@ -653,6 +676,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                     // no curvature left along p: stop with the current x, as the
                     // per-phase solver does, and let the line search judge it
                     ctl.state = PCG_DONE;
+                } else if (mixed) {
+                    ctl.al = div_to_f32(ctl.rz, pq);
+                    ctl.alpha = (double)ctl.al;
                 } else {
                     ctl.alpha = ctl.rz / pq;
                     ctl.al = (float)ctl.alpha;
@@ -698,16 +724,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             reduce(acc, [&](const double *t) {
                 ++ctl.it;
                 ctl.rz_old = ctl.rz;
-                ctl.beta = t[0] / ctl.rz_old;
-                ctl.bt = (float)ctl.beta;
+                if (mixed) {
+                    ctl.bt = div_to_f32(t[0], ctl.rz_old);
+                    ctl.beta = (double)ctl.bt;
+                } else {
+                    ctl.beta = t[0] / ctl.rz_old;
+                    ctl.bt = (float)ctl.beta;
+                }
                 ctl.rz = t[0];
                 ctl.rr = t[1];
                 if (!isfinite(t[0]) || !isfinite(t[1])) {
                     ctl.state = PCG_BAD;
                     return;
                 }
-                const bool done = ctl.rr <= A.tol2 * ctl.bb;
-                if (mixed && ctl.folds < A.max_replace && (done || ctl.rr <= 0.01 * ctl.rr_ref))
+                const bool done = ctl.rr <= ctl.rr_done;
+                if (mixed && ctl.folds < A.max_replace && (done || ctl.rr <= ctl.rr_fold))
                     ctl.state = PCG_FOLD;
                 else if (done)
                     ctl.state = PCG_DONE;
@@ -787,13 +818,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             }
             reduce(acc, [&](const double *t) {
                 ++ctl.folds;
-                ctl.beta = t[0] / ctl.rz_old;
-                ctl.bt = (float)ctl.beta;
+                ctl.bt = div_to_f32(t[0], ctl.rz_old);
+                ctl.beta = (double)ctl.bt;
                 ctl.rz = t[0];
                 ctl.rr = t[1];
-                ctl.rr_ref = t[1];
+                ctl.rr_fold = 0.01 * t[1];
                 if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
-                else if (ctl.rr <= A.tol2 * ctl.bb) ctl.state = PCG_DONE;
+                else if (ctl.rr <= ctl.rr_done) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
                 else ctl.state = PCG_RUN;
             });
@@ -819,6 +850,705 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
         A.dscal[S_T_STAGE] = 1e-6 * (double)tS;
         A.dscal[S_T_ROWS] = 1e-6 * (double)tR;
         A.dscal[S_T_CONTACT] = 1e-6 * (double)tC;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-reduction variant of the resident PCG: the recurrence of Chronopoulos
+// and Gear ("s-step iterative methods for symmetric linear systems", J.
+// Comput. Appl. Math. 25, 1989), which gives the iterates of the
+// two-reduction form in exact arithmetic with one grid-wide reduction per
+// iteration.  Iteration k:
+//   u = P r, w = H u; gamma = r.u, delta = u.w, |r|^2   (one reduction)
+//   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+//   p = u + beta p, s = w + beta s (s = H p by recurrence), x += alpha p,
+//   r -= alpha s.
+// The product needs u on the CTA's whole vertex window, so every CTA runs the
+// recurrences of s and r, and u = P r, on its window itself: the same
+// operations (explicitly rounded, no contraction left to the compiler) on the
+// same bits give every CTA bit-identical copies of the values the owner of a
+// row holds.  What crosses CTAs is only w: each owner publishes the full-row
+// sums of its rows (double-buffered by iteration parity) and the contact
+// pairs add their part in FP64 (triple-buffered: written in iteration k, read
+// after the reduction of k, cleared by the owners in k + 2).  The vertices of
+// a CTA's contact pairs may lie outside its window: there it takes r and s of
+// the previous iteration from the owners' published copy (double-buffered)
+// and applies the same update.  Blocks stay in shared memory as in the
+// resident variant, and so does the upper triangle of P over the window (P
+// is the inverse of a symmetric block; every CTA applies the same symmetric
+// form).  The row sums and contact parts are read from component planes in
+// global memory (L2), so a warp's loads are coalesced, the contact part only
+// at the vertices of a pair (flagged per vertex at the start of the solve).
+//
+// Mixed precision: s, r, u, p and the increment of x in FP32, dot products
+// compensated (AccF) and summed across CTAs in FP64, x in FP64.  Reliable
+// updates as in the two-reduction form (|r| down 10x, or convergence): x is
+// folded, r = b - H x is recomputed with FP64 vectors, and the product of the
+// same iteration is redone from the new r; the recurrences of s and p carry
+// on.
+// ---------------------------------------------------------------------------
+struct PcgCg1Layout {
+    size_t x, xl, pd, wq, u4, sw, rw, pw, val, nbr, rinfo, lvl, cg, cu, cw, cv, cm, fl, total;
+};
+
+__host__ __device__ inline PcgCg1Layout pcg_cg1_layout(bool mixed, int ct, int mt, int max_rows, int max_win,
+                                                       int max_ent, int max_len, int kc)
+{
+    PcgCg1Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    L.x = take(3 * (size_t)max_rows * 8);
+    L.xl = take(mixed ? 3 * (size_t)max_rows * ct : 0);
+    L.pd = take(3 * (size_t)max_rows * ct);
+    L.wq = take(3 * (size_t)max_rows * ct);
+    L.u4 = take(4 * (size_t)max_win * ct);
+    L.sw = take(3 * (size_t)max_win * ct);
+    L.rw = take(3 * (size_t)max_win * ct);
+    L.pw = take(6 * (size_t)max_win * ct);
+    L.val = take(9 * (size_t)max_ent * mt);
+    L.nbr = take((size_t)max_ent * 2);
+    L.rinfo = take((size_t)max_rows * 4);
+    L.lvl = take(((size_t)max_len + 1) * 4);
+    L.cg = take(12 * (size_t)kc * ct);
+    L.cu = take(12 * (size_t)kc * ct);
+    L.cw = take((size_t)kc * ct);
+    L.cv = take((size_t)kc * 16);
+    L.cm = take((size_t)kc * 4);
+    L.fl = take((size_t)max_win);
+    L.total = o;
+    return L;
+}
+
+// Global buffers of the single-reduction variant, in this order (byte
+// offsets as multiples of nv): row sums w (2 parities x 3 planes, 6 ct),
+// FP64 contact parts (3 buffers x 3 planes, 72), the owners' (r, s) (2
+// parities, 8 values per vertex, 16 ct), FP64 H x of the reliable updates
+// (24), the upper triangle of P (6 planes, 6 ct), a byte per vertex that
+// flags the vertices of contact pairs (zero between solves).
+struct PcgCg1Buf {
+    size_t wq, qc, rs, hx, pp, fl, total;
+};
+
+inline PcgCg1Buf pcg_cg1_buf(int nv_, int ct)
+{
+    const size_t nv = (size_t)nv_;
+    PcgCg1Buf B;
+    B.wq = 0;
+    B.qc = B.wq + 6 * nv * ct;
+    B.rs = B.qc + 72 * nv;
+    B.hx = B.rs + 16 * nv * ct;
+    B.pp = B.hx + 24 * nv;
+    B.fl = B.pp + 6 * nv * ct;
+    B.total = B.fl + ((nv + 15) & ~(size_t)15);
+    return B;
+}
+
+// scalar state of the single-reduction recurrence (thread 0 of each CTA;
+// the reciprocals of gamma_old and alpha_old are formed by another thread
+// during the product, off the path through the reduction: an FP64 division
+// is long on this GPU, whose FP64 pipe is narrow)
+struct PcgCg1Ctl {
+    double alpha, beta, gam_old, alp_old, inv_gam_old, inv_alp_old, rr, rr_done, rr_fold, bb;
+    float al, bt;
+    int it, folds, state, skip;
+};
+
+// explicitly rounded operations, so that every CTA computes the window
+// recurrences to the same bits whatever code the compiler emits around them
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float to_ct(double v, float) { return __double2float_rn(v); }
+__device__ __forceinline__ double to_ct(double v, double) { return v; }
+
+// u = P r for one vertex, P symmetric given by its upper triangle
+// (p00, p01, p02, p11, p12, p22)
+template <class CT>
+__device__ __forceinline__ void prec3(const CT (&P)[6], const CT (&r)[3], CT (&u)[3])
+{
+    u[0] = fma_rn(P[2], r[2], fma_rn(P[1], r[1], mul_rn(P[0], r[0])));
+    u[1] = fma_rn(P[4], r[2], fma_rn(P[3], r[1], mul_rn(P[1], r[0])));
+    u[2] = fma_rn(P[5], r[2], fma_rn(P[4], r[1], mul_rn(P[2], r[0])));
+}
+
+// row-major index of upper-triangle entry i of a 3x3 block: 0, 1, 2, 4, 5, 8
+__host__ __device__ constexpr int upper3(int i) { return i < 3 ? i : (i < 5 ? i + 1 : 8); }
+
+template <class MT, class VT>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
+{
+    using CT = typename std::conditional<(sizeof(MT) >= sizeof(VT)), MT, VT>::type;
+    constexpr bool mixed = sizeof(VT) == 4;
+    using Acc = typename std::conditional<mixed, AccF, double>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PcgCg1Ctl ctl;
+    __shared__ float2 red_f[3 * kPcgMaxWarps];
+    __shared__ double red_d[mixed ? 1 : 3 * kPcgThreads];
+    __shared__ double red_q4[12];
+    __shared__ unsigned long long tm[8];  // A, A2, -, -, t0, S, R, C
+    const MT *__restrict__ gval = (const MT *)A.val;
+    const MT *__restrict__ gpinv = (const MT *)A.pinv;
+    const int c = blockIdx.x;
+    const int r0 = A.part[c], r1 = A.part[c + 1], nr = r1 - r0;
+    const int wlo = A.win[2 * c], whi = A.win[2 * c + 1], nwin = whi - wlo;
+    const int E0 = A.frowptr[r0], ne = A.frowptr[r1] - E0;
+    const int nco = A.nc > c ? (A.nc - c + (int)gridDim.x - 1) / (int)gridDim.x : 0;  // pairs c + k grid
+    const int ncached = min(nco, A.kc);
+    const PcgCg1Layout L =
+        pcg_cg1_layout(mixed, sizeof(CT), sizeof(MT), A.max_rows, A.max_win, A.max_ent, A.max_len, A.kc);
+    const int ld = A.max_rows, lw = A.max_win;  // component-major: own rows a[k ld + i], window a[k lw + j]
+    double *s_x = (double *)(smem + L.x);
+    CT *s_xl = (CT *)(smem + L.xl);
+    CT *s_pd = (CT *)(smem + L.pd);
+    CT *s_wq = (CT *)(smem + L.wq);
+    CT *s_u4 = (CT *)(smem + L.u4);
+    CT *s_sw = (CT *)(smem + L.sw);
+    CT *s_rw = (CT *)(smem + L.rw);
+    CT *s_pw = (CT *)(smem + L.pw);
+    MT *s_val = (MT *)(smem + L.val);
+    unsigned short *s_nbr = (unsigned short *)(smem + L.nbr);
+    int *s_rinfo = (int *)(smem + L.rinfo);
+    int *s_lvl = (int *)(smem + L.lvl);
+    CT *s_cg = (CT *)(smem + L.cg);
+    CT *s_cu = (CT *)(smem + L.cu);
+    CT *s_cw = (CT *)(smem + L.cw);
+    int4 *s_cv = (int4 *)(smem + L.cv);
+    int *s_cm = (int *)(smem + L.cm);
+    unsigned char *s_fl = smem + L.fl;
+    const size_t nv = (size_t)A.nv;
+    CT *const wqb = (CT *)A.cwq;   // row sums of w: parity m, component q at wqb + nv (3 m + q)
+    double *const qcb = A.cqc;    // contact part of w: buffer m, component q at qcb + nv (3 m + q)
+    CT *const rsb = (CT *)A.crs;   // owners' (r, s): parity m at rsb + 8 nv m, 8 values per vertex
+    CT *const ppl = (CT *)A.cpp;   // P: upper-triangle entry i of vertex a at ppl[i nv + a]
+    unsigned char *const gfl = A.cfl;  // vertices of contact pairs
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int fe = E0 + e;
+        const int fb = A.fblk[fe];
+        const int slot = A.eslot[fe];
+        const MT *src = gval + 9 * (size_t)(fb & 0x7fffffff);
+        MT *dst = s_val + 9 * slot;
+        if (fb < 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dst[3 * i + j] = src[3 * j + i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[i] = src[i];
+        }
+        s_nbr[slot] = (unsigned short)(A.fnbr[fe] - wlo);
+    }
+    for (int j = threadIdx.x; j < A.lvlptr[c + 1] - A.lvlptr[c]; j += blockDim.x) s_lvl[j] = A.lvl[A.lvlptr[c] + j];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) s_rinfo[t] = A.rinfo[r0 + t];
+    for (int k = threadIdx.x; k < ncached; k += blockDim.x) {
+        const int i = c + k * (int)gridDim.x;
+        s_cv[k] = A.cv[i];
+        s_cm[k] = A.cmask[i];
+        s_cw[k] = (CT)A.cw[i];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) s_cg[12 * k + j] = (CT)A.cg[12 * (size_t)i + j];
+    }
+    for (int i = threadIdx.x; i < 3 * lw; i += blockDim.x) s_sw[i] = CT(0);
+    // the upper triangle of P of the own rows into the planes, and the flags
+    // of this CTA's pairs' vertices (read by other CTAs after the first
+    // reduction)
+    for (int e = threadIdx.x; e < 6 * nr; e += blockDim.x) {
+        const int i = e / nr, row = e - i * nr;
+        const size_t a = (size_t)(r0 + row);
+        ppl[(size_t)i * nv + a] = (CT)gpinv[9 * a + upper3(i)];
+    }
+    for (int kk = threadIdx.x; kk < nco; kk += blockDim.x) {
+        const int i = c + kk * (int)gridDim.x;
+        const int4 v = A.cv[i];
+        const int m = A.cmask[i];
+        if (m & 1) gfl[v.x] = 1;
+        if (m & 2) gfl[v.y] = 1;
+        if (m & 4) gfl[v.z] = 1;
+        if (m & 8) gfl[v.w] = 1;
+    }
+    auto load_p = [&](size_t a, CT (&P)[6]) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) P[i] = __ldcg(ppl + (size_t)i * nv + a);
+    };
+    // w of vertex a from the product of iteration m >= 0: the row sum plus,
+    // where the vertex belongs to a pair, the contact part rounded to CT (no
+    // FP64 arithmetic per window row: the FP64 pipe is narrow)
+    auto load_w = [&](size_t a, int m, bool in_pair, CT (&w)[3]) {
+        const CT *wq = wqb + 3 * nv * (size_t)(m & 1) + a;
+        const double *qc = qcb + 3 * nv * (size_t)(m % 3) + a;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            w[q] = __ldcg(wq + q * nv);
+            if (in_pair) w[q] = add_rn(w[q], to_ct(__ldcg(qc + q * nv), CT()));
+        }
+    };
+    // r of vertex a as its owner published it: values 0..2 (r) or 4..6 (s) of parity m
+    auto load_rs = [&](size_t a, int m, int off, CT (&v)[3]) {
+        const CT *p = rsb + 8 * nv * (size_t)(m & 1) + 8 * a + off;
+        if (mixed) {
+            const float4 f = __ldcg(reinterpret_cast<const float4 *>(p));
+            v[0] = f.x; v[1] = f.y; v[2] = f.z;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] = __ldcg(p + q);
+        }
+    };
+    unsigned nred = 0;
+    auto reduce = [&](auto &acc, auto on_total) {
+        constexpr int K = (int)std::extent<std::remove_reference_t<decltype(acc)>>::value;
+        double blk[K], tot[K];
+        if constexpr (mixed) block_sum<K>(acc, blk, red_f);
+        else block_sum<K>(acc, blk, red_d, red_q4);
+        if (threadIdx.x == 0) {
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            else ctl.state = PCG_ABORT;
+        }
+        ++nred;
+        __syncthreads();
+    };
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) tm[i] = 0;
+    __syncthreads();
+    // ---- init: x = 0, p = s = 0, r = b (published for iteration 0) --------
+    {
+        Acc acc[1] = {};
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+            const size_t a = (size_t)(r0 + i);
+            double bb = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double bk = A.b[3 * a + q];
+                s_x[q * ld + i] = 0.0;
+                if (mixed) s_xl[q * ld + i] = CT(0);
+                s_pd[q * ld + i] = CT(0);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) qcb[nv * (3 * m + q) + a] = 0.0;
+                A.qd[3 * a + q] = 0.0;
+                rsb[8 * a + q] = to_ct(bk, CT());
+                rsb[8 * a + 4 + q] = CT(0);
+                bb += bk * bk;
+            }
+            acc_add(acc[0], bb);
+        }
+        reduce(acc, [&](const double *t) {
+            ctl.bb = t[0];
+            ctl.rr = t[0];
+            ctl.rr_done = A.tol2 * t[0];
+            ctl.rr_fold = 0.01 * t[0];
+            ctl.alpha = ctl.beta = ctl.gam_old = ctl.alp_old = ctl.inv_gam_old = ctl.inv_alp_old = 0.0;
+            ctl.al = ctl.bt = 0.f;
+            ctl.it = 0;
+            ctl.folds = 0;
+            ctl.skip = 1;
+            if (t[0] > 0.0 && isfinite(t[0])) ctl.state = PCG_RUN;
+            else ctl.state = t[0] == 0.0 ? PCG_DONE : PCG_BAD;
+        });
+    }
+    if (ctl.state == PCG_RUN) {  // P and the pair flags over the window
+        for (int e = threadIdx.x; e < 6 * nwin; e += blockDim.x) {
+            const int i = e / nwin, j = e - i * nwin;
+            s_pw[i * lw + j] = __ldcg(ppl + (size_t)i * nv + wlo + j);
+        }
+        for (int j = threadIdx.x; j < nwin; j += blockDim.x) s_fl[j] = __ldcg(gfl + wlo + j);
+        __syncthreads();
+    }
+    while (ctl.state == PCG_RUN) {
+        const int k = ctl.it;
+        const bool upd = !ctl.skip;
+        const CT al = mixed ? (CT)ctl.al : (CT)ctl.alpha, bt = mixed ? (CT)ctl.bt : (CT)ctl.beta;
+        const double alpha = ctl.alpha;
+        if (timer) tm[4] = globaltimer();
+        Acc acc[3] = {};  // gamma = r.u, delta = u.H u, |r|^2
+        // ---- stage: the recurrences over the window and at the vertices of
+        // the cached contact pairs (items nwin + 4 pair + vertex), u = P r ----
+        {
+            CT *rsc = rsb + 8 * nv * (size_t)(k & 1);
+            double *qcn = qcb + 3 * nv * (size_t)((k + 1) % 3);  // product k - 2: read before the reduction of k - 1
+            const int nitem = nwin + 4 * ncached;
+            constexpr int RB = mixed ? 2 : 1;  // items per thread whose loads are issued together
+            for (int i0 = threadIdx.x; i0 < nitem; i0 += RB * blockDim.x) {
+                CT P[RB][6], w[RB][3], ro[RB][3], so[RB][3];
+                int av[RB];
+#pragma unroll
+                for (int v = 0; v < RB; ++v) {
+                    const int e = i0 + v * (int)blockDim.x;
+                    av[v] = -1;
+                    if (e < nwin) {
+                        av[v] = wlo + e;
+                    } else if (e < nitem) {
+                        const int kk = (e - nwin) >> 2, q = (e - nwin) & 3;
+                        if (s_cm[kk] >> q & 1) av[v] = (&s_cv[kk].x)[q];
+                    }
+                    if (av[v] >= 0) {
+                        const size_t a = (size_t)av[v];
+                        if (e < nwin) {
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) P[v][i] = s_pw[i * lw + e];
+                        } else {
+                            load_p(a, P[v]);
+                        }
+                        if (upd) load_w(a, k - 1, e >= nwin || s_fl[e], w[v]);
+                        if (e >= nwin && upd) {  // a pair's vertex: (r, s) of iteration k - 1
+                            load_rs(a, k - 1, 0, ro[v]);
+                            load_rs(a, k - 1, 4, so[v]);
+                        } else if (!upd) {
+                            load_rs(a, k, 0, ro[v]);  // r published for iteration k
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < RB; ++v) {
+                    const int e = i0 + v * (int)blockDim.x;
+                    if (e >= nitem) continue;
+                    CT r[3], s[3], u[3];
+                    if (e >= nwin) {  // u at a pair's vertex (zero where the pair has no vertex)
+                        const int kk = (e - nwin) >> 2, q = (e - nwin) & 3;
+                        if (av[v] >= 0) {
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                if (upd) {
+                                    s[j] = fma_rn(bt, so[v][j], w[v][j]);
+                                    r[j] = fma_rn(-al, s[j], ro[v][j]);
+                                } else {
+                                    r[j] = ro[v][j];
+                                }
+                            }
+                            prec3(P[v], r, u);
+                        } else {
+                            u[0] = u[1] = u[2] = CT(0);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) s_cu[12 * kk + 3 * q + j] = u[j];
+                        continue;
+                    }
+                    const int j = e, a = wlo + j, i = a - r0;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (upd) {
+                            s[q] = fma_rn(bt, s_sw[q * lw + j], w[v][q]);
+                            r[q] = fma_rn(-al, s[q], s_rw[q * lw + j]);
+                            s_sw[q * lw + j] = s[q];
+                        } else {
+                            r[q] = ro[v][q];
+                        }
+                        s_rw[q * lw + j] = r[q];
+                    }
+                    prec3(P[v], r, u);
+                    if (i >= 0 && i < nr) {  // own row
+                        if (upd) {
+                            CT uo[3];
+                            load3v(s_u4 + 4 * j, uo);  // u of iteration k - 1
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                const CT p = fma_rn(bt, s_pd[q * ld + i], uo[q]);
+                                s_pd[q * ld + i] = p;
+                                if (mixed) s_xl[q * ld + i] += al * p;
+                                else s_x[q * ld + i] += alpha * (double)p;
+                                qcn[(size_t)q * nv + a] = 0.0;
+                            }
+                            if (A.nc > 0) {
+                                if (mixed) {
+                                    float4 *d = reinterpret_cast<float4 *>(rsc + 8 * (size_t)a);
+                                    d[0] = make_float4((float)r[0], (float)r[1], (float)r[2], 0.f);
+                                    d[1] = make_float4((float)s[0], (float)s[1], (float)s[2], 0.f);
+                                } else {
+#pragma unroll
+                                    for (int q = 0; q < 3; ++q) {
+                                        rsc[8 * (size_t)a + q] = r[q];
+                                        rsc[8 * (size_t)a + 4 + q] = s[q];
+                                    }
+                                }
+                            }
+                        }
+                        acc_add(acc[0], (r[0] * u[0] + r[1] * u[1]) + r[2] * u[2]);
+                        acc_add(acc[2], (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+                    }
+                    if (mixed) *reinterpret_cast<float4 *>(s_u4 + 4 * j) = make_float4((float)u[0], (float)u[1], (float)u[2], 0.f);
+                    else
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) s_u4[4 * j + q] = u[q];
+                }
+            }
+        }
+        __syncthreads();
+        if (timer) tm[5] += globaltimer() - tm[4];
+        // ---- product: w = H u on the own rows (published), contact part ------
+        {
+            // rows are taken in order of decreasing length: their sums go to
+            // shared memory first and out to the planes in row order, so the
+            // global stores are coalesced
+            CT *wqc = wqb + 3 * nv * (size_t)(k & 1);
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                const int info = s_rinfo[t];
+                const int row = info >> 8, len = info & 255;
+                CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
+#pragma unroll 2
+                for (int j = 0; j < len; ++j) {
+                    const int slot = s_lvl[j] + t;
+                    const MT *v = s_val + 9 * slot;
+                    CT a[9], u[3];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) a[i] = (CT)v[i];
+                    load3v(s_u4 + 4 * s_nbr[slot], u);
+                    y0 += a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
+                    y1 += a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
+                    y2 += a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
+                }
+                s_wq[row] = y0;
+                s_wq[ld + row] = y1;
+                s_wq[2 * ld + row] = y2;
+                CT ui[3];
+                load3v(s_u4 + 4 * (r0 + row - wlo), ui);
+                acc_add(acc[1], (ui[0] * y0 + ui[1] * y1) + ui[2] * y2);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) wqc[(size_t)q * nv + r0 + i] = s_wq[q * ld + i];
+            if (timer) tm[6] += globaltimer() - tm[4];
+            if (threadIdx.x == blockDim.x - 1 && k > 0) {  // for the reduction below (read after its block sum)
+                ctl.inv_gam_old = 1.0 / ctl.gam_old;
+                ctl.inv_alp_old = 1.0 / ctl.alp_old;
+            }
+            double *qck = qcb + 3 * nv * (size_t)(k % 3);
+            CT cdot = CT(0);
+            for (int kk = threadIdx.x; kk < nco; kk += blockDim.x) {
+                CT g[12], u[12], w;
+                int vid[4], m;
+                if (kk < ncached) {
+                    const int4 v = s_cv[kk];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = s_cm[kk];
+                    w = s_cw[kk];
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        g[j] = s_cg[12 * kk + j];
+                        u[j] = s_cu[12 * kk + j];
+                    }
+                } else {  // beyond the cache: the same update at the pair's vertices
+                    const int i = c + kk * (int)gridDim.x;
+                    const int4 v = A.cv[i];
+                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                    m = A.cmask[i];
+                    w = (CT)A.cw[i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        CT uq[3] = {CT(0), CT(0), CT(0)};
+                        if (m >> q & 1) {
+                            const size_t a = (size_t)vid[q];
+                            CT P[6], r[3];
+                            load_p(a, P);
+                            if (upd) {
+                                CT wv[3], ro[3], so[3];
+                                load_w(a, k - 1, true, wv);
+                                load_rs(a, k - 1, 0, ro);
+                                load_rs(a, k - 1, 4, so);
+#pragma unroll
+                                for (int j = 0; j < 3; ++j) r[j] = fma_rn(-al, fma_rn(bt, so[j], wv[j]), ro[j]);
+                            } else {
+                                load_rs(a, k, 0, r);
+                            }
+                            prec3(P, r, uq);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
+                            u[3 * q + j] = uq[j];
+                        }
+                    }
+                }
+                CT s = CT(0);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) s += g[j] * u[j];
+                const CT t = w * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (m >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) atomicAdd(qck + (size_t)j * nv + vid[q], (double)(t * g[3 * q + j]));
+                cdot += t * s;
+            }
+            acc_add(acc[1], cdot);
+            if (timer) {
+                tm[7] += globaltimer() - tm[4];
+                const unsigned long long t1 = globaltimer();
+                tm[0] += t1 - tm[4];
+                tm[4] = t1;
+            }
+        }
+        reduce(acc, [&](const double *t) {
+            const double gam = t[0], del = t[1], rr = t[2];
+            ctl.rr = rr;
+            if (!isfinite(gam) || !isfinite(del) || !isfinite(rr)) {
+                ctl.state = PCG_BAD;
+                return;
+            }
+            const bool done = rr <= ctl.rr_done;
+            if (mixed && ctl.folds < A.max_replace && (done || rr <= ctl.rr_fold)) {
+                ctl.state = PCG_FOLD;
+                return;
+            }
+            if (done) {
+                ctl.state = PCG_DONE;
+                return;
+            }
+            if (ctl.it >= A.maxit) {
+                ctl.state = PCG_MAXIT;
+                return;
+            }
+            const double beta = ctl.it > 0 ? gam * ctl.inv_gam_old : 0.0;
+            const double den = ctl.it > 0 ? del - beta * gam * ctl.inv_alp_old : del;
+            if (!(den > 0.0) || !(gam > 0.0)) {  // no curvature left: stop with the current x
+                ctl.state = PCG_DONE;
+                return;
+            }
+            if (mixed) {
+                // the FP32 updates use alpha rounded to FP32: form it by an
+                // FP32 division of the FP64 quantities (short on this GPU)
+                // and carry exactly that value in the recurrence
+                ctl.al = div_to_f32(gam, den);
+                ctl.alpha = (double)ctl.al;
+            } else {
+                ctl.alpha = gam / den;
+                ctl.al = (float)ctl.alpha;
+            }
+            ctl.beta = beta;
+            ctl.bt = (float)beta;
+            ctl.gam_old = gam;
+            ctl.alp_old = ctl.alpha;
+            ++ctl.it;
+            ctl.skip = 0;
+        });
+        if (timer) tm[1] += globaltimer() - tm[4];
+        if constexpr (mixed) {
+        if (ctl.state == PCG_FOLD) {
+            // reliable update: x += x_l in FP64; the contact part of this
+            // iteration's product is dropped (the product is redone)
+            double *qck = qcb + 3 * nv * (size_t)(k % 3);
+            for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const double xv = s_x[q * ld + i] + (double)s_xl[q * ld + i];
+                    s_x[q * ld + i] = xv;
+                    s_xl[q * ld + i] = CT(0);
+                    A.x[3 * (size_t)(r0 + i) + q] = xv;
+                    qck[(size_t)q * nv + r0 + i] = 0.0;
+                }
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // x visible to every CTA
+            }
+            if (ctl.state == PCG_ABORT) break;
+            // H x with FP64 vectors (FP32 blocks): own full rows, then the
+            // contact part into qd
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                const int info = s_rinfo[t];
+                const int row = info >> 8, len = info & 255;
+                double h[3] = {0.0, 0.0, 0.0};
+                for (int j = 0; j < len; ++j) {
+                    const int slot = s_lvl[j] + t;
+                    const MT *v = s_val + 9 * slot;
+                    const size_t b = 3 * (size_t)(wlo + s_nbr[slot]);
+                    double xj[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) xj[q] = __ldcg(A.x + b + q);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        h[q] += (double)v[3 * q] * xj[0] + (double)v[3 * q + 1] * xj[1] + (double)v[3 * q + 2] * xj[2];
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) A.chx[3 * (size_t)(r0 + row) + q] = h[q];
+            }
+            for (int kk = threadIdx.x; kk < nco; kk += blockDim.x) {
+                const int i = c + kk * (int)gridDim.x;
+                const int4 v = A.cv[i];
+                const int mk = A.cmask[i];
+                const int vid[4] = {v.x, v.y, v.z, v.w};
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) s += A.cg[12 * (size_t)i + 3 * q + j] * __ldcg(A.x + 3 * vid[q] + j);
+                const double t = A.cw[i] * s;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk >> q & 1)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) atomicAdd(A.qd + 3 * vid[q] + j, t * A.cg[12 * (size_t)i + 3 * q + j]);
+            }
+            {
+                AccF none[1];
+                reduce(none, [&](const double *) {});  // contact part complete
+            }
+            if (ctl.state == PCG_ABORT) break;
+            // r = b - H x, published for the redone product of iteration k
+            CT *rsk = rsb + 8 * nv * (size_t)(k & 1);
+            AccF acc1[1];
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                const size_t a = (size_t)(r0 + i);
+                double rr = 0.0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const double rh = A.b[3 * a + q] - __ldcg(A.chx + 3 * a + q) - __ldcg(A.qd + 3 * a + q);
+                    A.qd[3 * a + q] = 0.0;
+                    rr += rh * rh;
+                    rsk[8 * a + q] = to_ct(rh, CT());
+                }
+                acc1[0].add(rr);
+            }
+            reduce(acc1, [&](const double *t) {
+                ++ctl.folds;
+                ctl.rr = t[0];
+                ctl.rr_fold = 0.01 * t[0];
+                if (!isfinite(t[0])) ctl.state = PCG_BAD;
+                else if (t[0] <= ctl.rr_done) ctl.state = PCG_DONE;
+                else {
+                    ctl.state = PCG_RUN;
+                    ctl.skip = 1;
+                }
+            });
+        }
+        }
+    }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            A.x[3 * (size_t)(r0 + i) + q] = s_x[q * ld + i] + (mixed ? (double)s_xl[q * ld + i] : 0.0);
+    // clear the pair flags (every CTA has copied its window's flags before
+    // the first product, and none reads them after its last reduction)
+    for (int kk = threadIdx.x; kk < nco; kk += blockDim.x) {
+        const int i = c + kk * (int)gridDim.x;
+        const int4 v = A.cv[i];
+        const int m = A.cmask[i];
+        if (m & 1) gfl[v.x] = 0;
+        if (m & 2) gfl[v.y] = 0;
+        if (m & 4) gfl[v.z] = 0;
+        if (m & 8) gfl[v.w] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.dflag[F_ITERS] = ctl.it;
+        A.dflag[F_MAXIT] = ctl.state == PCG_MAXIT;
+        A.dflag[F_DONE] = 1;
+        if (ctl.state == PCG_BAD) A.dflag[F_ERR] |= ERR_NONFINITE;
+        A.dscal[S_RR] = ctl.rr;
+        A.dscal[S_BB] = ctl.bb;
+        A.dscal[S_RZ] = ctl.gam_old;
+        A.dscal[S_T_SPMV] = 1e-6 * (double)tm[0];
+        A.dscal[S_T_RED1] = 1e-6 * (double)tm[1];
+        A.dscal[S_T_UPD] = 0.0;
+        A.dscal[S_T_RED2] = 0.0;
+        A.dscal[S_T_STAGE] = 1e-6 * (double)tm[5];
+        A.dscal[S_T_ROWS] = 1e-6 * (double)tm[6];
+        A.dscal[S_T_CONTACT] = 1e-6 * (double)tm[7];
     }
 }
 
@@ -1005,7 +1735,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             ctl.rz = t[0];
             ctl.bb = t[1];
             ctl.rr = t[1];
-            ctl.rr_ref = t[1];
+            ctl.rr_done = A.tol2 * t[1];
+            ctl.rr_fold = 0.01 * t[1];
             ctl.beta = 0.0;
             ctl.bt = 0.f;
             ctl.it = 0;
@@ -1170,8 +1901,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 if (!isfinite(pq)) ctl.state = PCG_BAD;
                 else if (!(pq > 0.0)) ctl.state = PCG_DONE;
                 else {
-                    ctl.alpha = ctl.rz / pq;
-                    ctl.al = (float)ctl.alpha;
+                    ctl.al = div_to_f32(ctl.rz, pq);
+                    ctl.alpha = (double)ctl.al;
                 }
             });
             if (timer) {
@@ -1236,16 +1967,16 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             reduce(acc, [&](const double *t) {
                 ++ctl.it;
                 ctl.rz_old = ctl.rz;
-                ctl.beta = t[0] / ctl.rz_old;
-                ctl.bt = (float)ctl.beta;
+                ctl.bt = div_to_f32(t[0], ctl.rz_old);
+                ctl.beta = (double)ctl.bt;
                 ctl.rz = t[0];
                 ctl.rr = t[1];
                 if (!isfinite(t[0]) || !isfinite(t[1])) {
                     ctl.state = PCG_BAD;
                     return;
                 }
-                const bool done = ctl.rr <= A.tol2 * ctl.bb;
-                if (ctl.folds < A.max_replace && (done || ctl.rr <= 0.01 * ctl.rr_ref)) ctl.state = PCG_FOLD;
+                const bool done = ctl.rr <= ctl.rr_done;
+                if (ctl.folds < A.max_replace && (done || ctl.rr <= ctl.rr_fold)) ctl.state = PCG_FOLD;
                 else if (done) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
             });
@@ -1337,13 +2068,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             }
             reduce(acc, [&](const double *t) {
                 ++ctl.folds;
-                ctl.beta = t[0] / ctl.rz_old;
-                ctl.bt = (float)ctl.beta;
+                ctl.bt = div_to_f32(t[0], ctl.rz_old);
+                ctl.beta = (double)ctl.bt;
                 ctl.rz = t[0];
                 ctl.rr = t[1];
-                ctl.rr_ref = t[1];
+                ctl.rr_fold = 0.01 * t[1];
                 if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
-                else if (ctl.rr <= A.tol2 * ctl.bb) ctl.state = PCG_DONE;
+                else if (ctl.rr <= ctl.rr_done) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
                 else ctl.state = PCG_RUN;
             });
@@ -1640,10 +2371,11 @@ static int setup_persistent(Scene &S)
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return BF_E_CUDA;
     const int per_sm = std::min(4, std::max(1, S.pcg_ctas_per_sm));
-    const int modes[4] = {PCG_RESIDENT, PCG_STREAM, PCG_SYM, PCG_GLOBAL};
+    const int modes[5] = {PCG_CG1, PCG_RESIDENT, PCG_STREAM, PCG_SYM, PCG_GLOBAL};
     for (int mode : modes) {
-        if (mode == PCG_RESIDENT && !S.pcg_allow_resident) continue;
-        if ((mode == PCG_RESIDENT || mode == PCG_STREAM) && S.pcg_force_global) continue;
+        if (mode == PCG_CG1 && !S.pcg_cg1) continue;
+        if ((mode == PCG_RESIDENT || mode == PCG_CG1) && !S.pcg_allow_resident) continue;
+        if ((mode == PCG_RESIDENT || mode == PCG_CG1 || mode == PCG_STREAM) && S.pcg_force_global) continue;
         if (mode == PCG_SYM) {  // mixed precision only (FP32 blocks and vector reductions)
             if constexpr (mixed && std::is_same<MT, float>::value) {
                 if (S.pcg_no_sym) continue;
@@ -1655,9 +2387,15 @@ static int setup_persistent(Scene &S)
             }
             continue;
         }
-        const void *kern = mode == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
-                           : mode == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
-                                                : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
+        const void *kern = mode == PCG_CG1        ? (const void *)k_pcg_cg1<MT, VT>
+                           : mode == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
+                           : mode == PCG_STREAM   ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
+                                                  : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
+        // shared-memory bytes at kc cached contact pairs
+        auto layout_bytes = [&](int mr, int mw, int me, int ml, int kc) -> size_t {
+            if (mode == PCG_CG1) return pcg_cg1_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, kc).total;
+            return pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, kc).total;
+        };
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BF_E_CUDA;
         for (int cps = per_sm; cps >= 1; --cps) {
@@ -1672,17 +2410,24 @@ static int setup_persistent(Scene &S)
             if (st == BF_E_CAPACITY) continue;
             if (st) return st;
             const size_t avail = (size_t)smem_optin - fa.sharedSizeBytes;
-            const PcgLayout L0 = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, 0);
-            if (L0.total > avail) continue;
-            int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(sizeof(CT)));
-            while (kc > 0 && pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, kc).total > avail) --kc;
-            const PcgLayout L = pcg_layout(mixed, sizeof(CT), sizeof(MT), mr, mw, me, ml, mode, kc);
+            const size_t L0 = layout_bytes(mr, mw, me, ml, 0);
+            if (L0 > avail) continue;
+            int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0) / pcg_contact_bytes(sizeof(CT)));
+            while (kc > 0 && layout_bytes(mr, mw, me, ml, kc) > avail) --kc;
+            const size_t Ltotal = layout_bytes(mr, mw, me, ml, kc);
             // the attribute is an upper bound shared by every scene: set it to
             // the most any launch may ask for, so concurrent set-ups agree
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
             int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, L.total);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, Ltotal);
             if (occ < cps) continue;
+            if (mode == PCG_CG1) {  // published row sums, contact parts, (r, s), H x
+                if (S.pcg_cg1buf) dev_free(S, S.pcg_cg1buf);
+                const PcgCg1Buf cbl = pcg_cg1_buf(S.nv, sizeof(CT));
+                S.pcg_cg1buf = (unsigned char *)dev_alloc(S, cbl.total);
+                if (!S.pcg_cg1buf) return BF_E_OOM;
+                cudaMemsetAsync(S.pcg_cg1buf + cbl.fl, 0, cbl.total - cbl.fl, S.stream);  // no vertex flagged
+            }
             if (mode == PCG_GLOBAL) {  // jagged block copy and per-CTA vectors in global memory
                 const size_t stride = (pcg_vec_layout(mixed, sizeof(CT), mr).total + 255) & ~(size_t)255;
                 if (S.pcg_gvec) dev_free(S, S.pcg_gvec);
@@ -1694,7 +2439,7 @@ static int setup_persistent(Scene &S)
             }
             S.pcg_grid = grid;
             S.pcg_block = block;
-            S.pcg_smem = (int)L.total;
+            S.pcg_smem = (int)Ltotal;
             S.pcg_resident = mode;
             S.pcg_max_rows = mr;
             S.pcg_max_ent = me;
@@ -1826,6 +2571,16 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     }
     A.uval = S.pcg_uval;
     A.yq = S.pcg_yq;
+    {
+        const PcgCg1Buf cbl = pcg_cg1_buf(S.nv, sizeof(VT) == 4 ? 4 : 8);
+        unsigned char *cb = S.pcg_cg1buf;
+        A.cwq = cb ? cb + cbl.wq : nullptr;
+        A.cqc = cb ? (double *)(cb + cbl.qc) : nullptr;
+        A.crs = cb ? cb + cbl.rs : nullptr;
+        A.chx = cb ? (double *)(cb + cbl.hx) : nullptr;
+        A.cpp = cb ? cb + cbl.pp : nullptr;
+        A.cfl = cb ? cb + cbl.fl : nullptr;
+    }
     if (S.pcg_resident == PCG_SYM) {
         if constexpr (std::is_same<MT, float>::value) {
             k_jagged_gather_upper<<<cdiv(S.nnzb, kThreads), kThreads, 0, S.stream>>>(
@@ -1855,6 +2610,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         const void *kern = S.pcg_resident == PCG_RESIDENT ? (const void *)k_pcg_persistent<MT, VT, PCG_RESIDENT>
                            : S.pcg_resident == PCG_STREAM ? (const void *)k_pcg_persistent<MT, VT, PCG_STREAM>
                            : S.pcg_resident == PCG_SYM    ? (const void *)k_pcg_sym
+                           : S.pcg_resident == PCG_CG1    ? (const void *)k_pcg_cg1<MT, VT>
                                                           : (const void *)k_pcg_persistent<MT, VT, PCG_GLOBAL>;
         e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(S.pcg_block), args, (size_t)S.pcg_smem, S.stream);
         ++S.n_launch;

@@ -98,7 +98,7 @@ def test_alone_equals_in_the_mix_with_autotuning(torch_cuda):
         serving.destroy(handles)
     assert out["failed"] == 0 and out["steps"] == 10 * len(seeds)
     tuned = out["pcg_mode_by_size_bucket"]
-    assert len(tuned) >= 1 and all(m in (0, 1, 2, 17, 18, 33, 34, 97, 98) for m in tuned.values())
+    assert len(tuned) >= 1 and all(m in (0, 1, 2, 129, 130, 17, 18, 33, 34, 97, 98) for m in tuned.values())
     tol = 1e-4 * target.bbox_diag()
     assert np.abs(xa - xm).max() <= tol, np.abs(xa - xm).max()
     assert np.abs(va - vm).max() <= tol / target.params.dt

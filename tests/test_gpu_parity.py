@@ -369,11 +369,14 @@ def test_empty_and_edge_cases(torch_cuda):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, precision):
-    """The persistent cooperative PCG (resident, streamed, and the two
-    global-memory variants: in mixed precision the symmetric one under mode
-    33 and the full-row one under 97) and the one-launch-per-phase PCG run
-    the same recurrences; all solve the oracle's system to the tolerance
-    (mixed precision: FP32 matrix, so the FP64 residual is looser)."""
+    """The persistent cooperative PCG (resident with the single-reduction
+    recurrence under mode 1, resident with two reductions per iteration under
+    mode 129, streamed, and the two global-memory variants: in mixed
+    precision the symmetric one under mode 33 and the full-row one under 97)
+    and the one-launch-per-phase PCG reach the same solution in about the
+    same number of iterations (the same Krylov iterates in exact
+    arithmetic); all solve the oracle's system to the tolerance (mixed
+    precision: FP32 matrix, so the FP64 residual is looser)."""
     torch = torch_cuda
     s, x, v, keys, lam, gam = contact_state
     sim, o = make_pair(s, x, v, keys, lam, gam, precision)
@@ -388,13 +391,17 @@ def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, pr
     b = -G_o
     H = o.hess_dense()
     sols, its = [], []
-    modes = (1, 17, 33, 97, 0)  # resident, streamed, global (symmetric in mixed), full-row global, per-phase
+    # resident (one reduction per iteration), resident with two, streamed,
+    # global (symmetric in mixed), full-row global, per-phase
+    modes = (1, 129, 17, 33, 97, 0)
     for mode in modes:
         B.bf_set_pcg_mode(sim.h, mode)
         xg = torch.zeros_like(G_g)
         it, _ = B.bf_pcg(sim.h, dev(torch, b), xg, 1e-6, 100000)
         if mode in (33, 97):
             assert B.bf_get_pcg_config(sim.h)["resident"] == (3 if precision and mode == 33 else 2)
+        if mode in (1, 129) and precision:  # FP64 blocks of this system do not fit in one CTA's shared memory
+            assert B.bf_get_pcg_config(sim.h)["resident"] == (4 if mode == 1 else 1)
         sols.append(host(xg).reshape(-1))
         its.append(it)
     bar = 1e-6 * 1.01 if precision == 0 else 1e-4
@@ -410,12 +417,13 @@ def test_pcg_persistent_matches_per_phase_launches(torch_cuda, contact_state, pr
 @pytest.mark.parametrize("precision", [0, 1])
 def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
     """On a system split over several CTAs (a 20k-tet scene after a few
-    steps, with contacts), the resident, streamed and global-vector
-    persistent variants (in mixed precision both the symmetric one and the
-    one streaming both triangles) at one and two CTAs per SM and the
-    per-phase launches reach the tolerance on the library's own operator and
-    agree with each other; the autotuner then times them and sets one whose
-    solve meets the tolerance."""
+    steps, with contacts), the resident (two reductions per iteration, and
+    the single-reduction recurrence), streamed and global-vector persistent
+    variants (in mixed precision both the symmetric one and the one
+    streaming both triangles) at one and two CTAs per SM and the per-phase
+    launches reach the tolerance on the library's own operator and agree
+    with each other, iteration counts within 5 %; the autotuner then times
+    them and sets one whose solve meets the tolerance."""
     torch = torch_cuda
     from paper_2512_12151_b300 import serving
     s = scenes.batch_scene(11, 1.8e4, 2e4, precision=precision)
@@ -432,7 +440,7 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
         B.bf_assemble(h, xt, xd, xd, G)
         b = -G
         sols, its, grids = [], [], []
-        modes = (1, 2, 17, 18, 33, 34, 97, 98, 0)
+        modes = (1, 2, 129, 130, 17, 18, 33, 34, 97, 98, 0)
         for mode in modes:
             B.bf_set_pcg_mode(h, mode)
             p = torch.zeros_like(xd)
@@ -444,9 +452,13 @@ def test_pcg_modes_agree_on_a_multi_cta_system(torch_cuda, precision):
             sols.append(host(p).reshape(-1))
             its.append(it)
             grids.append(B.bf_get_pcg_config(h))
-        # several CTAs; the symmetric variant (mixed) or the full-row one (FP64) under 33, the full-row one under 97
-        assert grids[0]["ctas"] > 1 and grids[4]["resident"] == (3 if precision else 2)
-        assert grids[6]["resident"] == 2
+        # several CTAs; the single-reduction resident variant under 1 and 2,
+        # the two-reduction one under 129 and 130, the symmetric variant
+        # (mixed) or the full-row one (FP64) under 33, the full-row one under 97
+        assert grids[0]["ctas"] > 1 and grids[6]["resident"] == (3 if precision else 2)
+        if precision:  # FP64 blocks: the resident variants do not fit at this split
+            assert [g["resident"] for g in grids[:4]] == [4, 4, 1, 1]
+        assert grids[8]["resident"] == 2
         last = len(modes) - 1
         for k in range(last):
             assert abs(its[k] - its[last]) <= max(2, its[last] // 20), its
@@ -478,16 +490,22 @@ def multi_cta_state():
     return s, x, v, keys, lam, gam
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision):
+@pytest.mark.parametrize("precision,mode", [(0, 1), (1, 1), (0, 129), (1, 129)])
+def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision, mode):
     """One time step from an oracle contact state on a system the persistent
-    PCG spreads over several CTAs: positions within 1e-6 (FP64) or 1e-4
-    (mixed) x the bounding-box diagonal, same active set in FP64."""
+    PCG spreads over several CTAs, with the single-reduction recurrence (mode
+    1) and with two reductions per iteration (mode 129): positions within
+    1e-6 (FP64) or 1e-4 (mixed) x the bounding-box diagonal, same active set
+    in FP64."""
     s, x, v, keys, lam, gam = multi_cta_state
     sim, o = make_pair(s, x, v, keys, lam, gam, precision)
+    B.bf_set_pcg_mode(sim.h, mode)
     o.step(1)
     _, st = sim.step(1)
-    assert B.bf_get_pcg_config(sim.h)["ctas"] > 1
+    cfg = B.bf_get_pcg_config(sim.h)
+    assert cfg["ctas"] > 1
+    if precision:  # FP64 blocks: the resident variants do not fit at this split
+        assert cfg["resident"] == (4 if mode == 1 else 1)
     xo, vo = o.get_state()
     xg, vg = sim.state()
     tol = (1e-6 if precision == 0 else 1e-4) * s.bbox_diag()
@@ -496,4 +514,34 @@ def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision):
         ko, _, _ = o.active_get()
         kg, _, _ = B.bf_get_active_set(sim.h)
         assert keyset(ko) == keyset(kg)
+    sim.close()
+
+
+@pytest.mark.parametrize("mode", [1, 129])
+def test_one_step_fp64_resident_scene(torch_cuda, mode):
+    """FP64 on a scene whose FP64 blocks fit in shared memory (a 2k-tet
+    stack over three CTAs): one time step from an oracle contact state with
+    the single-reduction recurrence (mode 1, variant 4) and with two
+    reductions per iteration (mode 129, variant 1) lands within 1e-6 x the
+    bounding-box diagonal of the oracle's step, with the same active set."""
+    s = scenes.batch_scene(5, 1e3, 2e3, precision=0)
+    o = O.Oracle(s)
+    for _ in range(40):
+        o.step(1)
+        if len(o.active_get()[0]) > 0:
+            break
+    x, v = o.get_state()
+    keys, lam, gam = o.active_get()
+    assert len(keys) > 0
+    sim, o2 = make_pair(s, x, v, keys, lam, gam, 0)
+    B.bf_set_pcg_mode(sim.h, mode)
+    o2.step(1)
+    st, _ = sim.step(1)
+    assert st == 0
+    cfg = B.bf_get_pcg_config(sim.h)
+    assert cfg["ctas"] > 1 and cfg["resident"] == (4 if mode == 1 else 1)
+    xo, _ = o2.get_state()
+    xg, _ = sim.state()
+    assert np.abs(xg - xo).max() <= 1e-6 * s.bbox_diag(), np.abs(xg - xo).max()
+    assert keyset(o2.active_get()[0]) == keyset(B.bf_get_active_set(sim.h)[0])
     sim.close()
