@@ -126,6 +126,18 @@ __device__ __forceinline__ float div_to_f32(double num, double den)
     return __double2float_rn(num / den);
 }
 
+// Finiteness and order tests on IEEE-754 bit patterns with integer
+// operations, for the scalar steps on the path through a grid-wide reduction
+// (this GPU's FP64 pipe is narrow): finite; 0 < x < inf; a <= b for a, b in
+// [+0, inf].
+__device__ __forceinline__ bool finite_b(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool pos_b(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool le_nonneg_b(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 {
     unsigned v;
@@ -559,7 +571,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             ctl.bt = 0.f;
             ctl.it = 0;
             ctl.folds = 0;
-            if (t[1] > 0.0 && isfinite(t[1]) && isfinite(t[0])) ctl.state = PCG_RUN;
+            if (pos_b(t[1]) && finite_b(t[0]) && finite_b(t[1])) ctl.state = PCG_RUN;
             else ctl.state = t[1] == 0.0 ? PCG_DONE : PCG_BAD;
         });
     }
@@ -670,9 +682,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
             }
             reduce(acc, [&](const double *t) {
                 const double pq = t[0];
-                if (!isfinite(pq)) {
+                if (!finite_b(pq)) {
                     ctl.state = PCG_BAD;
-                } else if (!(pq > 0.0)) {
+                } else if (!pos_b(pq)) {
                     // no curvature left along p: stop with the current x, as the
                     // per-phase solver does, and let the line search judge it
                     ctl.state = PCG_DONE;
@@ -733,12 +745,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 }
                 ctl.rz = t[0];
                 ctl.rr = t[1];
-                if (!isfinite(t[0]) || !isfinite(t[1])) {
+                if (!finite_b(t[0]) || !finite_b(t[1])) {
                     ctl.state = PCG_BAD;
                     return;
                 }
-                const bool done = ctl.rr <= ctl.rr_done;
-                if (mixed && ctl.folds < A.max_replace && (done || ctl.rr <= ctl.rr_fold))
+                const bool done = le_nonneg_b(ctl.rr, ctl.rr_done);  // rr, rr_done, rr_fold >= 0
+                if (mixed && ctl.folds < A.max_replace && (done || le_nonneg_b(ctl.rr, ctl.rr_fold)))
                     ctl.state = PCG_FOLD;
                 else if (done)
                     ctl.state = PCG_DONE;
@@ -823,8 +835,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
                 ctl.rz = t[0];
                 ctl.rr = t[1];
                 ctl.rr_fold = 0.01 * t[1];
-                if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
-                else if (ctl.rr <= ctl.rr_done) ctl.state = PCG_DONE;
+                if (!finite_b(t[0]) || !finite_b(t[1])) ctl.state = PCG_BAD;
+                else if (le_nonneg_b(ctl.rr, ctl.rr_done)) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
                 else ctl.state = PCG_RUN;
             });
@@ -952,10 +964,11 @@ inline PcgCg1Buf pcg_cg1_buf(int nv_, int ct)
 // during the product, off the path through the reduction: an FP64 division
 // is long on this GPU, whose FP64 pipe is narrow)
 struct PcgCg1Ctl {
-    double alpha, beta, gam_old, alp_old, inv_gam_old, inv_alp_old, rr, rr_done, rr_fold, bb;
+    double alpha, beta, gam_old, inv_gam_old, c_old, rr, rr_done, rr_fold, bb;  // c_old = 1 / (gamma_old alpha_old)
     float al, bt;
     int it, folds, state, skip;
 };
+
 
 // explicitly rounded operations, so that every CTA computes the window
 // recurrences to the same bits whatever code the compiler emits around them
@@ -1143,12 +1156,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
             ctl.rr = t[0];
             ctl.rr_done = A.tol2 * t[0];
             ctl.rr_fold = 0.01 * t[0];
-            ctl.alpha = ctl.beta = ctl.gam_old = ctl.alp_old = ctl.inv_gam_old = ctl.inv_alp_old = 0.0;
+            ctl.alpha = ctl.beta = ctl.gam_old = ctl.inv_gam_old = ctl.c_old = 0.0;
             ctl.al = ctl.bt = 0.f;
             ctl.it = 0;
             ctl.folds = 0;
             ctl.skip = 1;
-            if (t[0] > 0.0 && isfinite(t[0])) ctl.state = PCG_RUN;
+            if (pos_b(t[0])) ctl.state = PCG_RUN;
             else ctl.state = t[0] == 0.0 ? PCG_DONE : PCG_BAD;
         });
     }
@@ -1164,7 +1177,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
         const int k = ctl.it;
         const bool upd = !ctl.skip;
         const CT al = mixed ? (CT)ctl.al : (CT)ctl.alpha, bt = mixed ? (CT)ctl.bt : (CT)ctl.beta;
-        const double alpha = ctl.alpha;
+        const double alpha = ctl.alpha;  // FP64 only
         if (timer) tm[4] = globaltimer();
         Acc acc[3] = {};  // gamma = r.u, delta = u.H u, |r|^2
         // ---- stage: the recurrences over the window and at the vertices of
@@ -1284,98 +1297,107 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
         {
             // rows are taken in order of decreasing length: their sums go to
             // shared memory first and out to the planes in row order, so the
-            // global stores are coalesced
+            // global stores are coalesced.  Warps without a row (fewer rows
+            // than threads) take the contact pairs meanwhile; otherwise every
+            // thread sums rows, then takes pairs.
             CT *wqc = wqb + 3 * nv * (size_t)(k & 1);
-            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-                const int info = s_rinfo[t];
-                const int row = info >> 8, len = info & 255;
-                CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
-#pragma unroll 2
-                for (int j = 0; j < len; ++j) {
-                    const int slot = s_lvl[j] + t;
-                    const MT *v = s_val + 9 * slot;
-                    CT a[9], u[3];
+            double *qck = qcb + 3 * nv * (size_t)(k % 3);
+            const int nrw = (nr + 31) & ~31;
+            const bool split = nrw < (int)blockDim.x;
+            const int c0 = split ? nrw : 0, cstep = split ? (int)blockDim.x - nrw : (int)blockDim.x;
+            CT cdot = CT(0);
+            if (!split || (int)threadIdx.x < nrw) {
+                for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                    const int info = s_rinfo[t];
+                    const int row = info >> 8, len = info & 255;
+                    CT y0 = CT(0), y1 = CT(0), y2 = CT(0);
+#pragma unroll 4
+                    for (int j = 0; j < len; ++j) {
+                        const int slot = s_lvl[j] + t;
+                        const MT *v = s_val + 9 * slot;
+                        CT a[9], u[3];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) a[i] = (CT)v[i];
-                    load3v(s_u4 + 4 * s_nbr[slot], u);
-                    y0 += a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
-                    y1 += a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
-                    y2 += a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
+                        for (int i = 0; i < 9; ++i) a[i] = (CT)v[i];
+                        load3v(s_u4 + 4 * s_nbr[slot], u);
+                        y0 += a[0] * u[0] + a[1] * u[1] + a[2] * u[2];
+                        y1 += a[3] * u[0] + a[4] * u[1] + a[5] * u[2];
+                        y2 += a[6] * u[0] + a[7] * u[1] + a[8] * u[2];
+                    }
+                    s_wq[row] = y0;
+                    s_wq[ld + row] = y1;
+                    s_wq[2 * ld + row] = y2;
+                    CT ui[3];
+                    load3v(s_u4 + 4 * (r0 + row - wlo), ui);
+                    acc_add(acc[1], (ui[0] * y0 + ui[1] * y1) + ui[2] * y2);
                 }
-                s_wq[row] = y0;
-                s_wq[ld + row] = y1;
-                s_wq[2 * ld + row] = y2;
-                CT ui[3];
-                load3v(s_u4 + 4 * (r0 + row - wlo), ui);
-                acc_add(acc[1], (ui[0] * y0 + ui[1] * y1) + ui[2] * y2);
+            }
+            if (timer) tm[6] += globaltimer() - tm[4];
+            if (threadIdx.x == blockDim.x - 1 && k > 0) {  // for the reduction below (read after its block sum)
+                ctl.inv_gam_old = 1.0 / ctl.gam_old;
+                ctl.c_old = ctl.inv_gam_old / (mixed ? (double)ctl.al : ctl.alpha);
+            }
+            if (!split || (int)threadIdx.x >= nrw) {
+                for (int kk = (int)threadIdx.x - c0; kk < nco; kk += cstep) {
+                    CT g[12], u[12], w;
+                    int vid[4], m;
+                    if (kk < ncached) {
+                        const int4 v = s_cv[kk];
+                        vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                        m = s_cm[kk];
+                        w = s_cw[kk];
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) {
+                            g[j] = s_cg[12 * kk + j];
+                            u[j] = s_cu[12 * kk + j];
+                        }
+                    } else {  // beyond the cache: the same update at the pair's vertices
+                        const int i = c + kk * (int)gridDim.x;
+                        const int4 v = A.cv[i];
+                        vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
+                        m = A.cmask[i];
+                        w = (CT)A.cw[i];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            CT uq[3] = {CT(0), CT(0), CT(0)};
+                            if (m >> q & 1) {
+                                const size_t a = (size_t)vid[q];
+                                CT P[6], r[3];
+                                load_p(a, P);
+                                if (upd) {
+                                    CT wv[3], ro[3], so[3];
+                                    load_w(a, k - 1, true, wv);
+                                    load_rs(a, k - 1, 0, ro);
+                                    load_rs(a, k - 1, 4, so);
+#pragma unroll
+                                    for (int j = 0; j < 3; ++j) r[j] = fma_rn(-al, fma_rn(bt, so[j], wv[j]), ro[j]);
+                                } else {
+                                    load_rs(a, k, 0, r);
+                                }
+                                prec3(P, r, uq);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
+                                u[3 * q + j] = uq[j];
+                            }
+                        }
+                    }
+                    CT s = CT(0);
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) s += g[j] * u[j];
+                    const CT t = w * s;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (m >> q & 1)
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) atomicAdd(qck + (size_t)j * nv + vid[q], (double)(t * g[3 * q + j]));
+                    cdot += t * s;
+                }
             }
             __syncthreads();
             for (int i = threadIdx.x; i < nr; i += blockDim.x)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) wqc[(size_t)q * nv + r0 + i] = s_wq[q * ld + i];
-            if (timer) tm[6] += globaltimer() - tm[4];
-            if (threadIdx.x == blockDim.x - 1 && k > 0) {  // for the reduction below (read after its block sum)
-                ctl.inv_gam_old = 1.0 / ctl.gam_old;
-                ctl.inv_alp_old = 1.0 / ctl.alp_old;
-            }
-            double *qck = qcb + 3 * nv * (size_t)(k % 3);
-            CT cdot = CT(0);
-            for (int kk = threadIdx.x; kk < nco; kk += blockDim.x) {
-                CT g[12], u[12], w;
-                int vid[4], m;
-                if (kk < ncached) {
-                    const int4 v = s_cv[kk];
-                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
-                    m = s_cm[kk];
-                    w = s_cw[kk];
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        g[j] = s_cg[12 * kk + j];
-                        u[j] = s_cu[12 * kk + j];
-                    }
-                } else {  // beyond the cache: the same update at the pair's vertices
-                    const int i = c + kk * (int)gridDim.x;
-                    const int4 v = A.cv[i];
-                    vid[0] = v.x; vid[1] = v.y; vid[2] = v.z; vid[3] = v.w;
-                    m = A.cmask[i];
-                    w = (CT)A.cw[i];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        CT uq[3] = {CT(0), CT(0), CT(0)};
-                        if (m >> q & 1) {
-                            const size_t a = (size_t)vid[q];
-                            CT P[6], r[3];
-                            load_p(a, P);
-                            if (upd) {
-                                CT wv[3], ro[3], so[3];
-                                load_w(a, k - 1, true, wv);
-                                load_rs(a, k - 1, 0, ro);
-                                load_rs(a, k - 1, 4, so);
-#pragma unroll
-                                for (int j = 0; j < 3; ++j) r[j] = fma_rn(-al, fma_rn(bt, so[j], wv[j]), ro[j]);
-                            } else {
-                                load_rs(a, k, 0, r);
-                            }
-                            prec3(P, r, uq);
-                        }
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
-                            u[3 * q + j] = uq[j];
-                        }
-                    }
-                }
-                CT s = CT(0);
-#pragma unroll
-                for (int j = 0; j < 12; ++j) s += g[j] * u[j];
-                const CT t = w * s;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (m >> q & 1)
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) atomicAdd(qck + (size_t)j * nv + vid[q], (double)(t * g[3 * q + j]));
-                cdot += t * s;
-            }
             acc_add(acc[1], cdot);
             if (timer) {
                 tm[7] += globaltimer() - tm[4];
@@ -1387,12 +1409,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
         reduce(acc, [&](const double *t) {
             const double gam = t[0], del = t[1], rr = t[2];
             ctl.rr = rr;
-            if (!isfinite(gam) || !isfinite(del) || !isfinite(rr)) {
+            if (!finite_b(gam) || !finite_b(del) || !finite_b(rr)) {
                 ctl.state = PCG_BAD;
                 return;
             }
-            const bool done = rr <= ctl.rr_done;
-            if (mixed && ctl.folds < A.max_replace && (done || rr <= ctl.rr_fold)) {
+            const bool done = le_nonneg_b(rr, ctl.rr_done);  // rr, rr_done, rr_fold >= 0
+            if (mixed && ctl.folds < A.max_replace && (done || le_nonneg_b(rr, ctl.rr_fold))) {
                 ctl.state = PCG_FOLD;
                 return;
             }
@@ -1404,26 +1426,23 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
                 ctl.state = PCG_MAXIT;
                 return;
             }
-            const double beta = ctl.it > 0 ? gam * ctl.inv_gam_old : 0.0;
-            const double den = ctl.it > 0 ? del - beta * gam * ctl.inv_alp_old : del;
-            if (!(den > 0.0) || !(gam > 0.0)) {  // no curvature left: stop with the current x
+            // p.Hp = delta - beta gamma / alpha_old = delta - gamma^2 / (gamma_old alpha_old)
+            const double den = ctl.it > 0 ? fma(-(gam * gam), ctl.c_old, del) : del;
+            if (!pos_b(den) || !pos_b(gam)) {  // no curvature left: stop with the current x
                 ctl.state = PCG_DONE;
                 return;
             }
             if (mixed) {
-                // the FP32 updates use alpha rounded to FP32: form it by an
-                // FP32 division of the FP64 quantities (short on this GPU)
-                // and carry exactly that value in the recurrence
+                // the FP32 updates use alpha and beta rounded to FP32: alpha
+                // by an FP32 division of the FP64 quantities (short on this
+                // GPU), carried as exactly that value in the recurrence
                 ctl.al = div_to_f32(gam, den);
-                ctl.alpha = (double)ctl.al;
+                ctl.bt = ctl.it > 0 ? __double2float_rn(gam * ctl.inv_gam_old) : 0.f;
             } else {
                 ctl.alpha = gam / den;
-                ctl.al = (float)ctl.alpha;
+                ctl.beta = ctl.it > 0 ? gam * ctl.inv_gam_old : 0.0;
             }
-            ctl.beta = beta;
-            ctl.bt = (float)beta;
             ctl.gam_old = gam;
-            ctl.alp_old = ctl.alpha;
             ++ctl.it;
             ctl.skip = 0;
         });
@@ -1509,8 +1528,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
                 ++ctl.folds;
                 ctl.rr = t[0];
                 ctl.rr_fold = 0.01 * t[0];
-                if (!isfinite(t[0])) ctl.state = PCG_BAD;
-                else if (t[0] <= ctl.rr_done) ctl.state = PCG_DONE;
+                if (!finite_b(t[0])) ctl.state = PCG_BAD;
+                else if (le_nonneg_b(t[0], ctl.rr_done)) ctl.state = PCG_DONE;
                 else {
                     ctl.state = PCG_RUN;
                     ctl.skip = 1;
@@ -1741,7 +1760,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             ctl.bt = 0.f;
             ctl.it = 0;
             ctl.folds = 0;
-            if (t[1] > 0.0 && isfinite(t[1]) && isfinite(t[0])) ctl.state = PCG_RUN;
+            if (pos_b(t[1]) && finite_b(t[0]) && finite_b(t[1])) ctl.state = PCG_RUN;
             else ctl.state = t[1] == 0.0 ? PCG_DONE : PCG_BAD;
         });
     }
@@ -1898,8 +1917,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             }
             reduce(acc, [&](const double *t) {
                 const double pq = t[0];
-                if (!isfinite(pq)) ctl.state = PCG_BAD;
-                else if (!(pq > 0.0)) ctl.state = PCG_DONE;
+                if (!finite_b(pq)) ctl.state = PCG_BAD;
+                else if (!pos_b(pq)) ctl.state = PCG_DONE;
                 else {
                     ctl.al = div_to_f32(ctl.rz, pq);
                     ctl.alpha = (double)ctl.al;
@@ -1971,12 +1990,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 ctl.beta = (double)ctl.bt;
                 ctl.rz = t[0];
                 ctl.rr = t[1];
-                if (!isfinite(t[0]) || !isfinite(t[1])) {
+                if (!finite_b(t[0]) || !finite_b(t[1])) {
                     ctl.state = PCG_BAD;
                     return;
                 }
-                const bool done = ctl.rr <= ctl.rr_done;
-                if (ctl.folds < A.max_replace && (done || ctl.rr <= ctl.rr_fold)) ctl.state = PCG_FOLD;
+                const bool done = le_nonneg_b(ctl.rr, ctl.rr_done);  // rr, rr_done, rr_fold >= 0
+                if (ctl.folds < A.max_replace && (done || le_nonneg_b(ctl.rr, ctl.rr_fold))) ctl.state = PCG_FOLD;
                 else if (done) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
             });
@@ -2073,8 +2092,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                 ctl.rz = t[0];
                 ctl.rr = t[1];
                 ctl.rr_fold = 0.01 * t[1];
-                if (!isfinite(t[0]) || !isfinite(t[1])) ctl.state = PCG_BAD;
-                else if (ctl.rr <= ctl.rr_done) ctl.state = PCG_DONE;
+                if (!finite_b(t[0]) || !finite_b(t[1])) ctl.state = PCG_BAD;
+                else if (le_nonneg_b(ctl.rr, ctl.rr_done)) ctl.state = PCG_DONE;
                 else if (ctl.it >= A.maxit) ctl.state = PCG_MAXIT;
                 else ctl.state = PCG_RUN;
             });
