@@ -782,7 +782,9 @@ def run_eight(args, torch, B, scenes, stream, flush, ws, peak, peak_kind, seed):
     roof = pcg_roofline(kernels, info, s.nv, nc, True, cg2, peak, peak_kind, cfg, "pcg_persistent")
     if roof:
         roof["note"] = ("the matrix stays in shared memory for the whole solve, so per-iteration DRAM traffic is "
-                        "far below the algorithmic bytes (latency of the two grid-wide reductions bounds it)")
+                        "far below the algorithmic bytes; latency bounds it: the grid-wide reductions (one per "
+                        "iteration in the single-reduction form, variant 4; two in the two-reduction form, "
+                        "variant 1) and the L2 round trips of the window stage")
     # pass 3: end to end with host buffers; the positions after each step
     # give the free-running error curve against the stored oracle trajectory
     g = np.load(GOLDEN)
