@@ -353,9 +353,12 @@ int bf_enable_timers(bf_scene *scene, int32_t on);
  * the shared-memory copy of the matrix; adding 32 forces a global-memory
  * variant: in mixed precision the symmetric one (upper blocks streamed
  * once, transposed products by vector reductions into global memory),
- * else, or with 64 added, the one that streams both triangles.  The same
- * Krylov method in every mode (the same iterates in exact arithmetic); the
- * order of floating-point sums differs. */
+ * else, or with 64 added, the one that streams both triangles.  Adding 256
+ * keeps no contact pair in shared memory (every pair is read from global
+ * memory in every iteration; by default up to 256 pairs per CTA are cached
+ * in the shared memory left over).  The same Krylov method in every mode
+ * (the same iterates in exact arithmetic); the order of floating-point sums
+ * differs. */
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode);
 
 /* Configuration of the persistent PCG chosen at the scene's first solve

@@ -1417,7 +1417,7 @@ int bf_enable_timers(bf_scene *scene, int32_t on)
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
 {
     SCENE_OR_ARG(scene);
-    if (mode < 0 || mode > 255) return BF_E_ARG;
+    if (mode < 0 || mode > 511) return BF_E_ARG;
     S.pcg_mode = mode == 0 ? 0 : 1;
     if (mode > 0) {
         S.pcg_ctas_per_sm = mode & 15;
@@ -1425,6 +1425,7 @@ int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
         S.pcg_force_global = (mode & 32) ? 1 : 0;
         S.pcg_no_sym = (mode & 64) ? 1 : 0;
         S.pcg_cg1 = (mode & 128) ? 0 : 1;
+        S.pcg_no_cache = (mode & 256) ? 1 : 0;
         S.pcg_grid = 0;  // recomputed at the next solve
     }
     return BF_OK;
@@ -1448,7 +1449,7 @@ int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes,
     const int n = 3 * S.nv;
     const int keep_mode = S.pcg_mode == 0 ? 0
                           : (S.pcg_ctas_per_sm | (S.pcg_allow_resident ? 0 : 16) | (S.pcg_force_global ? 32 : 0) |
-                             (S.pcg_no_sym ? 64 : 0) | (S.pcg_cg1 ? 0 : 128));
+                             (S.pcg_no_sym ? 64 : 0) | (S.pcg_cg1 ? 0 : 128) | (S.pcg_no_cache ? 256 : 0));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);

@@ -2345,7 +2345,7 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     const size_t avail = smem_optin - fa.sharedSizeBytes;
     const PcgSymLayout L0 = pcg_sym_layout(mr, mw, mt, 0);
     if (L0.total > avail) return BF_E_CAPACITY;
-    int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(4));
+    int kc = S.pcg_no_cache ? 0 : (int)std::min<size_t>(kPcgMaxCached, (avail - L0.total) / pcg_contact_bytes(4));
     while (kc > 0 && pcg_sym_layout(mr, mw, mt, kc).total > avail) --kc;
     const PcgSymLayout L = pcg_sym_layout(mr, mw, mt, kc);
     cudaFuncSetAttribute(k_pcg_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
@@ -2431,7 +2431,7 @@ static int setup_persistent(Scene &S)
             const size_t avail = (size_t)smem_optin - fa.sharedSizeBytes;
             const size_t L0 = layout_bytes(mr, mw, me, ml, 0);
             if (L0 > avail) continue;
-            int kc = (int)std::min<size_t>(kPcgMaxCached, (avail - L0) / pcg_contact_bytes(sizeof(CT)));
+            int kc = S.pcg_no_cache ? 0 : (int)std::min<size_t>(kPcgMaxCached, (avail - L0) / pcg_contact_bytes(sizeof(CT)));
             while (kc > 0 && layout_bytes(mr, mw, me, ml, kc) > avail) --kc;
             const size_t Ltotal = layout_bytes(mr, mw, me, ml, kc);
             // the attribute is an upper bound shared by every scene: set it to

@@ -490,13 +490,14 @@ def multi_cta_state():
     return s, x, v, keys, lam, gam
 
 
-@pytest.mark.parametrize("precision,mode", [(0, 1), (1, 1), (0, 129), (1, 129)])
+@pytest.mark.parametrize("precision,mode", [(0, 1), (1, 1), (0, 129), (1, 129), (1, 257), (1, 385)])
 def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision, mode):
     """One time step from an oracle contact state on a system the persistent
     PCG spreads over several CTAs, with the single-reduction recurrence (mode
-    1) and with two reductions per iteration (mode 129): positions within
-    1e-6 (FP64) or 1e-4 (mixed) x the bounding-box diagonal, same active set
-    in FP64."""
+    1) and with two reductions per iteration (mode 129), each also with no
+    contact pair cached in shared memory (+256: every pair takes the path
+    that reads it from global memory): positions within 1e-6 (FP64) or 1e-4
+    (mixed) x the bounding-box diagonal, same active set in FP64."""
     s, x, v, keys, lam, gam = multi_cta_state
     sim, o = make_pair(s, x, v, keys, lam, gam, precision)
     B.bf_set_pcg_mode(sim.h, mode)
@@ -505,7 +506,7 @@ def test_one_step_multi_cta_scene(torch_cuda, multi_cta_state, precision, mode):
     cfg = B.bf_get_pcg_config(sim.h)
     assert cfg["ctas"] > 1
     if precision:  # FP64 blocks: the resident variants do not fit at this split
-        assert cfg["resident"] == (4 if mode == 1 else 1)
+        assert cfg["resident"] == (1 if mode & 128 else 4)
     xo, vo = o.get_state()
     xg, vg = sim.state()
     tol = (1e-6 if precision == 0 else 1e-4) * s.bbox_diag()
@@ -545,3 +546,46 @@ def test_one_step_fp64_resident_scene(torch_cuda, mode):
     assert np.abs(xg - xo).max() <= 1e-6 * s.bbox_diag(), np.abs(xg - xo).max()
     assert keyset(o2.active_get()[0]) == keyset(B.bf_get_active_set(sim.h)[0])
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pcg_uncached_contact_pairs(torch_cuda, precision):
+    """With no contact pair cached in shared memory (bf_set_pcg_mode + 256),
+    every persistent variant reads its pairs, and for the single-reduction
+    form the recurrences at the pairs' vertices, from global memory; on a
+    multi-CTA system in contact the solutions agree with the cached runs and
+    with the per-phase launches, iteration counts within 5 %."""
+    torch = torch_cuda
+    from paper_2512_12151_b300 import serving
+    s = scenes.batch_scene(11, 1.8e4, 2e4, precision=precision)
+    h, keep = serving.create(s)
+    try:
+        B.bf_step(h, 6)
+        x, _ = B.bf_get_state(h, s.nv)
+        xd = dev(torch, x)
+        xt = torch.zeros_like(xd)
+        B.bf_xtilde(h, xt)
+        B.bf_mu_init(h, xt, xd)
+        B.bf_linearize(h, xd)
+        assert len(B.bf_get_active_set(h)[0]) > 0
+        G = torch.zeros_like(xd)
+        B.bf_assemble(h, xt, xd, xd, G)
+        b = -G
+        modes = (1, 257, 385, 273, 289, 353, 0)  # resident 1-red., 2-red., streamed, global (sym), full-row, per-phase
+        sols, its, res = [], [], []
+        for mode in modes:
+            B.bf_set_pcg_mode(h, mode)
+            p = torch.zeros_like(xd)
+            it, _ = B.bf_pcg(h, b, p, 1e-6, 100000)
+            Hp = torch.zeros_like(xd)
+            B.bf_hess_apply(h, p, Hp)
+            res.append(float(torch.linalg.norm(Hp - b) / torch.linalg.norm(b)))
+            sols.append(host(p).reshape(-1))
+            its.append(it)
+        assert max(res) <= (1.01e-6 if precision == 0 else 1e-4), res
+        last = len(modes) - 1
+        for k in range(last):
+            assert abs(its[k] - its[last]) <= max(2, its[last] // 20), its
+            assert np.linalg.norm(sols[k] - sols[last]) <= 1e-4 * np.linalg.norm(sols[last])
+    finally:
+        B.bf_scene_destroy(h)
