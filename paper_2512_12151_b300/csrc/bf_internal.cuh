@@ -137,6 +137,7 @@ struct Scene {
     unsigned short *pcg_unbr = nullptr;   // ... window offset of each jagged slot
     float *pcg_uval = nullptr;            // ... jagged copy of the upper blocks (9 planes, FP32)
     float4 *pcg_yq = nullptr;             // ... transposed products and contact terms (one float4 per vertex)
+    float *pcg_pp = nullptr;              // ... upper triangle of the block-Jacobi inverse, six planes
     int *win = nullptr;       // persistent PCG: staged vertex window per CTA
     std::vector<int> h_fnbr;
     // reductions

@@ -1697,16 +1697,32 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         for (int j = 0; j < 12; ++j) s_cg[12 * k + j] = (CT)A.cg[12 * (size_t)i + j];
     }
     for (int i = threadIdx.x; i < 4 * nwin; i += blockDim.x) s_p4[i] = CT(0);  // p_old = 0
+    // P of the own rows as six planes of its upper triangle (P inverts a
+    // symmetric block): the update phase then loads them coalesced, six
+    // words per row instead of nine at a 36-byte stride
+    const size_t nvs = (size_t)A.nv;
+    float *const ppl = (float *)A.cpp;
+    for (int e = threadIdx.x; e < 6 * nr; e += blockDim.x) {
+        const int i = e / nr, row = e - i * nr;
+        const size_t a = (size_t)(r0 + row);
+        ppl[(size_t)i * nvs + a] = gpinv[9 * a + upper3(i)];
+    }
+    // z = P r of a row from its upper-triangle entries (p00 p01 p02 p11 p12 p22)
+    auto apply_p = [&](const float (&P)[6], const RT *rv, CT (&zc)[3]) {
+        zc[0] = P[0] * rv[0] + P[1] * rv[1] + P[2] * rv[2];
+        zc[1] = P[1] * rv[0] + P[3] * rv[1] + P[4] * rv[2];
+        zc[2] = P[2] * rv[0] + P[4] * rv[1] + P[5] * rv[2];
+    };
     // z = P r for local row `row` (written to global memory); returns r.z
     auto precond = [&](int row, const RT *rv) -> CT {
-        const int a = r0 + row;
-        const float *P = gpinv + 9 * (size_t)a;
-        CT zc[3];
+        const size_t a = (size_t)(r0 + row);
+        float P[6];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            zc[k] = __ldg(P + 3 * k) * rv[0] + __ldg(P + 3 * k + 1) * rv[1] + __ldg(P + 3 * k + 2) * rv[2];
-            z[3 * a + k] = zc[k];
-        }
+        for (int i = 0; i < 6; ++i) P[i] = __ldcg(ppl + (size_t)i * nvs + a);
+        CT zc[3];
+        apply_p(P, rv, zc);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) z[3 * a + k] = zc[k];
         return (rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2];
     };
     unsigned nred = 0;
@@ -1938,7 +1954,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             // kSymRowBatch rows per thread at a time, their global loads issued together
             for (int row0 = threadIdx.x; row0 < nr; row0 += kSymRowBatch * blockDim.x) {
                 float4 yg[kSymRowBatch];
-                float gq[kSymRowBatch][3], P[kSymRowBatch][9];
+                float gq[kSymRowBatch][3], P[kSymRowBatch][6];
 #pragma unroll
                 for (int u = 0; u < kSymRowBatch; ++u) {
                     const int row = row0 + u * blockDim.x;
@@ -1948,7 +1964,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
 #pragma unroll
                         for (int k = 0; k < 3; ++k) gq[u][k] = __ldcg(g_q + k * ld + row);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) P[u][i] = __ldg(gpinv + 9 * (size_t)a + i);
+                        for (int i = 0; i < 6; ++i) P[u][i] = __ldcg(ppl + (size_t)i * nvs + a);
                     }
                 }
 #pragma unroll
@@ -1968,11 +1984,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                             s_r[k * ld + row] = rv[k];
                         }
                         CT zc[3];
+                        apply_p(P[u], rv, zc);
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            zc[k] = P[u][3 * k] * rv[0] + P[u][3 * k + 1] * rv[1] + P[u][3 * k + 2] * rv[2];
-                            z[3 * a + k] = zc[k];
-                        }
+                        for (int k = 0; k < 3; ++k) z[3 * a + k] = zc[k];
                         acc[0].add((rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2]);
                         acc[1].add((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
                     }
@@ -2356,10 +2370,12 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     if (S.pcg_gvec) dev_free(S, S.pcg_gvec);
     if (S.pcg_uval) dev_free(S, S.pcg_uval);
     if (S.pcg_yq) dev_free(S, S.pcg_yq);
+    if (S.pcg_pp) dev_free(S, S.pcg_pp);
     S.pcg_gvec = (unsigned char *)dev_alloc(S, stride * grid);
     S.pcg_uval = (float *)dev_alloc(S, std::max<size_t>(ubytes, 128));
     S.pcg_yq = (float4 *)dev_alloc(S, (size_t)S.nv * sizeof(float4));
-    if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq) return BF_E_OOM;
+    S.pcg_pp = (float *)dev_alloc(S, 6 * (size_t)S.nv * sizeof(float));
+    if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq || !S.pcg_pp) return BF_E_OOM;
     S.pcg_gvec_stride = stride;
     S.pcg_grid = grid;
     S.pcg_block = block;
@@ -2597,7 +2613,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         A.cqc = cb ? (double *)(cb + cbl.qc) : nullptr;
         A.crs = cb ? cb + cbl.rs : nullptr;
         A.chx = cb ? (double *)(cb + cbl.hx) : nullptr;
-        A.cpp = cb ? cb + cbl.pp : nullptr;
+        A.cpp = S.pcg_resident == PCG_SYM ? (void *)S.pcg_pp : cb ? (void *)(cb + cbl.pp) : nullptr;
         A.cfl = cb ? cb + cbl.fl : nullptr;
     }
     if (S.pcg_resident == PCG_SYM) {
