@@ -138,6 +138,7 @@ struct Scene {
     float *pcg_uval = nullptr;            // ... jagged copy of the upper blocks (9 planes, FP32)
     float4 *pcg_yq = nullptr;             // ... transposed products and contact terms (one float4 per vertex)
     float *pcg_pp = nullptr;              // ... upper triangle of the block-Jacobi inverse, six planes
+    float4 *pcg_z4 = nullptr;             // ... z = P r, one float4 per vertex
     int *win = nullptr;       // persistent PCG: staged vertex window per CTA
     std::vector<int> h_fnbr;
     // reductions

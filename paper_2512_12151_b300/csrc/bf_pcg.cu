@@ -100,6 +100,7 @@ struct PcgArgs {
     void *cwq, *crs, *cpp;
     double *cqc, *chx;
     unsigned char *cfl;
+    float4 *z4;  // symmetric variant: z = P r, one float4 per vertex
 };
 
 enum { PCG_RUN = 0, PCG_DONE, PCG_MAXIT, PCG_BAD, PCG_FOLD, PCG_ABORT };
@@ -1625,6 +1626,7 @@ __host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win
 inline size_t pcg_sym_vec_bytes(int max_rows) { return ((60 * (size_t)max_rows) + 255) & ~(size_t)255; }
 
 constexpr int kSymRowBatch = 2;  // rows per thread whose update-phase loads are issued together
+constexpr int kSymStageBatch = 8;  // window vertices per thread whose staging loads are issued together
 constexpr int kSymPrefetchBytes = 32768;  // bytes per bulk L2 prefetch instruction
 
 // bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, a multiple of
@@ -1648,7 +1650,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     __shared__ PcgCtl ctl;
     __shared__ float2 red_f[2 * kPcgMaxWarps];
     const float *__restrict__ gpinv = (const float *)A.pinv;
-    VT *__restrict__ z = (VT *)A.z;
+    float4 *__restrict__ z4 = A.z4;  // z = P r, one float4 per vertex (one vector load each in the staging)
     VT *pb[2] = {(VT *)A.p0, (VT *)A.p1};
     float4 *__restrict__ yq = A.yq;
     const unsigned char *__restrict__ ub = (const unsigned char *)A.uval;
@@ -1721,8 +1723,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         for (int i = 0; i < 6; ++i) P[i] = __ldcg(ppl + (size_t)i * nvs + a);
         CT zc[3];
         apply_p(P, rv, zc);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) z[3 * a + k] = zc[k];
+        z4[a] = make_float4(zc[0], zc[1], zc[2], 0.f);
         return (rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2];
     };
     unsigned nred = 0;
@@ -1788,34 +1789,41 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             if (timer) tm[4] = globaltimer();
             const CT bt = (CT)ctl.bt;
             {
-                const int nf = 3 * nwin, ncf = 12 * ncached, ntot = nf + ncf;
-                const VT *zw = z + 3 * wlo;
-                for (int f0 = threadIdx.x; f0 < ntot; f0 += 8 * blockDim.x) {
-                    VT zz[8], pp[8];
+                // items: the window's vertices (z as one vector load each),
+                // then the components of the cached pairs' vertices
+                const int ncf = 12 * ncached, ntot = nwin + ncf;
+                const float *zs = (const float *)z4;
+                for (int f0 = threadIdx.x; f0 < ntot; f0 += kSymStageBatch * blockDim.x) {
+                    float4 zz[kSymStageBatch];
+                    VT pp[kSymStageBatch];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < kSymStageBatch; ++k) {
                         const int f = f0 + k * blockDim.x;
-                        zz[k] = VT(0);
+                        zz[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                         pp[k] = VT(0);
-                        if (f < nf) {
-                            zz[k] = __ldcg(zw + f);
+                        if (f < nwin) {
+                            zz[k] = __ldcg(z4 + wlo + f);
                         } else if (f < ntot) {
-                            const int g = f - nf, kk = g / 12, q = (g % 12) / 3, j = g % 3;
+                            const int g = f - nwin, kk = g / 12, q = (g % 12) / 3, j = g % 3;
                             if (s_cm[kk] >> q & 1) {
                                 const int v = (&s_cv[kk].x)[q];
-                                zz[k] = __ldcg(z + 3 * v + j);
+                                zz[k].x = __ldcg(zs + 4 * (size_t)v + j);
                                 pp[k] = __ldcg(pold + 3 * v + j);
                             }
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < kSymStageBatch; ++k) {
                         const int f = f0 + k * blockDim.x;
-                        if (f < nf) {
-                            CT *d = s_p4 + 4 * (f / 3) + f % 3;
-                            *d = dir_update(zz[k], bt, *d);
+                        if (f < nwin) {
+                            float4 *d = reinterpret_cast<float4 *>(s_p4 + 4 * f);
+                            float4 pv = *d;
+                            pv.x = dir_update(zz[k].x, bt, pv.x);
+                            pv.y = dir_update(zz[k].y, bt, pv.y);
+                            pv.z = dir_update(zz[k].z, bt, pv.z);
+                            *d = pv;
                         } else if (f < ntot) {
-                            s_cp[f - nf] = dir_update(zz[k], bt, pp[k]);
+                            s_cp[f - nwin] = dir_update(zz[k].x, bt, pp[k]);
                         }
                     }
                 }
@@ -1903,7 +1911,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
                             g[3 * q + j] = (CT)A.cg[12 * (size_t)i + 3 * q + j];
-                            u[3 * q + j] = (m >> q & 1) ? dir_update(__ldcg(z + 3 * vid[q] + j), bt,
+                            u[3 * q + j] = (m >> q & 1) ? dir_update(__ldcg((const float *)z4 + 4 * (size_t)vid[q] + j), bt,
                                                                      __ldcg(pold + 3 * vid[q] + j))
                                                         : CT(0);
                         }
@@ -1985,8 +1993,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                         }
                         CT zc[3];
                         apply_p(P[u], rv, zc);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) z[3 * a + k] = zc[k];
+                        z4[a] = make_float4(zc[0], zc[1], zc[2], 0.f);
                         acc[0].add((rv[0] * zc[0] + rv[1] * zc[1]) + rv[2] * zc[2]);
                         acc[1].add((rv[0] * rv[0] + rv[1] * rv[1]) + rv[2] * rv[2]);
                     }
@@ -2371,11 +2378,13 @@ static int setup_sym(Scene &S, int nsm, int cps, size_t smem_optin)
     if (S.pcg_uval) dev_free(S, S.pcg_uval);
     if (S.pcg_yq) dev_free(S, S.pcg_yq);
     if (S.pcg_pp) dev_free(S, S.pcg_pp);
+    if (S.pcg_z4) dev_free(S, S.pcg_z4);
     S.pcg_gvec = (unsigned char *)dev_alloc(S, stride * grid);
     S.pcg_uval = (float *)dev_alloc(S, std::max<size_t>(ubytes, 128));
     S.pcg_yq = (float4 *)dev_alloc(S, (size_t)S.nv * sizeof(float4));
     S.pcg_pp = (float *)dev_alloc(S, 6 * (size_t)S.nv * sizeof(float));
-    if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq || !S.pcg_pp) return BF_E_OOM;
+    S.pcg_z4 = (float4 *)dev_alloc(S, (size_t)S.nv * sizeof(float4));
+    if (!S.pcg_gvec || !S.pcg_uval || !S.pcg_yq || !S.pcg_pp || !S.pcg_z4) return BF_E_OOM;
     S.pcg_gvec_stride = stride;
     S.pcg_grid = grid;
     S.pcg_block = block;
@@ -2615,6 +2624,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
         A.chx = cb ? (double *)(cb + cbl.hx) : nullptr;
         A.cpp = S.pcg_resident == PCG_SYM ? (void *)S.pcg_pp : cb ? (void *)(cb + cbl.pp) : nullptr;
         A.cfl = cb ? cb + cbl.fl : nullptr;
+        A.z4 = S.pcg_z4;
     }
     if (S.pcg_resident == PCG_SYM) {
         if constexpr (std::is_same<MT, float>::value) {
