@@ -1579,10 +1579,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
 // twice: B_ij p_j joins row i's sum in registers, and B_ij^T p_i goes to
 // row j through a vector reduction (red.global.add.v4.f32) into the
 // accumulation vector yq, which the owner of row j reads (and clears) after
-// the grid-wide reduction that ends the product.  Contact terms add into
-// yq the same way.  The product p.Hp needs no complete q: with D_i the
-// diagonal blocks, p.Hp = sum_i p_i.D_i p_i + 2 sum_{i<j} p_i.B_ij p_j,
-// which each row's thread forms from its own blocks.
+// the grid-wide reduction that ends the product.  Each row's own sum and the
+// contact terms add into yq the same way, so yq holds q = H p complete.  The
+// product p.Hp needs no complete q: with D_i the diagonal blocks, p.Hp =
+// sum_i p_i.D_i p_i + 2 sum_{i<j} p_i.B_ij p_j, which each row's thread
+// forms from its own blocks.
 //
 // Per CTA: rows [part[c], part[c+1]) in order of decreasing upper length,
 // taken in rounds of blockDim.x rows (one per thread); the blocks stream in
@@ -1590,9 +1591,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
 // block) and each round is prefetched into L2 while the previous one is
 // summed, the first during the reductions before the product; the window
 // of p over [part[c], last upper neighbour] in shared memory (16-bit
-// offsets); r and the FP32 increment of x per row in shared memory; the
-// rows' part of q, FP64 x and H x of the reliable updates in a per-CTA
-// global vector (L2-resident).
+// offsets); r and the FP32 increment of x per row in shared memory; z = P r
+// as one float4 per vertex and P as six planes of its upper triangle in
+// global memory; FP64 x and H x of the reliable updates in a per-CTA global
+// vector (L2-resident).
 // ---------------------------------------------------------------------------
 struct PcgSymLayout {
     size_t p4, r, xl, rinfo, lvl, cg, cp, cw, cv, cm, total;
@@ -1621,9 +1623,8 @@ __host__ __device__ inline PcgSymLayout pcg_sym_layout(int max_rows, int max_win
     return L;
 }
 
-// per-CTA global vector of the symmetric variant: FP64 x and H x, FP32 row
-// sums q (3 per row each)
-inline size_t pcg_sym_vec_bytes(int max_rows) { return ((60 * (size_t)max_rows) + 255) & ~(size_t)255; }
+// per-CTA global vector of the symmetric variant: FP64 x and H x (3 per row each)
+inline size_t pcg_sym_vec_bytes(int max_rows) { return ((48 * (size_t)max_rows) + 255) & ~(size_t)255; }
 
 constexpr int kSymRowBatch = 2;  // rows per thread whose update-phase loads are issued together
 constexpr int kSymStageBatch = 8;  // window vertices per thread whose staging loads are issued together
@@ -1666,7 +1667,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
     const int ld = A.max_rows;  // per-row arrays are component-major: a[k * ld + row]
     double *g_x = (double *)(A.gvec + (size_t)c * A.gvec_stride);
     double *g_hx = g_x + 3 * (size_t)ld;
-    float *g_q = (float *)(g_hx + 3 * (size_t)ld);
     CT *s_p4 = (CT *)(smem + L.p4);
     RT *s_r = (RT *)(smem + L.r);
     RT *s_xl = (RT *)(smem + L.xl);
@@ -1878,8 +1878,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                         }
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) g_q[k * ld + row] = yd[k] + yo[k];
+                red_add4(yq + r0 + row, yd[0] + yo[0], yd[1] + yo[1], yd[2] + yo[2]);  // q complete in yq
                 acc[0].add((pi[0] * yd[0] + pi[1] * yd[1]) + pi[2] * yd[2]);
                 acc[0].add(2.f * ((pi[0] * yo[0] + pi[1] * yo[1]) + pi[2] * yo[2]));
             }
@@ -1962,15 +1961,14 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
             // kSymRowBatch rows per thread at a time, their global loads issued together
             for (int row0 = threadIdx.x; row0 < nr; row0 += kSymRowBatch * blockDim.x) {
                 float4 yg[kSymRowBatch];
-                float gq[kSymRowBatch][3], P[kSymRowBatch][6];
+                float P[kSymRowBatch][6];
 #pragma unroll
                 for (int u = 0; u < kSymRowBatch; ++u) {
                     const int row = row0 + u * blockDim.x;
                     if (row < nr) {
                         const int a = r0 + row;
                         yg[u] = __ldcg(yq + a);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) gq[u][k] = __ldcg(g_q + k * ld + row);
+
 #pragma unroll
                         for (int i = 0; i < 6; ++i) P[u][i] = __ldcg(ppl + (size_t)i * nvs + a);
                     }
@@ -1983,7 +1981,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
                         yq[a] = make_float4(0.f, 0.f, 0.f, 0.f);
                         CT pc[3];
                         load3v(s_p4 + 4 * row, pc);
-                        const float qk[3] = {gq[u][0] + yg[u].x, gq[u][1] + yg[u].y, gq[u][2] + yg[u].z};
+                        const float qk[3] = {yg[u].x, yg[u].y, yg[u].z};
                         RT rv[3];
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
