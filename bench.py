@@ -611,9 +611,10 @@ def run_large(args, torch, B, scenes, stream, ws, peak, peak_kind):
 
 
 def run_large_window(args, torch, B, scenes, stream, ws, **params):
-    """The headline scene with modified parameters (the CCD-reuse option):
-    the same window around peak compression, steps before it untimed, each
-    timed step with CUDA events; no replays and no release."""
+    """The headline scene with modified parameters (the CCD-reuse option, or
+    the paper's CG tolerance): the same window around peak compression, the
+    steps before it untimed with the same parameters, each timed step with
+    CUDA events; no replays and no release."""
     s = scenes.spiky_balls(precision=1)
     for k, v in params.items():
         setattr(s.params, k, v)
@@ -910,6 +911,8 @@ def main():
     ap.add_argument("--large-reuse", type=int, default=0, help="headline with the CCD-reuse option")
     ap.add_argument("--large-reuse-line", type=int, default=1,
                     help="the headline window again with the CCD-reuse option, as an extra line (0: skip)")
+    ap.add_argument("--large-tol-line", type=int, default=1,
+                    help="the headline window again at the paper's CG tolerance 1e-4, as an extra line (0: skip)")
     ap.add_argument("--eight-cubes", type=int, default=1, help="the eight-cube line (0: skip)")
     ap.add_argument("--two-cubes", type=int, default=1, help="the two-cube FP64 line (0: skip)")
     ap.add_argument("--batched-scenes", type=int, default=256,
@@ -968,6 +971,12 @@ def main():
         LR["workload"] = ("the spiky-ball compression with the CCD-reuse option (one CCD per outer iteration serves "
                           "UpdateActiveSet and MaxStepSize), the same window, mixed precision")
         _progress(f"large with CCD reuse: {LR['steps_per_s']:.3f} steps/s")
+    LT = None
+    if args.large_tol_line:
+        LT = run_large_window(args, torch, B, scenes, stream, ws, cg_tol=1e-4)
+        LT["workload"] = ("the spiky-ball compression at the paper's CG relative tolerance 1e-4 (the headline uses "
+                          "1e-6), every step up to the window at that tolerance, the same window, mixed precision")
+        _progress(f"large at CG tolerance 1e-4: {LT['steps_per_s']:.3f} steps/s")
 
     # ---- the two-cube scene, FP64 (the small configuration) --------------------
     T = run_two(torch, B, scenes, stream, flush, ws) if args.two_cubes else None
@@ -1133,6 +1142,8 @@ def main():
                                  "us_per_iteration_by_mode": {str(k): round(v, 3) for k, v in E["tuned"][1].items()}}}
         if LR:
             line["large_ccd_reuse"] = LR
+        if LT:
+            line["large_cg_tol_1e-4"] = LT
         if T:
             line["two_cubes_fp64"] = T
         if batched:
