@@ -389,6 +389,16 @@ int bf_get_pcg_config(bf_scene *scene, int32_t *cfg);
 int bf_autotune_pcg(bf_scene *scene, int32_t iters, int32_t cap, int32_t *modes, double *us_per_iter,
                     int32_t *n_out, int32_t *best);
 
+/* Failure-detection test of the persistent PCG's bounded waits (not needed
+ * in normal use).  With `on` nonzero, the scene's next persistent solves
+ * arrive at their grid barriers as usual but wait on a device word that no
+ * CTA increments, so the first grid-wide reduction of a solve never
+ * completes: every CTA gives up after its time limit (2 s), the kernel
+ * ends, the solve returns BF_E_CUDA, and the scene and the CUDA context stay
+ * usable (call again with 0 to solve normally).  Returns BF_E_ARG for a NULL
+ * scene. */
+int bf_test_pcg_barrier_fail(bf_scene *scene, int32_t on);
+
 /* Number of this library's own kernel launches issued for the scene since
  * creation (sorts and scans done by CUB are not counted); *n host. */
 int bf_get_launch_count(bf_scene *scene, int64_t *n);

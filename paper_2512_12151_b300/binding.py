@@ -110,6 +110,7 @@ def lib():
         "bf_enable_timers": [_P, C.c_int32],
         "bf_get_launch_count": [_P, C.POINTER(C.c_int64)],
         "bf_set_pcg_mode": [_P, C.c_int32],
+        "bf_test_pcg_barrier_fail": [_P, C.c_int32],
         "bf_autotune_pcg": [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                             C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "bf_get_pcg_config": [_P, _P],
@@ -433,6 +434,10 @@ def bf_autotune_pcg(h, iters=64):
 
 def bf_set_pcg_mode(h, mode):
     _check("bf_set_pcg_mode", lib().bf_set_pcg_mode(h, mode))
+
+
+def bf_test_pcg_barrier_fail(h, on):
+    _check("bf_test_pcg_barrier_fail", lib().bf_test_pcg_barrier_fail(h, on))
 
 
 def bf_get_pcg_config(h):

@@ -1414,6 +1414,13 @@ int bf_enable_timers(bf_scene *scene, int32_t on)
     return BF_OK;
 }
 
+int bf_test_pcg_barrier_fail(bf_scene *scene, int32_t on)
+{
+    SCENE_OR_ARG(scene);
+    S.pcg_bar_fail = on ? 1 : 0;
+    return BF_OK;
+}
+
 int bf_set_pcg_mode(bf_scene *scene, int32_t mode)
 {
     SCENE_OR_ARG(scene);

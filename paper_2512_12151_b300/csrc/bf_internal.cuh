@@ -132,6 +132,7 @@ struct Scene {
     int pcg_no_sym = 0;           // persistent PCG: skip the symmetric (upper-only) variant
     int pcg_cg1 = 1;              // persistent PCG: single-reduction recurrence when the blocks are resident
     int pcg_no_cache = 0;         // persistent PCG: no contact pairs cached in shared memory
+    int pcg_bar_fail = 0;         // persistent PCG: barriers poll an idle word (failure-detection test hook)
     unsigned char *pcg_cg1buf = nullptr;  // ... its published row sums, contact parts, (r, s) and H x
     int *pcg_uedst = nullptr;             // symmetric variant: jagged position of each upper block
     unsigned short *pcg_unbr = nullptr;   // ... window offset of each jagged slot

@@ -85,6 +85,7 @@ struct PcgArgs {
     double *qd;               // FP64 contact part of H x (reliable updates)
     double *res;
     unsigned *bar;
+    const unsigned *bar_poll;  // the word the barrier spins on (bar, or an idle word in the failure test)
     double tol2;
     int maxit, max_replace, max_rows, max_ent, max_win, max_len, kc;
     double *dscal;
@@ -262,11 +263,12 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s: far bey
 // written after this one).  Barrier: one arrival counter whose top bit
 // flips when every CTA has arrived (CTA 0 adds 0x80000000 - (gridDim.x - 1),
 // the others 1, so the sum of one barrier's arrivals is 0x80000000), with a
-// release on the arrival and acquire loads while spinning (bounded:
-// ERR_BARRIER and false on timeout).
+// release on the arrival and acquire loads of `poll` while spinning
+// (bounded: ERR_BARRIER and false on timeout).  `poll` is `bar` except in the
+// failure-detection test, which polls a word no CTA increments.
 template <int K>
-__device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, unsigned n, unsigned *bar, int *dflag,
-                                           double (&tot)[K])
+__device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, unsigned n, unsigned *bar,
+                                           const unsigned *poll, int *dflag, double (&tot)[K])
 {
     const unsigned slot = n % 3u, next = (n + 1u) % 3u;
 #pragma unroll
@@ -282,7 +284,7 @@ __device__ __forceinline__ bool grid_total(const double (&v)[K], double *acc, un
     const unsigned want = ((n + 1u) & 1u) << 31;
     unsigned spins = 0;
     unsigned long long t_start = 0;
-    while ((ld_acquire_gpu(bar) & 0x80000000u) != want) {
+    while ((ld_acquire_gpu(poll) & 0x80000000u) != want) {
         if ((++spins & 255u) == 0u) {  // give up after kBarrierTimeoutNs
             const unsigned long long t = globaltimer();
             if (t_start == 0) t_start = t;
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_persistent(PcgArgs A)
         if constexpr (mixed) block_sum<K>(acc, blk, red_f);
         else block_sum<K>(acc, blk, red_d, red_q4);
         if (threadIdx.x == 0) {
-            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.bar_poll, A.dflag, tot)) on_total(tot);
             else ctl.state = PCG_ABORT;
         }
         ++nred;
@@ -1121,7 +1123,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cg1(PcgArgs A)
         if constexpr (mixed) block_sum<K>(acc, blk, red_f);
         else block_sum<K>(acc, blk, red_d, red_q4);
         if (threadIdx.x == 0) {
-            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.bar_poll, A.dflag, tot)) on_total(tot);
             else ctl.state = PCG_ABORT;
         }
         ++nred;
@@ -1732,7 +1734,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_sym(PcgArgs A)
         double blk[K], tot[K];
         block_sum<K>(acc, blk, red_f);
         if (threadIdx.x == 0) {
-            if (grid_total<K>(blk, A.res, nred, A.bar, A.dflag, tot)) on_total(tot);
+            if (grid_total<K>(blk, A.res, nred, A.bar, A.bar_poll, A.dflag, tot)) on_total(tot);
             else ctl.state = PCG_ABORT;
         }
         ++nred;
@@ -2594,6 +2596,7 @@ static int persistent_impl(Scene &S, const MT *val, const MT *pinv, VT *p0, VT *
     A.qd = S.cg_qc;  // FP64 contact part of H p, and of H x in the reliable updates
     A.res = S.dscal + S_RES;
     A.bar = S.bar;
+    A.bar_poll = S.pcg_bar_fail ? S.bar + 1 : S.bar;  // failure-detection test: a word no CTA increments
     A.tol2 = tol * tol;
     A.maxit = maxit;
     A.max_replace = 64;

@@ -589,3 +589,47 @@ def test_pcg_uncached_contact_pairs(torch_cuda, precision):
             assert np.linalg.norm(sols[k] - sols[last]) <= 1e-4 * np.linalg.norm(sols[last])
     finally:
         B.bf_scene_destroy(h)
+
+
+def test_pcg_bounded_waits_report_and_recover(torch_cuda):
+    """Failure detection without a GPU fault: with the grid barriers waiting
+    on a word that no CTA increments (bf_test_pcg_barrier_fail), the first
+    grid-wide reduction of a solve never completes, every CTA of each
+    persistent variant (single-reduction resident, two-reduction resident,
+    symmetric) gives up after its 2 s limit and the solve returns BF_E_CUDA;
+    the next solve on the same scene and context succeeds."""
+    import time
+    torch = torch_cuda
+    from paper_2512_12151_b300 import serving
+    s = scenes.batch_scene(11, 1.8e4, 2e4, precision=1)
+    h, keep = serving.create(s)
+    try:
+        B.bf_step(h, 2)
+        x, _ = B.bf_get_state(h, s.nv)
+        xd = dev(torch, x)
+        xt = torch.zeros_like(xd)
+        B.bf_xtilde(h, xt)
+        B.bf_mu_init(h, xt, xd)
+        B.bf_linearize(h, xd)
+        G = torch.zeros_like(xd)
+        B.bf_assemble(h, xt, xd, xd, G)
+        for mode, variant in ((1, 4), (129, 1), (33, 3)):
+            B.bf_set_pcg_mode(h, mode)
+            p = torch.zeros_like(xd)
+            B.bf_pcg(h, -G, p, 1e-6, 100000)  # set-up solve
+            assert B.bf_get_pcg_config(h)["resident"] == variant
+            B.bf_test_pcg_barrier_fail(h, 1)
+            t0 = time.perf_counter()
+            with pytest.raises(B.BfError) as e:
+                B.bf_pcg(h, -G, torch.zeros_like(xd), 1e-6, 100000)
+            assert e.value.status == -3  # BF_E_CUDA
+            assert 1.5 < time.perf_counter() - t0 < 30.0  # every CTA waited out its 2 s limit, no longer
+            B.bf_test_pcg_barrier_fail(h, 0)
+            p = torch.zeros_like(xd)
+            it, _ = B.bf_pcg(h, -G, p, 1e-6, 100000)
+            Hp = torch.zeros_like(xd)
+            B.bf_hess_apply(h, p, Hp)
+            assert it > 0 and float(torch.linalg.norm(Hp + G) / torch.linalg.norm(G)) <= 1e-4
+        assert B.bf_step(h, 1)[0] == 0  # the scene steps on
+    finally:
+        B.bf_scene_destroy(h)
