@@ -2445,8 +2445,11 @@ static int setup_persistent(Scene &S)
         for (int cps = per_sm; cps >= 1; --cps) {
             // small systems take fewer CTAs (about kPcgEntriesPerCta blocks
             // each), which keeps the barriers short and leaves SMs to other
-            // scenes running concurrently
-            const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nfull, kPcgEntriesPerCta)));
+            // scenes running concurrently; FP64 blocks take a quarter of that
+            // (twice the bytes, and B300's narrow FP64 pipe: the blocks then
+            // fit in shared memory and their arithmetic spreads over more SMs)
+            const int per_cta = sizeof(MT) == 8 ? kPcgEntriesPerCta / 4 : kPcgEntriesPerCta;
+            const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nfull, per_cta)));
             if (grid > kPcgMaxGrid) continue;
             const int block = (kPcgThreads / cps) & ~31;
             int mr = 0, me = 0, mw = 0, ml = 0;
