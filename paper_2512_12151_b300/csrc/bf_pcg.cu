@@ -2443,14 +2443,12 @@ static int setup_persistent(Scene &S)
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BF_E_CUDA;
         for (int cps = per_sm; cps >= 1; --cps) {
-            // small systems take fewer CTAs (about kPcgEntriesPerCta / 2
-            // blocks each in mixed precision: measured best for many scenes
-            // running concurrently, against twice and half that), which keeps
-            // the barriers short and leaves SMs to the other scenes; FP64
-            // blocks take a quarter of kPcgEntriesPerCta (twice the bytes, and
-            // B300's narrow FP64 pipe: the blocks then fit in shared memory
-            // and their arithmetic spreads over more SMs)
-            const int per_cta = sizeof(MT) == 8 ? kPcgEntriesPerCta / 4 : kPcgEntriesPerCta / 2;
+            // small systems take fewer CTAs (about kPcgEntriesPerCta blocks
+            // each), which keeps the barriers short and leaves SMs to other
+            // scenes running concurrently; FP64 blocks take a quarter of that
+            // (twice the bytes, and B300's narrow FP64 pipe: the blocks then
+            // fit in shared memory and their arithmetic spreads over more SMs)
+            const int per_cta = sizeof(MT) == 8 ? kPcgEntriesPerCta / 4 : kPcgEntriesPerCta;
             const int grid = std::max(1, std::min(nsm * cps, cdiv(S.nfull, per_cta)));
             if (grid > kPcgMaxGrid) continue;
             const int block = (kPcgThreads / cps) & ~31;
